@@ -1,0 +1,250 @@
+"""CPU oracle for the seed-hit + diagonal-skip + ungapped X-drop hot path.
+
+TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the benchmark's
+CPU-baseline leg (and its `--impl reference` arm) may import this package. It
+is the plain serial definition that the CUDA library is checked against bit
+for bit; it shares no code with that library and imports nothing from it.
+
+The arithmetic lives in `sfe_oracle.c` (plain C). This module only marshals
+numpy arrays through ctypes. Every definition it relies on is stated in the
+header comment of `sfe_oracle.c`; the MLP reference for learned binning is in
+`mlp.py`.
+"""
+from __future__ import annotations
+
+import contextlib
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+DEFAULT_PATTERN = "1110100110010101111"  # 12 of 19, Section 7
+
+# HOXD70 (Chiaromonte, Yap and Miller 2002), rows = target base, columns =
+# query base, order A C G T; the substitution scores of the paper's LASTZ
+# pipeline (Section 2). Recalled from the literature; pinned in the tests by
+# its published symmetries, not by a printed copy.
+HOXD70 = np.array([
+    [91, -114, -31, -123],
+    [-114, 100, -125, -31],
+    [-31, -125, 100, -114],
+    [-123, -31, -114, 91],
+], dtype=np.int32)
+XDROP = 910       # LASTZ default: 10 x the A:A score
+HSP_THRESH = 3000  # LASTZ default ungapped threshold
+
+SKIP_PASSING_ONLY = 1
+
+HSP_DTYPE = np.dtype([("strand", "<i4"), ("tpos", "<i4"), ("qpos", "<i4"), ("len", "<i4"),
+                      ("score", "<i4")])
+EXT_DTYPE = np.dtype({
+    "names": ["strand", "t", "q", "lext", "rext", "lscored", "rscored", "score"],
+    "formats": ["<i4"] * 7 + ["<i8"],
+    "offsets": [0, 4, 8, 12, 16, 20, 24, 32],
+    "itemsize": 40,
+})
+
+
+class _Stats(C.Structure):
+    _fields_ = [("hits", C.c_int64), ("extended", C.c_int64), ("cells", C.c_int64),
+                ("hsps", C.c_int64)]
+
+
+class _Ext(C.Structure):
+    _fields_ = [("strand", C.c_int32), ("t", C.c_int32), ("q", C.c_int32),
+                ("lext", C.c_int32), ("rext", C.c_int32), ("lscored", C.c_int32),
+                ("rscored", C.c_int32), ("_pad", C.c_int32), ("score", C.c_int64)]
+
+
+_lib = None
+
+
+def _bind(path: str):
+    L = C.CDLL(path)
+    u8p = C.POINTER(C.c_uint8)
+    i32p = C.POINTER(C.c_int32)
+    i64p = C.POINTER(C.c_int64)
+    L.or_encode.argtypes = [u8p, C.c_int64, u8p]
+    L.or_encode.restype = C.c_int
+    L.or_revcomp.argtypes = [u8p, C.c_int64, u8p]
+    L.or_revcomp.restype = None
+    L.or_run.argtypes = [u8p, C.c_int64, u8p, C.c_int64, C.c_char_p, C.c_int, C.c_int,
+                         i32p, C.c_int32, C.c_int32, C.c_int, C.c_int, C.POINTER(C.c_int)]
+    L.or_run.restype = C.c_void_p
+    L.or_run_diagonal.argtypes = [u8p, C.c_int64, u8p, C.c_int64, C.c_int, C.c_int64,
+                                  C.c_int64, C.c_char_p, C.c_int, i32p, C.c_int32,
+                                  C.c_int32, C.c_int, C.c_int, C.POINTER(C.c_int)]
+    L.or_run_diagonal.restype = C.c_void_p
+    L.or_seed_hits.argtypes = [u8p, C.c_int64, u8p, C.c_int64, C.c_char_p, C.c_int,
+                               i64p, i64p, C.c_int64, C.POINTER(C.c_int)]
+    L.or_seed_hits.restype = C.c_int64
+    L.or_xdrop.argtypes = [u8p, C.c_int64, u8p, C.c_int64, C.c_int64, C.c_int64, C.c_int,
+                           i32p, C.c_int32, C.POINTER(_Ext)]
+    L.or_xdrop.restype = None
+    L.or_result_count.argtypes = [C.c_void_p]
+    L.or_result_count.restype = C.c_int64
+    L.or_result_ext_count.argtypes = [C.c_void_p]
+    L.or_result_ext_count.restype = C.c_int64
+    L.or_result_stats.argtypes = [C.c_void_p, C.POINTER(_Stats)]
+    L.or_result_stats.restype = None
+    L.or_result_copy.argtypes = [C.c_void_p, C.c_void_p]
+    L.or_result_copy.restype = None
+    L.or_result_copy_ext.argtypes = [C.c_void_p, C.c_void_p]
+    L.or_result_copy_ext.restype = None
+    L.or_result_free.argtypes = [C.c_void_p]
+    L.or_result_free.restype = None
+    return L
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = _bind(_build.build())
+    return _lib
+
+
+@contextlib.contextmanager
+def use_library(path: str):
+    """Temporarily route every oracle call through another build of sfe_oracle.c.
+
+    The mutation tests use this to check that the pins reject oracles with a
+    planted mistake.
+    """
+    global _lib
+    saved = lib()
+    _lib = _bind(path)
+    try:
+        yield
+    finally:
+        _lib = saved
+
+
+def _u8(a) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.uint8)
+    return a if a.size else np.zeros(1, np.uint8)[:0]
+
+
+def _ptr(a, t):
+    if a.size == 0:
+        a = np.zeros(1, dtype=a.dtype)
+        _keep.append(a)
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+_keep: list = []
+
+
+def _scores(scores) -> np.ndarray:
+    m = np.ascontiguousarray(np.asarray(scores, dtype=np.int32).reshape(16))
+    return m
+
+
+def encode(ascii_bytes: bytes) -> np.ndarray:
+    a = np.frombuffer(bytes(ascii_bytes), dtype=np.uint8).copy()
+    out = np.zeros(max(1, a.size), dtype=np.uint8)
+    if lib().or_encode(_ptr(a, C.c_uint8), a.size, _ptr(out, C.c_uint8)) != 0:
+        raise ValueError("symbol outside ACGTacgt")
+    return out[: a.size]
+
+
+def revcomp(Q) -> np.ndarray:
+    Q = _u8(Q)
+    out = np.zeros(max(1, Q.size), dtype=np.uint8)
+    lib().or_revcomp(_ptr(Q, C.c_uint8), Q.size, _ptr(out, C.c_uint8))
+    return out[: Q.size]
+
+
+@dataclass
+class Result:
+    hsps: np.ndarray          # HSP_DTYPE, sorted by (strand, tpos, qpos, len, score)
+    hits: int
+    extended: int
+    cells: int
+    ext: np.ndarray | None    # EXT_DTYPE log of every extension (processing order)
+
+    @property
+    def stats(self) -> dict:
+        return {"hits": self.hits, "extended": self.extended, "cells": self.cells,
+                "hsps": int(self.hsps.size)}
+
+
+def _collect(h, err, keep_log) -> Result:
+    if not h:
+        raise RuntimeError(f"oracle error {err.value}")
+    L = lib()
+    try:
+        n = L.or_result_count(h)
+        out = np.zeros(n, dtype=HSP_DTYPE)
+        if n:
+            L.or_result_copy(h, out.ctypes.data)
+        st = _Stats()
+        L.or_result_stats(h, C.byref(st))
+        ext = None
+        if keep_log:
+            m = L.or_result_ext_count(h)
+            ext = np.zeros(m, dtype=EXT_DTYPE)
+            if m:
+                L.or_result_copy_ext(h, ext.ctypes.data)
+        return Result(out, st.hits, st.extended, st.cells, ext)
+    finally:
+        L.or_result_free(h)
+
+
+def run(T, Q, pattern: str = DEFAULT_PATTERN, transition: bool = True, strands: int = 3,
+        scores=HOXD70, X: int = XDROP, thresh: int = HSP_THRESH, flags: int = 0,
+        keep_log: bool = False) -> Result:
+    """The filter stage on one pair: hits -> per-diagonal skip -> X-drop -> sorted HSPs."""
+    T, Q = _u8(T), _u8(Q)
+    M = _scores(scores)
+    err = C.c_int(0)
+    h = lib().or_run(_ptr(T, C.c_uint8), T.size, _ptr(Q, C.c_uint8), Q.size, pattern.encode(),
+                     int(transition), int(strands), _ptr(M, C.c_int32), int(X), int(thresh),
+                     int(flags), int(keep_log), C.byref(err))
+    return _collect(h, err, keep_log)
+
+
+def run_diagonal(T, Qs, strand: int, d: int, E0: int = -(1 << 62), pattern: str = DEFAULT_PATTERN,
+                 transition: bool = True, scores=HOXD70, X: int = XDROP,
+                 thresh: int = HSP_THRESH, flags: int = 0, keep_log: bool = False) -> Result:
+    """The walk restricted to diagonal d = t - q of Qs (Qs already strand-oriented)."""
+    T, Qs = _u8(T), _u8(Qs)
+    M = _scores(scores)
+    err = C.c_int(0)
+    h = lib().or_run_diagonal(_ptr(T, C.c_uint8), T.size, _ptr(Qs, C.c_uint8), Qs.size,
+                              int(strand), int(d), int(E0), pattern.encode(), int(transition),
+                              _ptr(M, C.c_int32), int(X), int(thresh), int(flags),
+                              int(keep_log), C.byref(err))
+    return _collect(h, err, keep_log)
+
+
+def seed_hits(T, Qs, pattern: str = DEFAULT_PATTERN, transition: bool = True):
+    """All hits (t, q) of T against the strand-oriented Qs, sorted by (t - q, t)."""
+    T, Qs = _u8(T), _u8(Qs)
+    err = C.c_int(0)
+    L = lib()
+    empty = np.zeros(1, dtype=np.int64)
+    n = L.or_seed_hits(_ptr(T, C.c_uint8), T.size, _ptr(Qs, C.c_uint8), Qs.size,
+                       pattern.encode(), int(transition), _ptr(empty, C.c_int64),
+                       _ptr(empty, C.c_int64), 0, C.byref(err))
+    if n < 0:
+        raise RuntimeError(f"oracle error {err.value}")
+    t = np.zeros(max(n, 1), dtype=np.int64)
+    q = np.zeros(max(n, 1), dtype=np.int64)
+    L.or_seed_hits(_ptr(T, C.c_uint8), T.size, _ptr(Qs, C.c_uint8), Qs.size, pattern.encode(),
+                   int(transition), _ptr(t, C.c_int64), _ptr(q, C.c_int64), n, C.byref(err))
+    return t[:n], q[:n]
+
+
+def xdrop(T, Qs, t: int, q: int, span: int = 19, scores=HOXD70, X: int = XDROP) -> dict:
+    """One ungapped X-drop extension of the hit (t, q)."""
+    T, Qs = _u8(T), _u8(Qs)
+    M = _scores(scores)
+    e = _Ext()
+    lib().or_xdrop(_ptr(T, C.c_uint8), T.size, _ptr(Qs, C.c_uint8), Qs.size, int(t), int(q),
+                   int(span), _ptr(M, C.c_int32), int(X), C.byref(e))
+    return {"lext": e.lext, "rext": e.rext, "lscored": e.lscored, "rscored": e.rscored,
+            "score": e.score, "tpos": t - e.lext, "qpos": q - e.lext,
+            "len": span + e.lext + e.rext, "end": t + span + e.rext,
+            "cells": span + e.lscored + e.rscored}

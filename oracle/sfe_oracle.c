@@ -1,0 +1,537 @@
+/*
+ * CPU oracle for spaced-seed hit generation, the per-diagonal skip and the
+ * ungapped X-drop filter (the filter stage of the seed-filter-extend pipeline,
+ * Section 1 and Section 2 of the paper; its loop shape is Algorithm 1).
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the plain, slow, serial statement of
+ * what the CUDA library must compute bit for bit. It is used by the tests, by
+ * the smoke check and by the benchmark's CPU-baseline leg, never by the product
+ * path, and it shares no code, header or table with the CUDA library.
+ *
+ * Coding: A=0, C=1, G=2, T=3 (one byte per base). Complement x^3, transition
+ * partner x^2 (A<->G, C<->T).
+ *
+ * Definitions (the paper names the steps but fixes none of these details; each
+ * reading below is recorded in the design notes):
+ *
+ *  Seed (Section 7): a pattern of '1' (care) and '0' (don't care) positions,
+ *  default 1110100110010101111 (weight 12, span 19). (s, t, q) is a hit iff at
+ *  every care offset c, T[t+c] equals Qs[q+c], except that with transition
+ *  tolerance (Section 2) at most one care offset may hold a transition
+ *  (T[t+c] == Qs[q+c]^2). Q+ = Q; Q- = reverse complement of Q, and minus-strand
+ *  coordinates index Q-.
+ *
+ *  Skip (Algorithm 1, the IsContained test; the masking-list update): hits are
+ *  processed per (strand, diagonal d = t - q) in increasing t. A hit with
+ *  t < E is skipped, where E is the exclusive end of the last extended HSP on
+ *  that diagonal (E starts below every t). E is updated after every extension,
+ *  or only after extensions that reach the threshold when OR_SKIP_PASSING_ONLY
+ *  is set.
+ *
+ *  X-drop (Section 2, Section 8: ungapped, 1-D): the HSP always holds the whole
+ *  seed span [t, t+span). The right extension scores bases t+span, t+span+1, ...
+ *  while both sequences last, keeping the running sum, its maximum (which
+ *  starts at 0 for the empty extension) and the earliest length at which the
+ *  maximum is reached; it stops right after the first base at which
+ *  maximum - sum > X. The left extension is the mirror image from t-1 down.
+ *  HSP = [t - lbest_len, t + span + rbest_len), score = span score + both
+ *  maxima. E = t + span + rbest_len. cells = span + bases scored on both sides.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_OK 0
+#define OR_EINVAL (-1)
+#define OR_ENOMEM (-2)
+
+#define OR_SKIP_PASSING_ONLY 1
+
+typedef struct {
+    int32_t strand, tpos, qpos, len, score;
+} or_hsp;
+
+typedef struct {
+    int64_t hits;     /* seed hits enumerated */
+    int64_t extended; /* hits not skipped, i.e. X-drop extensions run */
+    int64_t cells;    /* span + bases scored, summed over extended hits */
+    int64_t hsps;     /* extensions with score >= threshold */
+} or_stats;
+
+/* One extension, as a record (used for per-hit logs). */
+typedef struct {
+    int32_t strand, t, q, lext, rext, lscored, rscored;
+    int64_t score;
+} or_ext;
+
+typedef struct {
+    int span, weight;
+    int care[32];
+} or_pattern;
+
+/* ---------------------------------------------------------------- basics */
+
+int or_encode(const uint8_t *ascii, int64_t n, uint8_t *codes)
+{
+    for (int64_t i = 0; i < n; i++) {
+        switch (ascii[i]) {
+        case 'A': case 'a': codes[i] = 0; break;
+        case 'C': case 'c': codes[i] = 1; break;
+        case 'G': case 'g': codes[i] = 2; break;
+        case 'T': case 't': codes[i] = 3; break;
+        default: return OR_EINVAL;
+        }
+    }
+    return OR_OK;
+}
+
+void or_revcomp(const uint8_t *q, int64_t n, uint8_t *out)
+{
+    for (int64_t i = 0; i < n; i++)
+        out[i] = (uint8_t)(q[n - 1 - i] ^ 3);
+}
+
+int or_parse_pattern(const char *s, or_pattern *p)
+{
+    int n = (int)strlen(s);
+    if (n < 1 || n > 32)
+        return OR_EINVAL;
+    p->span = n;
+    p->weight = 0;
+    for (int i = 0; i < n; i++) {
+        if (s[i] == '1')
+            p->care[p->weight++] = i;
+        else if (s[i] != '0')
+            return OR_EINVAL;
+    }
+    if (p->weight < 1 || p->weight > 16)
+        return OR_EINVAL;
+    return OR_OK;
+}
+
+/* The hit predicate, written out directly (Section 7 seed, Section 2 transitions). */
+int or_is_hit(const uint8_t *T, const uint8_t *Qs, int64_t t, int64_t q,
+              const or_pattern *p, int transition)
+{
+    int used = 0;
+    for (int i = 0; i < p->weight; i++) {
+        uint8_t a = T[t + p->care[i]], b = Qs[q + p->care[i]];
+        if (a == b)
+            continue;
+        if (transition && (a ^ b) == 2 && !used) {
+            used = 1;
+            continue;
+        }
+        return 0;
+    }
+    return 1;
+}
+
+/* ------------------------------------------------------------- the index */
+
+typedef struct {
+    uint32_t key;
+    int64_t pos;
+} or_entry;
+
+static int cmp_entry(const void *a, const void *b)
+{
+    const or_entry *x = (const or_entry *)a, *y = (const or_entry *)b;
+    if (x->key != y->key)
+        return x->key < y->key ? -1 : 1;
+    return (x->pos > y->pos) - (x->pos < y->pos);
+}
+
+static uint32_t seed_key(const uint8_t *S, int64_t pos, const or_pattern *p)
+{
+    uint32_t k = 0;
+    for (int i = 0; i < p->weight; i++)
+        k = (k << 2) | S[pos + p->care[i]];
+    return k;
+}
+
+/* First index in the sorted table whose key is >= k. */
+static int64_t lower_key(const or_entry *tab, int64_t n, uint32_t k)
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (tab[mid].key < k)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+typedef struct {
+    int64_t t, q;
+} or_tq;
+
+typedef struct {
+    or_tq *v;
+    int64_t n, cap;
+} tq_vec;
+
+static int tq_push(tq_vec *a, int64_t t, int64_t q)
+{
+    if (a->n == a->cap) {
+        int64_t nc = a->cap ? a->cap * 2 : 1024;
+        or_tq *nv = (or_tq *)realloc(a->v, (size_t)nc * sizeof(or_tq));
+        if (!nv)
+            return OR_ENOMEM;
+        a->v = nv;
+        a->cap = nc;
+    }
+    a->v[a->n].t = t;
+    a->v[a->n].q = q;
+    a->n++;
+    return OR_OK;
+}
+
+static int cmp_diag_t(const void *a, const void *b)
+{
+    const or_tq *x = (const or_tq *)a, *y = (const or_tq *)b;
+    int64_t dx = x->t - x->q, dy = y->t - y->q;
+    if (dx != dy)
+        return dx < dy ? -1 : 1;
+    return (x->t > y->t) - (x->t < y->t);
+}
+
+/* Every hit of one strand, sorted by (diagonal t-q, t). */
+static int enumerate_hits(const uint8_t *T, int64_t tlen, const uint8_t *Qs, int64_t qlen,
+                          const or_pattern *p, int transition, tq_vec *out)
+{
+    out->v = NULL;
+    out->n = out->cap = 0;
+    if (tlen < p->span || qlen < p->span)
+        return OR_OK;
+    int64_t nt = tlen - p->span + 1;
+    or_entry *tab = (or_entry *)malloc((size_t)nt * sizeof(or_entry));
+    if (!tab)
+        return OR_ENOMEM;
+    for (int64_t t = 0; t < nt; t++) {
+        tab[t].key = seed_key(T, t, p);
+        tab[t].pos = t;
+    }
+    qsort(tab, (size_t)nt, sizeof(or_entry), cmp_entry);
+    int nprobe = transition ? 1 + p->weight : 1;
+    for (int64_t q = 0; q + p->span <= qlen; q++) {
+        uint32_t k = seed_key(Qs, q, p);
+        for (int j = 0; j < nprobe; j++) {
+            uint32_t pk = j == 0 ? k : k ^ (2u << (2 * (p->weight - j)));
+            for (int64_t i = lower_key(tab, nt, pk); i < nt && tab[i].key == pk; i++) {
+                if (tq_push(out, tab[i].pos, q)) {
+                    free(tab);
+                    return OR_ENOMEM;
+                }
+            }
+        }
+    }
+    free(tab);
+    qsort(out->v, (size_t)out->n, sizeof(or_tq), cmp_diag_t);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------ extension */
+
+void or_xdrop(const uint8_t *T, int64_t tlen, const uint8_t *Qs, int64_t qlen, int64_t t,
+              int64_t q, int span, const int32_t *M, int32_t X, or_ext *e)
+{
+    int64_t s0 = 0;
+    for (int k = 0; k < span; k++)
+        s0 += M[T[t + k] * 4 + Qs[q + k]];
+
+    int64_t sum = 0, best = 0, bestlen = 0, n = 0;
+    while (t + span + n < tlen && q + span + n < qlen) {
+        sum += M[T[t + span + n] * 4 + Qs[q + span + n]];
+        n++;
+        if (sum > best) {
+            best = sum;
+            bestlen = n;
+        }
+        if (best - sum > X)
+            break;
+    }
+    int64_t rbest = best;
+    e->rext = (int32_t)bestlen;
+    e->rscored = (int32_t)n;
+
+    sum = best = bestlen = n = 0;
+    while (t - 1 - n >= 0 && q - 1 - n >= 0) {
+        sum += M[T[t - 1 - n] * 4 + Qs[q - 1 - n]];
+        n++;
+        if (sum > best) {
+            best = sum;
+            bestlen = n;
+        }
+        if (best - sum > X)
+            break;
+    }
+    e->lext = (int32_t)bestlen;
+    e->lscored = (int32_t)n;
+    e->score = s0 + rbest + best;
+    e->t = (int32_t)t;
+    e->q = (int32_t)q;
+}
+
+/* ------------------------------------------------------------- results */
+
+typedef struct {
+    or_hsp *hsp;
+    int64_t n, cap;
+    or_ext *ext; /* optional log of every extension, in processing order */
+    int64_t next, extcap;
+    int keep_log;
+    or_stats st;
+} or_result;
+
+static int push_hsp(or_result *r, const or_hsp *h)
+{
+    if (r->n == r->cap) {
+        int64_t nc = r->cap ? r->cap * 2 : 256;
+        or_hsp *nv = (or_hsp *)realloc(r->hsp, (size_t)nc * sizeof(or_hsp));
+        if (!nv)
+            return OR_ENOMEM;
+        r->hsp = nv;
+        r->cap = nc;
+    }
+    r->hsp[r->n++] = *h;
+    return OR_OK;
+}
+
+static int push_ext(or_result *r, const or_ext *e)
+{
+    if (r->next == r->extcap) {
+        int64_t nc = r->extcap ? r->extcap * 2 : 1024;
+        or_ext *nv = (or_ext *)realloc(r->ext, (size_t)nc * sizeof(or_ext));
+        if (!nv)
+            return OR_ENOMEM;
+        r->ext = nv;
+        r->extcap = nc;
+    }
+    r->ext[r->next++] = *e;
+    return OR_OK;
+}
+
+static int cmp_hsp(const void *a, const void *b)
+{
+    const or_hsp *x = (const or_hsp *)a, *y = (const or_hsp *)b;
+    if (x->strand != y->strand) return x->strand < y->strand ? -1 : 1;
+    if (x->tpos != y->tpos) return x->tpos < y->tpos ? -1 : 1;
+    if (x->qpos != y->qpos) return x->qpos < y->qpos ? -1 : 1;
+    if (x->len != y->len) return x->len < y->len ? -1 : 1;
+    if (x->score != y->score) return x->score < y->score ? -1 : 1;
+    return 0;
+}
+
+/*
+ * The serial walk over one strand's hits, already grouped by diagonal and
+ * ordered by t (Algorithm 1 with X-drop as the extension, restricted to one
+ * diagonal's masking state).
+ */
+static int walk(const uint8_t *T, int64_t tlen, const uint8_t *Qs, int64_t qlen, int strand,
+                const tq_vec *h, const or_pattern *p, const int32_t *M, int32_t X,
+                int32_t thresh, int flags, or_result *r)
+{
+    int64_t i = 0;
+    while (i < h->n) {
+        int64_t d = h->v[i].t - h->v[i].q;
+        int64_t E = INT64_MIN;
+        for (; i < h->n && h->v[i].t - h->v[i].q == d; i++) {
+            int64_t t = h->v[i].t, q = h->v[i].q;
+            r->st.hits++;
+            if (t < E)
+                continue; /* inside an HSP already extended on this diagonal */
+            or_ext e;
+            or_xdrop(T, tlen, Qs, qlen, t, q, p->span, M, X, &e);
+            e.strand = strand;
+            r->st.extended++;
+            r->st.cells += p->span + e.lscored + e.rscored;
+            int pass = e.score >= thresh;
+            if (pass || !(flags & OR_SKIP_PASSING_ONLY))
+                E = t + p->span + e.rext;
+            if (r->keep_log && push_ext(r, &e))
+                return OR_ENOMEM;
+            if (pass) {
+                or_hsp o;
+                o.strand = strand;
+                o.tpos = (int32_t)(t - e.lext);
+                o.qpos = (int32_t)(q - e.lext);
+                o.len = p->span + e.lext + e.rext;
+                o.score = (int32_t)e.score;
+                r->st.hsps++;
+                if (push_hsp(r, &o))
+                    return OR_ENOMEM;
+            }
+        }
+    }
+    return OR_OK;
+}
+
+/*
+ * Full filter stage for one target/query pair. strands: bit 0 = plus strand,
+ * bit 1 = minus strand. Returns a result handle (NULL on error, with *err set).
+ */
+or_result *or_run(const uint8_t *T, int64_t tlen, const uint8_t *Q, int64_t qlen,
+                  const char *pattern, int transition, int strands, const int32_t *M,
+                  int32_t X, int32_t thresh, int flags, int keep_log, int *err)
+{
+    or_pattern p;
+    *err = OR_OK;
+    if (or_parse_pattern(pattern, &p) || X < 0 || tlen < 0 || qlen < 0) {
+        *err = OR_EINVAL;
+        return NULL;
+    }
+    or_result *r = (or_result *)calloc(1, sizeof(or_result));
+    if (!r) {
+        *err = OR_ENOMEM;
+        return NULL;
+    }
+    r->keep_log = keep_log;
+    uint8_t *rc = NULL;
+    for (int s = 0; s < 2; s++) {
+        if (!(strands & (1 << s)))
+            continue;
+        const uint8_t *Qs = Q;
+        if (s == 1) {
+            rc = (uint8_t *)malloc((size_t)(qlen > 0 ? qlen : 1));
+            if (!rc) {
+                *err = OR_ENOMEM;
+                break;
+            }
+            or_revcomp(Q, qlen, rc);
+            Qs = rc;
+        }
+        tq_vec h;
+        int e = enumerate_hits(T, tlen, Qs, qlen, &p, transition, &h);
+        if (!e)
+            e = walk(T, tlen, Qs, qlen, s, &h, &p, M, X, thresh, flags, r);
+        free(h.v);
+        if (e) {
+            *err = e;
+            break;
+        }
+    }
+    free(rc);
+    if (*err) {
+        free(r->hsp);
+        free(r->ext);
+        free(r);
+        return NULL;
+    }
+    qsort(r->hsp, (size_t)r->n, sizeof(or_hsp), cmp_hsp);
+    return r;
+}
+
+/*
+ * The same walk restricted to one diagonal d = t - q of one strand (Qs given
+ * directly), with hits found by testing every position of the diagonal with
+ * the predicate. E0 is the skip state the diagonal starts with. Used for
+ * sampled checks on inputs too large for or_run.
+ */
+or_result *or_run_diagonal(const uint8_t *T, int64_t tlen, const uint8_t *Qs, int64_t qlen,
+                           int strand, int64_t d, int64_t E0, const char *pattern,
+                           int transition, const int32_t *M, int32_t X, int32_t thresh,
+                           int flags, int keep_log, int *err)
+{
+    or_pattern p;
+    *err = OR_OK;
+    if (or_parse_pattern(pattern, &p) || X < 0) {
+        *err = OR_EINVAL;
+        return NULL;
+    }
+    or_result *r = (or_result *)calloc(1, sizeof(or_result));
+    if (!r) {
+        *err = OR_ENOMEM;
+        return NULL;
+    }
+    r->keep_log = keep_log;
+    int64_t E = E0;
+    int64_t t0 = d > 0 ? d : 0;
+    for (int64_t t = t0; t + p.span <= tlen && t - d + p.span <= qlen; t++) {
+        int64_t q = t - d;
+        if (!or_is_hit(T, Qs, t, q, &p, transition))
+            continue;
+        r->st.hits++;
+        if (t < E)
+            continue;
+        or_ext e;
+        or_xdrop(T, tlen, Qs, qlen, t, q, p.span, M, X, &e);
+        e.strand = strand;
+        r->st.extended++;
+        r->st.cells += p.span + e.lscored + e.rscored;
+        int pass = e.score >= thresh;
+        if (pass || !(flags & OR_SKIP_PASSING_ONLY))
+            E = t + p.span + e.rext;
+        if (keep_log && push_ext(r, &e)) {
+            *err = OR_ENOMEM;
+            break;
+        }
+        if (pass) {
+            or_hsp o = {strand, (int32_t)(t - e.lext), (int32_t)(q - e.lext),
+                        p.span + e.lext + e.rext, (int32_t)e.score};
+            r->st.hsps++;
+            if (push_hsp(r, &o)) {
+                *err = OR_ENOMEM;
+                break;
+            }
+        }
+    }
+    if (*err) {
+        free(r->hsp);
+        free(r->ext);
+        free(r);
+        return NULL;
+    }
+    qsort(r->hsp, (size_t)r->n, sizeof(or_hsp), cmp_hsp);
+    return r;
+}
+
+/* Seed hits of one strand, sorted by (diagonal, t): writes up to cap pairs. */
+int64_t or_seed_hits(const uint8_t *T, int64_t tlen, const uint8_t *Qs, int64_t qlen,
+                     const char *pattern, int transition, int64_t *t_out, int64_t *q_out,
+                     int64_t cap, int *err)
+{
+    or_pattern p;
+    *err = OR_OK;
+    if (or_parse_pattern(pattern, &p)) {
+        *err = OR_EINVAL;
+        return -1;
+    }
+    tq_vec h;
+    int e = enumerate_hits(T, tlen, Qs, qlen, &p, transition, &h);
+    if (e) {
+        *err = e;
+        return -1;
+    }
+    for (int64_t i = 0; i < h.n && i < cap; i++) {
+        t_out[i] = h.v[i].t;
+        q_out[i] = h.v[i].q;
+    }
+    int64_t n = h.n;
+    free(h.v);
+    return n;
+}
+
+int64_t or_result_count(const or_result *r) { return r->n; }
+int64_t or_result_ext_count(const or_result *r) { return r->next; }
+void or_result_stats(const or_result *r, or_stats *st) { *st = r->st; }
+void or_result_copy(const or_result *r, or_hsp *out)
+{
+    if (r->n)
+        memcpy(out, r->hsp, (size_t)r->n * sizeof(or_hsp));
+}
+void or_result_copy_ext(const or_result *r, or_ext *out)
+{
+    if (r->next)
+        memcpy(out, r->ext, (size_t)r->next * sizeof(or_ext));
+}
+void or_result_free(or_result *r)
+{
+    if (!r)
+        return;
+    free(r->hsp);
+    free(r->ext);
+    free(r);
+}
