@@ -1,0 +1,172 @@
+/*
+ * sfe.h - C ABI of the GB300 seed-filter-extend filter stage.
+ *
+ * The library computes the filter stage of the seed-filter-extend pipeline
+ * (Section 1 of "Dependencies and Dataflow in Seed-Filter-Extend Pipelines"):
+ * spaced-seed hits between a target T and both strands of a query Q
+ * (12-of-19 seed 1110100110010101111 with transition tolerance, Section 2 and
+ * Section 7), the loop-carried skip of hits that fall inside a region already
+ * extended on their diagonal (Algorithm 1, the IsContained test and the
+ * masking-list update), and the ungapped X-drop extension that turns the
+ * surviving hits into HSPs (Section 2 and Section 8: a 1-D dynamic program
+ * with no gaps). Every step runs in hand-written CUDA kernels for sm_103a.
+ *
+ * Conventions shared by every call:
+ *  - Bases: ASCII A/C/G/T (either case), or 2-bit codes A=0 C=1 G=2 T=3 one per
+ *    byte when sfe_params.input_codes = 1. Any other symbol gives SFE_EINVAL.
+ *  - Coordinates are 0-based, half-open. Strand 0 is the query as given;
+ *    strand 1 is its reverse complement and its coordinates index the reverse
+ *    complement (qpos 0 is the complement of the last query base).
+ *  - A hit (strand, tpos, qpos) means the seed pattern matches at T[tpos..] and
+ *    Q_strand[qpos..]. Its diagonal is tpos - qpos.
+ *  - The X-drop rule: each side extends base by base; it stops right after the
+ *    first base at which (running maximum - running sum) > X, or at the end of
+ *    either sequence; the HSP ends where the maximum was first reached. The HSP
+ *    always holds the whole seed span. Scores are int32 sums of
+ *    scores[4 * target_base + query_base].
+ *  - A hit is skipped when tpos < E, E being the exclusive end of the last
+ *    extended HSP on its (strand, diagonal); E is advanced by every extension
+ *    (or only by those reaching hsp_thresh with SFE_SKIP_PASSING_ONLY).
+ *  - Pointers may be device pointers (from cudaMalloc or a PyTorch CUDA
+ *    tensor) or host pointers (pageable or pinned); the library detects which
+ *    with cudaPointerGetAttributes and copies host data in and out itself.
+ *  - Work is queued on the context's stream. Every call returns after its
+ *    results (counts, stats, host outputs) are complete.
+ *  - Outputs are caller-owned buffers with a capacity; when the result does
+ *    not fit, the call returns SFE_EOVERFLOW and sets the needed count.
+ *  - Scratch memory is owned by the context (grown on demand, reused across
+ *    calls, freed by sfe_ctx_destroy). A context is not thread-safe; use one
+ *    context per host thread.
+ *  - Return codes: SFE_OK (0) or a negative SFE_E* code; sfe_last_error()
+ *    describes the most recent failure of the calling thread.
+ */
+#ifndef SFE_H
+#define SFE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SFE_OK 0
+#define SFE_EINVAL (-1)    /* bad argument or symbol */
+#define SFE_ENOMEM (-2)    /* device allocation failed */
+#define SFE_ECUDA (-3)     /* a CUDA call failed */
+#define SFE_ETIMEOUT (-4)  /* a bounded device wait ran out */
+#define SFE_EOVERFLOW (-5) /* output capacity too small (needed count returned), or a score left int32 */
+
+/* sfe_params.flags */
+#define SFE_SKIP_PASSING_ONLY 1 /* advance E only for HSPs with score >= hsp_thresh */
+
+typedef struct sfe_ctx sfe_ctx;
+typedef struct sfe_index sfe_index;
+
+/* One seed hit. */
+typedef struct {
+    int32_t strand, tpos, qpos;
+} sfe_hit;
+
+/* One HSP (high-scoring ungapped segment); len is the same in T and Q. */
+typedef struct {
+    int32_t strand, tpos, qpos, len, score;
+} sfe_hsp;
+
+/* One HSP of a batch of pairs. */
+typedef struct {
+    int32_t pair, strand, tpos, qpos, len, score;
+} sfe_batch_hsp;
+
+typedef struct {
+    const char *seed_pattern; /* '1' care, '0' don't care; span <= 32, weight <= 14; NULL = 12of19 */
+    int32_t transition;       /* 1: at most one care position may be a transition (A<->G, C<->T) */
+    int32_t strands;          /* bit 0: strand 0 (plus), bit 1: strand 1 (minus) */
+    int32_t scores[16];       /* scores[4 * target_base + query_base] */
+    int32_t xdrop;            /* X >= 0 (and < 2^30) */
+    int32_t hsp_thresh;       /* HSPs with score >= hsp_thresh are reported */
+    int32_t flags;            /* SFE_SKIP_PASSING_ONLY */
+    int32_t input_codes;      /* 0: ASCII ACGTacgt, 1: codes 0..3 */
+    int32_t lane_cap;         /* bases per side a lane extends before handing the diagonal to a warp; 0 = default */
+    int32_t reserved;
+    int64_t tile_hits;        /* hits per query tile (bounds scratch memory); 0 = default */
+} sfe_params;
+
+/* Statistics of one call. cells is the work measure of the method: seed span
+ * plus the bases scored on both sides, summed over hits that were extended. */
+typedef struct {
+    int64_t hits;       /* seed hits enumerated */
+    int64_t extended;   /* hits extended (not skipped) */
+    int64_t cells;      /* span + bases scored, over extended hits */
+    int64_t hsps;       /* HSPs with score >= hsp_thresh */
+    int64_t lane_tasks; /* diagonals walked by single lanes */
+    int64_t warp_tasks; /* diagonals handed to whole warps */
+    int64_t tiles;      /* query tiles processed */
+    int64_t reserved;
+} sfe_stats;
+
+/* Fill *p with the defaults: 12of19 with one transition, both strands,
+ * HOXD70 scores, X = 910, hsp_thresh = 3000. Returns SFE_OK. */
+int sfe_params_default(sfe_params *p);
+
+const char *sfe_strerror(int code);
+const char *sfe_last_error(void);
+
+/* Create a context on CUDA device `device` with its own non-blocking stream. */
+int sfe_ctx_create(int device, sfe_ctx **out);
+/* Queue later work on `stream` (a cudaStream_t, e.g. a PyTorch stream); NULL
+ * restores the context's own stream. The caller keeps the stream alive. */
+int sfe_ctx_set_stream(sfe_ctx *ctx, void *stream);
+void sfe_ctx_destroy(sfe_ctx *ctx);
+
+/*
+ * Seeding index over the target (the "position table" of Section 5):
+ * 2-bit packing, spaced-seed keys at every target position, a stable device
+ * radix sort by key and a CSR table of 4^weight + 1 offsets. target: tlen
+ * bases, host or device. Only seed_pattern, transition and input_codes of
+ * *params are used. The index keeps the packed target; free it with
+ * sfe_index_free. SFE_EINVAL on a bad pattern or symbol.
+ */
+int sfe_index_build(sfe_ctx *ctx, const uint8_t *target, int64_t tlen, const sfe_params *params,
+                    sfe_index **out);
+void sfe_index_free(sfe_index *index);
+
+/*
+ * Seed hits of the query against the index (Section 2 and Section 7), for the
+ * strands in the bit mask `strands`. hits: caller buffer of `cap` records (host
+ * or device), written sorted by (strand, diagonal, tpos). *nhits receives the
+ * number of hits; if it exceeds cap nothing is written and SFE_EOVERFLOW is
+ * returned.
+ */
+int sfe_seed_hits(sfe_ctx *ctx, const sfe_index *index, const uint8_t *query, int64_t qlen,
+                  int32_t strands, sfe_hit *hits, int64_t cap, int64_t *nhits);
+
+/*
+ * Per-diagonal skip and ungapped X-drop over a hit list (Algorithm 1 with the
+ * X-drop filter, Section 2 and Section 8). hits: nhits records in any order
+ * (host or device); each is grouped by (strand, diagonal) and walked in tpos
+ * order. scores: 16 int32 as in sfe_params. hsps: caller buffer of cap
+ * records (host or device), written sorted by (strand, tpos, qpos, len,
+ * score). *nhsps receives the HSP count (SFE_EOVERFLOW if above cap). stats
+ * may be NULL. A hit whose seed span leaves either sequence gives SFE_EINVAL.
+ */
+int sfe_ungapped_xdrop(sfe_ctx *ctx, const sfe_index *index, const uint8_t *query, int64_t qlen,
+                       const sfe_hit *hits, int64_t nhits, const int32_t scores[16], int32_t X,
+                       int32_t hsp_thresh, sfe_hsp *hsps, int64_t cap, int64_t *nhsps,
+                       sfe_stats *stats);
+
+/*
+ * The whole filter stage for one pair: index, hits on the requested strands,
+ * skip and X-drop, sorted HSPs. Inputs and outputs host or device; the query
+ * is processed in tiles of at most params->tile_hits hits with the skip state
+ * carried across tiles, so the result does not depend on the tiling.
+ */
+int sfe_run(sfe_ctx *ctx, const uint8_t *target, int64_t tlen, const uint8_t *query, int64_t qlen,
+            const sfe_params *params, sfe_hsp *hsps, int64_t cap, int64_t *nhsps,
+            sfe_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFE_H */

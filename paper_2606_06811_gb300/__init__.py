@@ -1,0 +1,11 @@
+"""GB300-native filter stage of the seed-filter-extend pipeline.
+
+Spaced-seed hits, the per-diagonal skip and the ungapped X-drop extension,
+computed by hand-written CUDA kernels for sm_103a behind the C ABI of
+include/sfe.h. `sfe` is the Python binding (argument marshalling only);
+`build` compiles the library in-tree.
+"""
+from .sfe import (  # noqa: F401
+    HIT_DTYPE, HSP_DTYPE, SKIP_PASSING_ONLY, Context, Index, Params, SfeError, Stats,
+    default_params, exported_symbols, lib,
+)

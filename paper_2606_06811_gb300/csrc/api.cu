@@ -1,0 +1,778 @@
+// C ABI of libsfe (declared in include/sfe.h): context and scratch arena,
+// host/device staging, and the order of the kernels of the filter stage.
+#include <algorithm>
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sfe_internal.cuh"
+
+using namespace sfe;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CK(x)                                                                              \
+    do {                                                                                   \
+        cudaError_t e_ = (x);                                                              \
+        if (e_ != cudaSuccess) {                                                           \
+            cudaGetLastError();                                                            \
+            return fail(SFE_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_));       \
+        }                                                                                  \
+    } while (0)
+
+#define TRY(x)                   \
+    do {                         \
+        int r_ = (x);            \
+        if (r_ != SFE_OK) return r_; \
+    } while (0)
+
+// HOXD70 (Chiaromonte, Yap and Miller 2002), target base major, order ACGT.
+const int32_t kHoxd70[16] = {91,   -114, -31, -123, -114, 100,  -125, -31,
+                             -31,  -125, 100, -114, -123, -31,  -114, 91};
+const char *kDefaultPattern = "1110100110010101111";
+
+constexpr int kDefaultLaneCap = 96;
+constexpr long long kDefaultTileHits = 1LL << 28;
+constexpr unsigned long long kQueueMax = 1ull << 22;
+
+enum Slot {
+    SL_TIN, SL_QIN, SL_TP, SL_QP, SL_QM, SL_KEYS_A, SL_KEYS_B, SL_BCOUNT, SL_OFFS, SL_POS,
+    SL_COUNTS, SL_STARTS, SL_HITS_A, SL_HITS_B, SL_FLAGS, SL_SEGSCAN, SL_SEGSTART, SL_QUEUE,
+    SL_HSPS, SL_TMP, SL_ECARRY, SL_PUB, SL_BOUNDS, NSLOT
+};
+
+// Small device block: scores, counters and flags of one call.
+struct Small {
+    int32_t scores[16];
+    DevCounters ctr;
+    uint32_t status;       // pack / conversion status
+    uint32_t queue_len;
+    unsigned long long split;
+    unsigned long long pad[4];
+};
+
+int bits_for(long long v) {
+    int b = 1;
+    while (b < 63 && (1LL << b) <= v) b++;
+    return b;
+}
+
+}  // namespace
+
+struct sfe_ctx {
+    int device = 0;
+    cudaStream_t own = nullptr;
+    cudaStream_t st = nullptr;
+    void *buf[NSLOT] = {};
+    size_t cap[NSLOT] = {};
+    Small *small = nullptr;       // device
+    Small *host_small = nullptr;  // pinned mirror
+};
+
+struct sfe_index {
+    int device = 0;
+    long long tlen = 0;
+    SeedPattern pat{};
+    int transition = 1;
+    int codes = 0;                 // input format of the target, reused for queries
+    uint32_t *tp_alloc = nullptr;  // packed target with padding
+    uint32_t *offs = nullptr;      // 4^weight + 1
+    uint32_t *pos = nullptr;       // tlen - span + 1
+};
+
+namespace {
+
+int ensure(sfe_ctx *c, int slot, size_t bytes, void **out) {
+    if (bytes < 256) bytes = 256;
+    if (c->cap[slot] < bytes) {
+        if (c->buf[slot]) {
+            CK(cudaFreeAsync(c->buf[slot], c->st));
+            c->buf[slot] = nullptr;
+            c->cap[slot] = 0;
+        }
+        size_t nb = bytes + bytes / 8;
+        void *p = nullptr;
+        cudaError_t e = cudaMallocAsync(&p, nb, c->st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SFE_ENOMEM, "device allocation of " + std::to_string(nb) + " bytes failed");
+        }
+        c->buf[slot] = p;
+        c->cap[slot] = nb;
+    }
+    *out = c->buf[slot];
+    return SFE_OK;
+}
+
+template <typename T>
+int ensure_t(sfe_ctx *c, int slot, size_t count, T **out) {
+    void *p = nullptr;
+    TRY(ensure(c, slot, count * sizeof(T), &p));
+    *out = reinterpret_cast<T *>(p);
+    return SFE_OK;
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int parse_pattern(const char *s, SeedPattern *p) {
+    if (!s) s = kDefaultPattern;
+    int n = (int)strlen(s);
+    if (n < 1 || n > MAX_SPAN) return fail(SFE_EINVAL, "seed pattern span must be 1..32");
+    memset(p, 0, sizeof(*p));
+    p->span = n;
+    for (int i = 0; i < n; i++) {
+        if (s[i] == '1')
+            p->care[p->weight++] = i;
+        else if (s[i] != '0')
+            return fail(SFE_EINVAL, "seed pattern holds a character other than 0/1");
+    }
+    if (p->weight < 1 || p->weight > MAX_WEIGHT)
+        return fail(SFE_EINVAL, "seed pattern weight must be 1..14");
+    return SFE_OK;
+}
+
+int check_params(const sfe_params *p) {
+    if (!p) return fail(SFE_EINVAL, "params is NULL");
+    if (p->xdrop < 0 || p->xdrop >= (1 << 30)) return fail(SFE_EINVAL, "xdrop must be in [0, 2^30)");
+    if (p->strands < 1 || p->strands > 3) return fail(SFE_EINVAL, "strands must be 1, 2 or 3");
+    if (p->lane_cap < 0) return fail(SFE_EINVAL, "lane_cap must be >= 0");
+    if (p->tile_hits < 0) return fail(SFE_EINVAL, "tile_hits must be >= 0");
+    if (p->input_codes != 0 && p->input_codes != 1) return fail(SFE_EINVAL, "input_codes must be 0 or 1");
+    for (int i = 0; i < 16; i++)
+        if (p->scores[i] < -(1 << 20) || p->scores[i] > (1 << 20))
+            return fail(SFE_EINVAL, "scores must lie in [-2^20, 2^20]");
+    return SFE_OK;
+}
+
+int check_len(long long n, const char *what) {
+    if (n < 0 || n > (long long)INT_MAX - 1024)
+        return fail(SFE_EINVAL, std::string(what) + " length must be in [0, 2^31 - 1024]");
+    return SFE_OK;
+}
+
+int begin(sfe_ctx *c) {
+    if (!c) return fail(SFE_EINVAL, "context is NULL");
+    CK(cudaSetDevice(c->device));
+    CK(cudaMemsetAsync(c->small, 0, sizeof(Small), c->st));
+    return SFE_OK;
+}
+
+// Bytes in (host or device) -> device pointer (host data copied to `slot`).
+int stage(sfe_ctx *c, int slot, const void *src, size_t bytes, const void **dev) {
+    if (bytes == 0 || is_device_ptr(src)) {
+        *dev = src;
+        return SFE_OK;
+    }
+    if (!src) return fail(SFE_EINVAL, "input pointer is NULL");
+    void *d = nullptr;
+    TRY(ensure(c, slot, bytes, &d));
+    CK(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, c->st));
+    *dev = d;
+    return SFE_OK;
+}
+
+size_t packed_words(long long n) { return (size_t)((n + 15) / 16) + 2 * SEQ_PAD; }
+
+// Pack `n` bases from `src` (device) into a padded buffer; returns base-0 pointer.
+int pack_into(sfe_ctx *c, const uint8_t *src, long long n, int codes, uint32_t *alloc,
+              uint32_t **base0) {
+    *base0 = alloc + SEQ_PAD;
+    CK(launch_pack(src, n, codes, *base0, &c->small->status, c->st));
+    return SFE_OK;
+}
+
+int pack_slot(sfe_ctx *c, int slot, const uint8_t *src, long long n, int codes, uint32_t **base0) {
+    uint32_t *a = nullptr;
+    TRY(ensure_t(c, slot, packed_words(n), &a));
+    return pack_into(c, src, n, codes, a, base0);
+}
+
+int rc_slot(sfe_ctx *c, int slot, const uint32_t *fwd, long long n, uint32_t **base0) {
+    uint32_t *a = nullptr;
+    TRY(ensure_t(c, slot, packed_words(n), &a));
+    *base0 = a + SEQ_PAD;
+    CK(launch_revcomp(fwd, n, *base0, c->st));
+    return SFE_OK;
+}
+
+int sync_small(sfe_ctx *c) {
+    CK(cudaMemcpyAsync(c->host_small, c->small, sizeof(Small), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return SFE_OK;
+}
+
+int check_status(uint32_t st) {
+    if (st & ST_BAD_SYMBOL) return fail(SFE_EINVAL, "sequence holds a symbol outside ACGTacgt");
+    if (st & ST_BAD_HIT) return fail(SFE_EINVAL, "a hit's seed span leaves the sequences");
+    if (st & ST_SCORE_OVERFLOW) return fail(SFE_EOVERFLOW, "an HSP score left the int32 range");
+    return SFE_OK;
+}
+
+struct IndexView {
+    const uint32_t *T;
+    long long tlen;
+    SeedPattern pat;
+    int transition;
+    const uint32_t *offs;
+    const uint32_t *pos;
+};
+
+// Spaced keys -> stable radix sort -> CSR (offsets, positions).
+int build_index(sfe_ctx *c, const uint32_t *T, long long tlen, const SeedPattern &pat,
+                uint32_t *offs, uint32_t *pos) {
+    const long long npos = std::max(0LL, tlen - pat.span + 1);
+    const long long nbuckets = 1LL << (2 * pat.weight);
+    uint32_t *counts = nullptr;
+    TRY(ensure_t(c, SL_BCOUNT, (size_t)nbuckets, &counts));
+    CK(cudaMemsetAsync(counts, 0, (size_t)nbuckets * 4, c->st));
+    void *tmp = nullptr;
+    TRY(ensure(c, SL_TMP, std::max(radix_sort_temp_bytes(npos), scan_temp_bytes(nbuckets)), &tmp));
+    if (npos > 0) {
+        uint64_t *ka = nullptr, *kb = nullptr;
+        TRY(ensure_t(c, SL_KEYS_A, (size_t)npos, &ka));
+        TRY(ensure_t(c, SL_KEYS_B, (size_t)npos, &kb));
+        CK(launch_seed_keys(T, tlen, pat, ka, c->st));
+        bool in_b = false;
+        CK(radix_sort(ka, kb, nullptr, nullptr, npos, 32, 32 + 2 * pat.weight, tmp, &in_b, c->st));
+        CK(launch_csr_counts(in_b ? kb : ka, npos, counts, pos, c->st));
+    }
+    CK(scan_u32_to_u32(counts, offs, nbuckets, tmp, c->st));
+    return SFE_OK;
+}
+
+// Count pass + exclusive scan of one strand; returns the total on the host.
+int count_hits(sfe_ctx *c, const IndexView &ix, const uint32_t *Qs, long long qlen,
+               unsigned long long **starts_out, long long *nq_out, unsigned long long *total) {
+    *total = 0;
+    const long long nq = qlen - ix.pat.span + 1;
+    *nq_out = nq;
+    if (nq <= 0 || ix.tlen < ix.pat.span) {
+        *nq_out = 0;
+        return SFE_OK;
+    }
+    HitParams hp;
+    hp.pat = ix.pat;
+    hp.transition = ix.transition;
+    hp.qlen = qlen;
+    hp.qoff = qlen - ix.pat.span;
+    uint32_t *counts = nullptr;
+    unsigned long long *starts = nullptr;
+    void *tmp = nullptr;
+    TRY(ensure_t(c, SL_COUNTS, (size_t)nq, &counts));
+    TRY(ensure_t(c, SL_STARTS, (size_t)nq + 1, &starts));
+    TRY(ensure(c, SL_TMP, scan_temp_bytes(nq), &tmp));
+    CK(launch_hit_count(Qs, hp, ix.offs, 0, nq, counts, c->st));
+    CK(scan_u32_to_u64(counts, starts, nq, tmp, c->st));
+    CK(cudaMemcpyAsync(total, starts + nq, 8, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    *starts_out = starts;
+    return SFE_OK;
+}
+
+__global__ void tile_bounds_kernel(const unsigned long long *starts, long long nq,
+                                   unsigned long long per, long long ntiles, long long *bounds,
+                                   unsigned long long *bstarts) {
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k > ntiles) return;
+    long long b;
+    if (k == 0) {
+        b = 0;
+    } else if (k == ntiles) {
+        b = nq;
+    } else {
+        unsigned long long target = per * (unsigned long long)k;
+        long long lo = 0, hi = nq;  // first q with starts[q] >= target
+        while (lo < hi) {
+            long long mid = (lo + hi) / 2;
+            if (starts[mid] < target)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        b = lo;
+    }
+    bounds[k] = b;
+    bstarts[k] = starts[b];
+}
+
+__global__ void strand_split_kernel(const uint64_t *keys, long long n, unsigned long long *split) {
+    long long lo = 0, hi = n;  // first index with bit 63 set
+    while (lo < hi) {
+        long long mid = (lo + hi) / 2;
+        if ((keys[mid] >> 63) == 0)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    *split = (unsigned long long)lo;
+}
+
+struct WalkSetup {
+    const uint32_t *T;
+    long long tlen;
+    const uint32_t *Qs;
+    long long qlen;
+    int strand;
+    int span;
+    const sfe_params *p;
+    int32_t *Ecarry;
+    Hsp *hsps;
+    unsigned long long hsp_cap;
+};
+
+// Segments of hits sorted by (diagonal, t), then the lane and warp walks.
+int walk_sorted(sfe_ctx *c, const uint64_t *hits, long long n, const WalkSetup &ws) {
+    if (n <= 0) return SFE_OK;
+    uint32_t *flags = nullptr, *seg_start = nullptr;
+    unsigned long long *segscan = nullptr;
+    uint4 *queue = nullptr;
+    void *tmp = nullptr;
+    TRY(ensure_t(c, SL_FLAGS, (size_t)n, &flags));
+    TRY(ensure_t(c, SL_SEGSCAN, (size_t)n + 1, &segscan));
+    TRY(ensure_t(c, SL_SEGSTART, (size_t)n + 1, &seg_start));
+    const unsigned long long qcap = std::min<unsigned long long>((unsigned long long)n, kQueueMax);
+    TRY(ensure_t(c, SL_QUEUE, (size_t)qcap, &queue));
+    TRY(ensure(c, SL_TMP, segments_temp_bytes(n), &tmp));
+    CK(launch_segments(hits, n, flags, segscan, seg_start, tmp, c->st));
+    CK(cudaMemsetAsync(&c->small->queue_len, 0, 4, c->st));
+    WalkParams wp;
+    wp.T = ws.T;
+    wp.Q = ws.Qs;
+    wp.tlen = ws.tlen;
+    wp.qlen = ws.qlen;
+    wp.span = ws.span;
+    wp.strand = ws.strand;
+    wp.xdrop = ws.p->xdrop;
+    wp.thresh = ws.p->hsp_thresh;
+    wp.flags = ws.p->flags;
+    wp.lane_cap = ws.p->lane_cap > 0 ? ws.p->lane_cap : kDefaultLaneCap;
+    wp.qoff = ws.qlen - ws.span;
+    wp.scores = c->small->scores;
+    wp.Ecarry = ws.Ecarry;
+    wp.hsps = ws.hsps;
+    wp.hsp_cap = ws.hsp_cap;
+    wp.ctr = &c->small->ctr;
+    wp.queue = queue;
+    wp.queue_cap = qcap;
+    wp.queue_len = &c->small->queue_len;
+    CK(launch_walk_lanes(hits, seg_start, segscan + n, n, wp, c->st));
+    CK(launch_walk_warps(hits, seg_start, wp, 0, c->st));
+    return SFE_OK;
+}
+
+// Sort the HSPs found and copy them out; sets *nhsps (SFE_EOVERFLOW if > cap).
+int finish_hsps(sfe_ctx *c, Hsp *dev, unsigned long long found, long long tlen, long long qlen,
+                sfe_hsp *out, int64_t cap, int64_t *nhsps) {
+    *nhsps = (int64_t)found;
+    if ((long long)found > cap) return fail(SFE_EOVERFLOW, "HSP buffer too small");
+    if (found == 0) return SFE_OK;
+    void *tmp = nullptr;
+    TRY(ensure(c, SL_TMP, hsp_sort_temp_bytes((long long)found), &tmp));
+    CK(hsp_sort(dev, (long long)found, bits_for(tlen), bits_for(qlen), tmp, c->st));
+    const bool dev_out = is_device_ptr(out);
+    CK(cudaMemcpyAsync(out, dev, found * sizeof(Hsp),
+                       dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return SFE_OK;
+}
+
+void fill_stats(const Small &s, sfe_stats *st, long long hits, long long tiles) {
+    if (!st) return;
+    memset(st, 0, sizeof(*st));
+    st->hits = hits;
+    st->extended = (int64_t)s.ctr.extended;
+    st->cells = (int64_t)s.ctr.cells;
+    st->hsps = (int64_t)s.ctr.hsps;
+    st->lane_tasks = (int64_t)s.ctr.lane_tasks;
+    st->warp_tasks = (int64_t)s.ctr.warp_tasks;
+    st->tiles = tiles;
+}
+
+int upload_scores(sfe_ctx *c, const int32_t *scores) {
+    CK(cudaMemcpyAsync(c->small->scores, scores, 64, cudaMemcpyHostToDevice, c->st));
+    return SFE_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+int sfe_params_default(sfe_params *p) {
+    if (!p) return fail(SFE_EINVAL, "params is NULL");
+    memset(p, 0, sizeof(*p));
+    p->seed_pattern = kDefaultPattern;
+    p->transition = 1;
+    p->strands = 3;
+    memcpy(p->scores, kHoxd70, sizeof(kHoxd70));
+    p->xdrop = 910;
+    p->hsp_thresh = 3000;
+    return SFE_OK;
+}
+
+const char *sfe_strerror(int code) {
+    switch (code) {
+    case SFE_OK: return "ok";
+    case SFE_EINVAL: return "invalid argument";
+    case SFE_ENOMEM: return "out of device memory";
+    case SFE_ECUDA: return "CUDA error";
+    case SFE_ETIMEOUT: return "bounded device wait ran out";
+    case SFE_EOVERFLOW: return "output capacity or int32 range exceeded";
+    default: return "unknown error";
+    }
+}
+
+const char *sfe_last_error(void) { return g_err.c_str(); }
+
+int sfe_ctx_create(int device, sfe_ctx **out) {
+    if (!out) return fail(SFE_EINVAL, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(SFE_EINVAL, "no such CUDA device");
+    CK(cudaSetDevice(device));
+    sfe_ctx *c = new sfe_ctx();
+    c->device = device;
+    cudaError_t e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&c->small, sizeof(Small));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->host_small, sizeof(Small));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (c->small) cudaFree(c->small);
+        if (c->own) cudaStreamDestroy(c->own);
+        delete c;
+        return fail(SFE_ECUDA, std::string("context setup: ") + cudaGetErrorString(e));
+    }
+    c->st = c->own;
+    *out = c;
+    return SFE_OK;
+}
+
+int sfe_ctx_set_stream(sfe_ctx *c, void *stream) {
+    if (!c) return fail(SFE_EINVAL, "context is NULL");
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->st));
+    c->st = stream ? reinterpret_cast<cudaStream_t>(stream) : c->own;
+    return SFE_OK;
+}
+
+void sfe_ctx_destroy(sfe_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->st);
+    for (int i = 0; i < NSLOT; i++)
+        if (c->buf[i]) cudaFreeAsync(c->buf[i], c->st);
+    cudaStreamSynchronize(c->st);
+    if (c->small) cudaFree(c->small);
+    if (c->host_small) cudaFreeHost(c->host_small);
+    if (c->own) cudaStreamDestroy(c->own);
+    delete c;
+}
+
+int sfe_index_build(sfe_ctx *c, const uint8_t *target, int64_t tlen, const sfe_params *params,
+                    sfe_index **out) {
+    if (!out) return fail(SFE_EINVAL, "out is NULL");
+    *out = nullptr;
+    TRY(check_len(tlen, "target"));
+    SeedPattern pat;
+    TRY(parse_pattern(params ? params->seed_pattern : nullptr, &pat));
+    const int codes = params ? params->input_codes : 0;
+    TRY(begin(c));
+    const void *tdev = nullptr;
+    TRY(stage(c, SL_TIN, target, (size_t)tlen, &tdev));
+    sfe_index *ix = new sfe_index();
+    ix->device = c->device;
+    ix->tlen = tlen;
+    ix->pat = pat;
+    ix->transition = params ? params->transition : 1;
+    ix->codes = codes;
+    const long long npos = std::max(0LL, (long long)tlen - pat.span + 1);
+    const long long nbuckets = 1LL << (2 * pat.weight);
+    cudaError_t e = cudaMalloc(&ix->tp_alloc, packed_words(tlen) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&ix->offs, (size_t)(nbuckets + 1) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&ix->pos, (size_t)std::max(1LL, npos) * 4);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        sfe_index_free(ix);
+        return fail(SFE_ENOMEM, "index allocation failed");
+    }
+    uint32_t *T = nullptr;
+    int r = pack_into(c, reinterpret_cast<const uint8_t *>(tdev), tlen, codes, ix->tp_alloc, &T);
+    if (r == SFE_OK) r = build_index(c, T, tlen, pat, ix->offs, ix->pos);
+    if (r == SFE_OK) r = sync_small(c);
+    if (r == SFE_OK) r = check_status(c->host_small->status);
+    if (r != SFE_OK) {
+        sfe_index_free(ix);
+        return r;
+    }
+    *out = ix;
+    return SFE_OK;
+}
+
+void sfe_index_free(sfe_index *ix) {
+    if (!ix) return;
+    cudaSetDevice(ix->device);
+    if (ix->tp_alloc) cudaFree(ix->tp_alloc);
+    if (ix->offs) cudaFree(ix->offs);
+    if (ix->pos) cudaFree(ix->pos);
+    delete ix;
+}
+
+static IndexView view_of(const sfe_index *ix) {
+    IndexView v;
+    v.T = ix->tp_alloc + SEQ_PAD;
+    v.tlen = ix->tlen;
+    v.pat = ix->pat;
+    v.transition = ix->transition;
+    v.offs = ix->offs;
+    v.pos = ix->pos;
+    return v;
+}
+
+int sfe_seed_hits(sfe_ctx *c, const sfe_index *ix, const uint8_t *query, int64_t qlen,
+                  int32_t strands, sfe_hit *hits, int64_t cap, int64_t *nhits) {
+    if (!ix || !nhits) return fail(SFE_EINVAL, "index or nhits is NULL");
+    if (strands < 1 || strands > 3) return fail(SFE_EINVAL, "strands must be 1, 2 or 3");
+    TRY(check_len(qlen, "query"));
+    TRY(begin(c));
+    const IndexView v = view_of(ix);
+    const void *qdev = nullptr;
+    TRY(stage(c, SL_QIN, query, (size_t)qlen, &qdev));
+    uint32_t *Qp = nullptr, *Qm = nullptr;
+    TRY(pack_slot(c, SL_QP, reinterpret_cast<const uint8_t *>(qdev), qlen, ix->codes, &Qp));
+    TRY(rc_slot(c, SL_QM, Qp, qlen, &Qm));
+    TRY(sync_small(c));
+    TRY(check_status(c->host_small->status));
+    unsigned long long tot[2] = {0, 0};
+    long long nq = 0;
+    for (int s = 0; s < 2; s++) {
+        if (!(strands & (1 << s))) continue;
+        unsigned long long *starts = nullptr;
+        TRY(count_hits(c, v, s ? Qm : Qp, qlen, &starts, &nq, &tot[s]));
+    }
+    const unsigned long long need = tot[0] + tot[1];
+    *nhits = (int64_t)need;
+    if ((long long)need > cap) return fail(SFE_EOVERFLOW, "hit buffer too small");
+    if (need == 0) return SFE_OK;
+    const bool dev_out = is_device_ptr(hits);
+    sfe_hit *dst = hits;
+    if (!dev_out) TRY(ensure_t(c, SL_PUB, (size_t)need, &dst));
+    unsigned long long at = 0;
+    const int DB = bits_for(ix->tlen + qlen - 2LL * v.pat.span);
+    for (int s = 0; s < 2; s++) {
+        if (!(strands & (1 << s)) || tot[s] == 0) continue;
+        unsigned long long *starts = nullptr;
+        unsigned long long t2 = 0;
+        TRY(count_hits(c, v, s ? Qm : Qp, qlen, &starts, &nq, &t2));
+        uint64_t *ha = nullptr, *hb = nullptr;
+        void *tmp = nullptr;
+        TRY(ensure_t(c, SL_HITS_A, (size_t)t2, &ha));
+        TRY(ensure_t(c, SL_HITS_B, (size_t)t2, &hb));
+        TRY(ensure(c, SL_TMP, radix_sort_temp_bytes((long long)t2), &tmp));
+        HitParams hp;
+        hp.pat = v.pat;
+        hp.transition = v.transition;
+        hp.qlen = qlen;
+        hp.qoff = qlen - v.pat.span;
+        CK(launch_hit_write(s ? Qm : Qp, hp, v.offs, v.pos, 0, nq, starts, 0, ha, c->st));
+        bool in_b = false;
+        CK(radix_sort(ha, hb, nullptr, nullptr, (long long)t2, 32, 32 + DB, tmp, &in_b, c->st));
+        CK(launch_hits_to_public(in_b ? hb : ha, (long long)t2, s, hp.qoff, dst + at, c->st));
+        at += t2;
+    }
+    if (!dev_out)
+        CK(cudaMemcpyAsync(hits, dst, need * sizeof(sfe_hit), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return SFE_OK;
+}
+
+int sfe_ungapped_xdrop(sfe_ctx *c, const sfe_index *ix, const uint8_t *query, int64_t qlen,
+                       const sfe_hit *hits, int64_t nhits, const int32_t scores[16], int32_t X,
+                       int32_t hsp_thresh, sfe_hsp *hsps, int64_t cap, int64_t *nhsps,
+                       sfe_stats *stats) {
+    if (!ix || !nhsps || !scores) return fail(SFE_EINVAL, "index, scores or nhsps is NULL");
+    if (nhits < 0 || nhits >= (1LL << 32)) return fail(SFE_EINVAL, "nhits out of range");
+    TRY(check_len(qlen, "query"));
+    sfe_params p;
+    sfe_params_default(&p);
+    memcpy(p.scores, scores, 64);
+    p.xdrop = X;
+    p.hsp_thresh = hsp_thresh;
+    TRY(check_params(&p));
+    TRY(begin(c));
+    const IndexView v = view_of(ix);
+    const int span = v.pat.span;
+    TRY(upload_scores(c, p.scores));
+    const void *qdev = nullptr, *hdev = nullptr;
+    TRY(stage(c, SL_QIN, query, (size_t)qlen, &qdev));
+    TRY(stage(c, SL_PUB, hits, (size_t)nhits * sizeof(sfe_hit), &hdev));
+    uint32_t *Qp = nullptr, *Qm = nullptr;
+    TRY(pack_slot(c, SL_QP, reinterpret_cast<const uint8_t *>(qdev), qlen, ix->codes, &Qp));
+    TRY(rc_slot(c, SL_QM, Qp, qlen, &Qm));
+    uint64_t *ha = nullptr, *hb = nullptr;
+    void *tmp = nullptr;
+    TRY(ensure_t(c, SL_HITS_A, (size_t)std::max<int64_t>(1, nhits), &ha));
+    TRY(ensure_t(c, SL_HITS_B, (size_t)std::max<int64_t>(1, nhits), &hb));
+    TRY(ensure(c, SL_TMP, radix_sort_temp_bytes(nhits), &tmp));
+    CK(launch_public_to_walk(reinterpret_cast<const sfe_hit *>(hdev), nhits, v.tlen, qlen, span, ha,
+                             &c->small->status, c->st));
+    TRY(sync_small(c));
+    TRY(check_status(c->host_small->status));
+    // (strand, diagonal, t): three stable passes, least significant first
+    const int TB = bits_for(v.tlen);
+    const int DB = bits_for(v.tlen + qlen);
+    uint64_t *cur = ha, *oth = hb;
+    bool in_b = false;
+    CK(radix_sort(cur, oth, nullptr, nullptr, nhits, 0, TB, tmp, &in_b, c->st));
+    if (in_b) std::swap(cur, oth);
+    CK(radix_sort(cur, oth, nullptr, nullptr, nhits, 32, 32 + DB, tmp, &in_b, c->st));
+    if (in_b) std::swap(cur, oth);
+    CK(radix_sort(cur, oth, nullptr, nullptr, nhits, 63, 64, tmp, &in_b, c->st));
+    if (in_b) std::swap(cur, oth);
+    if (nhits > 0) strand_split_kernel<<<1, 1, 0, c->st>>>(cur, nhits, &c->small->split);
+    CK(cudaGetLastError());
+    TRY(sync_small(c));
+    const long long split = nhits > 0 ? (long long)c->host_small->split : 0;
+    Hsp *hd = nullptr;
+    unsigned long long hcap = std::max<unsigned long long>(1ull << 16, (unsigned long long)cap);
+    for (int attempt = 0; attempt < 2; attempt++) {
+        TRY(ensure_t(c, SL_HSPS, (size_t)hcap, &hd));
+        CK(cudaMemsetAsync(&c->small->ctr, 0, sizeof(DevCounters), c->st));
+        for (int s = 0; s < 2; s++) {
+            const long long b = s ? split : 0, e = s ? nhits : split;
+            WalkSetup ws{v.T, v.tlen, s ? Qm : Qp, qlen, s, span, &p, nullptr, hd, hcap};
+            TRY(walk_sorted(c, cur + b, e - b, ws));
+        }
+        TRY(sync_small(c));
+        if (c->host_small->ctr.hsps <= hcap) break;
+        hcap = c->host_small->ctr.hsps;
+    }
+    Small sm = *c->host_small;
+    TRY(check_status(sm.ctr.status));
+    fill_stats(sm, stats, nhits, 1);
+    return finish_hsps(c, hd, sm.ctr.hsps, v.tlen, qlen, hsps, cap, nhsps);
+}
+
+int sfe_run(sfe_ctx *c, const uint8_t *target, int64_t tlen, const uint8_t *query, int64_t qlen,
+            const sfe_params *params, sfe_hsp *hsps, int64_t cap, int64_t *nhsps,
+            sfe_stats *stats) {
+    if (!nhsps) return fail(SFE_EINVAL, "nhsps is NULL");
+    TRY(check_params(params));
+    TRY(check_len(tlen, "target"));
+    TRY(check_len(qlen, "query"));
+    SeedPattern pat;
+    TRY(parse_pattern(params->seed_pattern, &pat));
+    TRY(begin(c));
+    TRY(upload_scores(c, params->scores));
+    const void *tdev = nullptr, *qdev = nullptr;
+    TRY(stage(c, SL_TIN, target, (size_t)tlen, &tdev));
+    TRY(stage(c, SL_QIN, query, (size_t)qlen, &qdev));
+    uint32_t *Tp = nullptr, *Qp = nullptr, *Qm = nullptr;
+    TRY(pack_slot(c, SL_TP, reinterpret_cast<const uint8_t *>(tdev), tlen, params->input_codes, &Tp));
+    TRY(pack_slot(c, SL_QP, reinterpret_cast<const uint8_t *>(qdev), qlen, params->input_codes, &Qp));
+    if (params->strands & 2) TRY(rc_slot(c, SL_QM, Qp, qlen, &Qm));
+    const long long npos = std::max(0LL, (long long)tlen - pat.span + 1);
+    uint32_t *offs = nullptr, *pos = nullptr;
+    TRY(ensure_t(c, SL_OFFS, (size_t)(1LL << (2 * pat.weight)) + 1, &offs));
+    TRY(ensure_t(c, SL_POS, (size_t)std::max(1LL, npos), &pos));
+    TRY(build_index(c, Tp, tlen, pat, offs, pos));
+    IndexView v{Tp, tlen, pat, params->transition, offs, pos};
+
+    const long long tile_hits = params->tile_hits > 0 ? params->tile_hits : kDefaultTileHits;
+    const int DB = bits_for(tlen + qlen);
+    long long hits_total = 0, tiles_total = 0;
+    Hsp *hd = nullptr;
+    unsigned long long hcap = std::max<unsigned long long>(1ull << 16, (unsigned long long)cap);
+    if (c->cap[SL_HSPS] / sizeof(Hsp) > hcap) hcap = c->cap[SL_HSPS] / sizeof(Hsp);
+    for (int attempt = 0; attempt < 2; attempt++) {
+        hits_total = tiles_total = 0;
+        TRY(ensure_t(c, SL_HSPS, (size_t)hcap, &hd));
+        CK(cudaMemsetAsync(&c->small->ctr, 0, sizeof(DevCounters), c->st));
+        for (int s = 0; s < 2; s++) {
+            if (!(params->strands & (1 << s))) continue;
+            const uint32_t *Qs = s ? Qm : Qp;
+            unsigned long long *starts = nullptr, total = 0;
+            long long nq = 0;
+            TRY(count_hits(c, v, Qs, qlen, &starts, &nq, &total));
+            hits_total += (long long)total;
+            if (total == 0) continue;
+            // query tiles of at most ~tile_hits hits each
+            long long ntiles = (long long)((total + tile_hits - 1) / tile_hits);
+            std::vector<long long> qb(ntiles + 1);
+            std::vector<unsigned long long> hb(ntiles + 1);
+            if (ntiles == 1) {
+                qb[0] = 0;
+                qb[1] = nq;
+                hb[0] = 0;
+                hb[1] = total;
+            } else {
+                long long *bd = nullptr;
+                TRY(ensure_t(c, SL_BOUNDS, (size_t)(2 * (ntiles + 1)), &bd));
+                unsigned long long *bs = reinterpret_cast<unsigned long long *>(bd + ntiles + 1);
+                tile_bounds_kernel<<<(unsigned)((ntiles + 1 + 255) / 256), 256, 0, c->st>>>(
+                    starts, nq, (unsigned long long)tile_hits, ntiles, bd, bs);
+                CK(cudaGetLastError());
+                CK(cudaMemcpyAsync(qb.data(), bd, (ntiles + 1) * 8, cudaMemcpyDeviceToHost, c->st));
+                CK(cudaMemcpyAsync(hb.data(), bs, (ntiles + 1) * 8, cudaMemcpyDeviceToHost, c->st));
+                CK(cudaStreamSynchronize(c->st));
+            }
+            unsigned long long maxtile = 0;
+            for (long long k = 0; k < ntiles; k++) maxtile = std::max(maxtile, hb[k + 1] - hb[k]);
+            if (maxtile >= (1ull << 32)) return fail(SFE_EINVAL, "a query tile exceeds 2^32 hits");
+            int32_t *Ecarry = nullptr;
+            if (ntiles > 1) {
+                const long long nd = tlen + qlen;
+                TRY(ensure_t(c, SL_ECARRY, (size_t)nd, &Ecarry));
+                CK(cudaMemsetAsync(Ecarry, 0x80, (size_t)nd * 4, c->st));  // every E < 0
+            }
+            uint64_t *ha = nullptr, *hbuf = nullptr;
+            void *tmp = nullptr;
+            TRY(ensure_t(c, SL_HITS_A, (size_t)maxtile, &ha));
+            TRY(ensure_t(c, SL_HITS_B, (size_t)maxtile, &hbuf));
+            TRY(ensure(c, SL_TMP, radix_sort_temp_bytes((long long)maxtile), &tmp));
+            HitParams hp;
+            hp.pat = pat;
+            hp.transition = params->transition;
+            hp.qlen = qlen;
+            hp.qoff = qlen - pat.span;
+            for (long long k = 0; k < ntiles; k++) {
+                const long long nh = (long long)(hb[k + 1] - hb[k]);
+                if (nh == 0) continue;
+                tiles_total++;
+                CK(launch_hit_write(Qs, hp, offs, pos, qb[k], qb[k + 1], starts + qb[k], hb[k], ha,
+                                    c->st));
+                bool in_b = false;
+                CK(radix_sort(ha, hbuf, nullptr, nullptr, nh, 32, 32 + DB, tmp, &in_b, c->st));
+                WalkSetup ws{Tp, tlen, Qs, qlen, s, pat.span, params, Ecarry, hd, hcap};
+                TRY(walk_sorted(c, in_b ? hbuf : ha, nh, ws));
+            }
+        }
+        TRY(sync_small(c));
+        if (c->host_small->ctr.hsps <= hcap) break;
+        hcap = c->host_small->ctr.hsps;  // grow and run again
+    }
+    Small sm = *c->host_small;
+    TRY(check_status(sm.status | sm.ctr.status));
+    fill_stats(sm, stats, hits_total, tiles_total);
+    return finish_hsps(c, hd, sm.ctr.hsps, tlen, qlen, hsps, cap, nhsps);
+}
+
+}  // extern "C"

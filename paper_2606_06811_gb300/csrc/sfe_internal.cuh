@@ -1,0 +1,162 @@
+// Internal declarations shared by the CUDA translation units of libsfe.
+//
+// Packed sequence layout (every kernel that reads bases uses it):
+//   2 bits per base, 16 bases per uint32, base i in word i/16 at bits 2*(i%16).
+//   A packed buffer holds SEQ_PAD words of zeros before base 0 and SEQ_PAD
+//   words after the last base, so a 16- or 32-base window that starts up to
+//   64 bases before 0 or ends up to 64 bases past the end stays in bounds.
+//   Kernels receive a pointer to the word that holds base 0.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sfe.h"
+
+namespace sfe {
+
+constexpr int SEQ_PAD = 4;          // words of padding on each side
+constexpr int MAX_SPAN = 32;
+constexpr int MAX_WEIGHT = 14;      // 4^14 + 1 offsets = 1 GiB of CSR
+constexpr int BLOCK = 256;
+
+// Device status bits (accumulated with atomicOr into one uint32).
+constexpr uint32_t ST_BAD_SYMBOL = 1u;
+constexpr uint32_t ST_SCORE_OVERFLOW = 2u;
+constexpr uint32_t ST_HSP_OVERFLOW = 4u;
+constexpr uint32_t ST_QUEUE_OVERFLOW = 8u;
+constexpr uint32_t ST_BAD_HIT = 16u;
+
+struct SeedPattern {
+    int span;
+    int weight;
+    int care[MAX_SPAN];
+};
+
+// Counters written by the walkers (one struct in device memory).
+struct DevCounters {
+    unsigned long long extended;
+    unsigned long long cells;
+    unsigned long long hsps;       // HSPs found (may exceed the HSP buffer)
+    unsigned long long lane_tasks;
+    unsigned long long warp_tasks; // queue entries
+    unsigned int status;
+    unsigned int pad;
+};
+
+// HSP as written by the walkers (same layout as sfe_hsp).
+struct Hsp {
+    int32_t strand, tpos, qpos, len, score;
+};
+
+// A hit in the walk layout: high word = diagonal index D = t - q + (qlen - span),
+// low word = t. Sorting by the high word (stably, from query order) groups a
+// diagonal's hits in increasing t.
+__host__ __device__ inline uint64_t make_hit(uint32_t D, uint32_t t) {
+    return ((uint64_t)D << 32) | t;
+}
+
+// 16 bases starting at base p (p may be negative down to -64): base p in bits 0-1.
+__device__ __forceinline__ uint32_t win16(const uint32_t *__restrict__ S, long long p) {
+    long long w = p >> 4;  // arithmetic shift: floor division
+    uint32_t lo = __ldg(S + w), hi = __ldg(S + w + 1);
+    return __funnelshift_r(lo, hi, (uint32_t)(p & 15) * 2u);
+}
+
+__device__ __forceinline__ uint32_t base_at(const uint32_t *__restrict__ S, long long p) {
+    return (__ldg(S + (p >> 4)) >> ((uint32_t)(p & 15) * 2u)) & 3u;
+}
+
+// ------------------------------------------------------------ host launchers
+// All launchers queue work on `st` and return cudaGetLastError().
+
+// bytes -> packed words (n bases). codes: 0 = ASCII, 1 = 2-bit codes.
+// dst points at the word of base 0 of a buffer with SEQ_PAD words on each side;
+// the padding is zeroed too. Bad symbols set ST_BAD_SYMBOL in *status.
+cudaError_t launch_pack(const uint8_t *src, long long n, int codes, uint32_t *dst,
+                        uint32_t *status, cudaStream_t st);
+// Reverse complement of a packed sequence of n bases into another padded buffer.
+cudaError_t launch_revcomp(const uint32_t *src, long long n, uint32_t *dst, cudaStream_t st);
+// keys[p] = (seed key of p) << 32 | p, for p in [0, n - span].
+cudaError_t launch_seed_keys(const uint32_t *S, long long n, SeedPattern pat, uint64_t *keys,
+                             cudaStream_t st);
+// CSR bucket sizes (counts zeroed by the caller) and the positions column from
+// keys sorted by their high word; offsets = exclusive scan of counts.
+cudaError_t launch_csr_counts(const uint64_t *sorted, long long m, uint32_t *counts,
+                              uint32_t *positions, cudaStream_t st);
+
+// Stable LSD radix sort of n uint64 keys by bits [lo, hi), optional uint32
+// values carried along. Uses (a, b) ping-pong and returns in *result_in_b
+// whether the sorted data ended in the b buffers. tmp: radix_sort_temp_bytes(n).
+size_t radix_sort_temp_bytes(long long n);
+cudaError_t radix_sort(uint64_t *keys_a, uint64_t *keys_b, uint32_t *vals_a, uint32_t *vals_b,
+                       long long n, int lo, int hi, void *tmp, bool *result_in_b,
+                       cudaStream_t st);
+
+// Exclusive scan of n uint32 into uint64 (out has n + 1 entries: out[n] = total).
+size_t scan_temp_bytes(long long n);
+cudaError_t scan_u32_to_u64(const uint32_t *in, unsigned long long *out, long long n, void *tmp,
+                            cudaStream_t st);
+cudaError_t scan_u32_to_u32(const uint32_t *in, uint32_t *out, long long n, void *tmp,
+                            cudaStream_t st);
+
+// Seed-hit counting and writing for query positions [q0, q1) of one strand.
+struct HitParams {
+    SeedPattern pat;
+    int transition;
+    long long qlen;
+    long long qoff;  // qlen - span, so D = t - q + qoff >= 0
+};
+cudaError_t launch_hit_count(const uint32_t *Qs, HitParams hp, const uint32_t *offsets,
+                             long long q0, long long q1, uint32_t *counts, cudaStream_t st);
+cudaError_t launch_hit_write(const uint32_t *Qs, HitParams hp, const uint32_t *offsets,
+                             const uint32_t *positions, long long q0, long long q1,
+                             const unsigned long long *starts, unsigned long long base,
+                             uint64_t *hits, cudaStream_t st);
+
+// Segment heads of hits sorted by the high word: seg_start[0..nseg], nseg
+// written to *nseg_dev. tmp: segments_temp_bytes(n).
+size_t segments_temp_bytes(long long n);
+cudaError_t launch_segments(const uint64_t *hits, long long n, uint32_t *flags,
+                            unsigned long long *scan, uint32_t *seg_start, void *tmp,
+                            cudaStream_t st);
+
+struct WalkParams {
+    const uint32_t *T;   // packed target (base 0)
+    const uint32_t *Q;   // packed query strand (base 0)
+    long long tlen, qlen;
+    int span;
+    int strand;
+    int xdrop;
+    int thresh;
+    int flags;
+    int lane_cap;
+    long long qoff;      // qlen - span
+    const int32_t *scores;  // 16 int32 in device memory
+    int32_t *Ecarry;     // per-diagonal E carried across query tiles (nullptr: single tile)
+    Hsp *hsps;
+    unsigned long long hsp_cap;
+    DevCounters *ctr;
+    uint4 *queue;        // hand-off queue: (segment, hit index, E, unused)
+    unsigned long long queue_cap;
+    unsigned int *queue_len;
+};
+// nseg_dev: device count of segments (<= nseg_max, which sizes the grid).
+cudaError_t launch_walk_lanes(const uint64_t *hits, const uint32_t *seg_start,
+                              const unsigned long long *nseg_dev, long long nseg_max,
+                              WalkParams wp, cudaStream_t st);
+cudaError_t launch_walk_warps(const uint64_t *hits, const uint32_t *seg_start, WalkParams wp,
+                              int grid_warps, cudaStream_t st);
+
+// Sort HSPs in place by (strand, tpos, qpos, len, score); tpos < 2^tbits,
+// qpos < 2^qbits, tbits + qbits <= 62. tmp: hsp_sort_temp_bytes(n).
+size_t hsp_sort_temp_bytes(long long n);
+cudaError_t hsp_sort(Hsp *hsps, long long n, int tbits, int qbits, void *tmp, cudaStream_t st);
+
+// Conversions between the public hit record and the walk layout.
+cudaError_t launch_hits_to_public(const uint64_t *hits, long long n, int strand, long long qoff,
+                                  sfe_hit *out, cudaStream_t st);
+cudaError_t launch_public_to_walk(const sfe_hit *in, long long n, long long tlen, long long qlen,
+                                  int span, uint64_t *out, uint32_t *status, cudaStream_t st);
+
+}  // namespace sfe

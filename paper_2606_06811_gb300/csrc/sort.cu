@@ -1,0 +1,466 @@
+// Device radix sort (stable, LSD, 8-bit digits), exclusive scans and the HSP
+// ordering. Written from scratch: no CUB in the library.
+//
+// Radix sort per 8-bit digit pass, over a grid of G CTAs that each own one
+// contiguous chunk of the input (a whole number of 4096-element tiles):
+//   1. rs_hist:    per-CTA digit counts -> counts[digit * G + cta], digit totals
+//   2. rs_offsets: per digit, exclusive scan over CTAs plus the digit's base
+//   3. rs_scatter: each CTA walks its tiles in order; warps rank their elements
+//      stably with __match_any_sync in element order, the tile is reordered in
+//      shared memory, and runs of equal digits are written out contiguously.
+// Traffic per pass: the keys are read twice and written once (plus values).
+#include "sfe_internal.cuh"
+
+namespace sfe {
+
+namespace {
+
+constexpr int RS_BLOCK = 256;
+constexpr int RS_WARPS = RS_BLOCK / 32;
+constexpr int RS_ITEMS = 16;
+constexpr int RS_TILE = RS_BLOCK * RS_ITEMS;  // 4096
+constexpr int RS_R = 256;                     // buckets per pass (+1 for padding lanes)
+
+int g_num_sms = 0;
+
+int num_sms() {
+    if (g_num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 1;
+    }
+    return g_num_sms;
+}
+
+struct RsGeom {
+    int G;
+    long long chunk;
+};
+
+RsGeom rs_geom(long long n) {
+    long long tiles = (n + RS_TILE - 1) / RS_TILE;
+    long long gmax = 4LL * num_sms();
+    long long G = tiles < gmax ? tiles : gmax;
+    if (G < 1) G = 1;
+    long long per = (tiles + G - 1) / G;
+    RsGeom g;
+    g.G = (int)((tiles + per - 1) / per);
+    if (g.G < 1) g.G = 1;
+    g.chunk = per * RS_TILE;
+    return g;
+}
+
+__global__ void __launch_bounds__(RS_BLOCK) rs_hist(const uint64_t *__restrict__ keys,
+                                                    long long n, int shift, unsigned mask,
+                                                    long long chunk, unsigned *__restrict__ counts,
+                                                    unsigned *__restrict__ totals, int G) {
+    __shared__ unsigned h[RS_WARPS][RS_R];
+    for (int i = threadIdx.x; i < RS_WARPS * RS_R; i += RS_BLOCK) (&h[0][0])[i] = 0;
+    __syncthreads();
+    long long beg = (long long)blockIdx.x * chunk;
+    long long end = min(n, beg + chunk);
+    int w = threadIdx.x >> 5;
+    for (long long i = beg + threadIdx.x; i < end; i += RS_BLOCK) {
+        unsigned d = (unsigned)(keys[i] >> shift) & mask;
+        atomicAdd(&h[w][d], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < RS_R; d += RS_BLOCK) {
+        unsigned s = 0;
+#pragma unroll
+        for (int k = 0; k < RS_WARPS; k++) s += h[k][d];
+        counts[(long long)d * G + blockIdx.x] = s;
+        if (s) atomicAdd(&totals[d], s);
+    }
+}
+
+// Inclusive warp scan.
+__device__ __forceinline__ unsigned warp_incl(unsigned v) {
+    int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_incl64(unsigned long long v) {
+    int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
+// Exclusive scan over a block of BLOCK threads (one value each); returns the
+// thread's exclusive prefix and the block total in *total. Uses `sh` (>= 33).
+template <int NT>
+__device__ __forceinline__ unsigned long long block_excl64(unsigned long long v,
+                                                           unsigned long long *sh,
+                                                           unsigned long long *total) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long inc = warp_incl64(v);
+    if (lane == 31) sh[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long s = (lane < NT / 32) ? sh[lane] : 0ull;
+        unsigned long long si = warp_incl64(s);
+        if (lane < NT / 32) sh[lane] = si - s;
+        if (lane == 31) sh[32] = si;
+    }
+    __syncthreads();
+    unsigned long long r = sh[w] + inc - v;
+    *total = sh[32];
+    __syncthreads();
+    return r;
+}
+
+// Block d: offsets[d * G + g] = sum(totals[< d]) + sum(counts[d * G + < g]).
+__global__ void __launch_bounds__(RS_BLOCK) rs_offsets(unsigned *__restrict__ counts,
+                                                       const unsigned *__restrict__ totals, int G) {
+    __shared__ unsigned long long sh[33];
+    int d = blockIdx.x;
+    unsigned long long b = 0;
+    for (int k = threadIdx.x; k < d; k += RS_BLOCK) b += totals[k];
+    unsigned long long tot;
+    block_excl64<RS_BLOCK>(b, sh, &tot);
+    unsigned long long carry = tot;
+    for (int base = 0; base < G; base += RS_BLOCK) {
+        int g = base + threadIdx.x;
+        unsigned long long c = (g < G) ? counts[(long long)d * G + g] : 0ull;
+        unsigned long long t2;
+        unsigned long long ex = block_excl64<RS_BLOCK>(c, sh, &t2);
+        if (g < G) counts[(long long)d * G + g] = (unsigned)(carry + ex);
+        carry += t2;
+    }
+}
+
+template <bool VALS>
+__global__ void __launch_bounds__(RS_BLOCK) rs_scatter(
+    const uint64_t *__restrict__ kin, uint64_t *__restrict__ kout,
+    const unsigned *__restrict__ vin, unsigned *__restrict__ vout, long long n, int shift,
+    unsigned mask, long long chunk, const unsigned *__restrict__ offsets, int G) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *sk = reinterpret_cast<uint64_t *>(smem);                     // RS_TILE
+    unsigned *sv = reinterpret_cast<unsigned *>(sk + RS_TILE);              // RS_TILE (VALS)
+    unsigned *wh = sv + (VALS ? RS_TILE : 0);                               // RS_WARPS*(R+1)
+    unsigned *tcount = wh + RS_WARPS * (RS_R + 1);                          // R+1
+    unsigned *tstart = tcount + (RS_R + 1);                                 // R+1
+    unsigned *run = tstart + (RS_R + 1);                                    // R
+
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const long long beg = (long long)blockIdx.x * chunk;
+    const long long end = min(n, beg + chunk);
+    for (int d = tid; d < RS_R; d += RS_BLOCK) run[d] = offsets[(long long)d * G + blockIdx.x];
+
+    for (long long tb = beg; tb < end; tb += RS_TILE) {
+        const unsigned tile_n = (unsigned)min((long long)RS_TILE, end - tb);
+        for (int i = tid; i < RS_WARPS * (RS_R + 1); i += RS_BLOCK) wh[i] = 0;
+        __syncthreads();
+
+        uint64_t k[RS_ITEMS];
+        unsigned v[RS_ITEMS], dg[RS_ITEMS], rk[RS_ITEMS];
+        const unsigned wbase = w * 32 * RS_ITEMS;
+#pragma unroll
+        for (int j = 0; j < RS_ITEMS; j++) {
+            unsigned e = wbase + j * 32 + lane;
+            bool valid = e < tile_n;
+            k[j] = valid ? kin[tb + e] : ~0ull;
+            if (VALS) v[j] = valid ? vin[tb + e] : 0u;
+            dg[j] = valid ? ((unsigned)(k[j] >> shift) & mask) : (unsigned)RS_R;
+        }
+        unsigned *myh = wh + w * (RS_R + 1);
+#pragma unroll
+        for (int j = 0; j < RS_ITEMS; j++) {
+            unsigned peers = __match_any_sync(0xffffffffu, dg[j]);
+            unsigned lt = peers & ((1u << lane) - 1u);
+            unsigned cnt = myh[dg[j]];
+            rk[j] = cnt + __popc(lt);
+            __syncwarp();
+            if (lt == 0) myh[dg[j]] = cnt + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        // per digit: exclusive prefix across warps, tile totals
+        for (int d = tid; d <= RS_R; d += RS_BLOCK) {
+            unsigned s = 0;
+#pragma unroll
+            for (int ww = 0; ww < RS_WARPS; ww++) {
+                unsigned c = wh[ww * (RS_R + 1) + d];
+                wh[ww * (RS_R + 1) + d] = s;
+                s += c;
+            }
+            tcount[d] = s;
+        }
+        __syncthreads();
+        // exclusive scan of tcount[0..R] by warp 0 (9 values per lane)
+        if (w == 0) {
+            constexpr int PER = (RS_R + 1 + 31) / 32;
+            unsigned loc[PER], s = 0;
+#pragma unroll
+            for (int i = 0; i < PER; i++) {
+                int d = lane * PER + i;
+                loc[i] = (d <= RS_R) ? tcount[d] : 0u;
+                s += loc[i];
+            }
+            unsigned inc = warp_incl(s);
+            unsigned ex = inc - s;
+#pragma unroll
+            for (int i = 0; i < PER; i++) {
+                int d = lane * PER + i;
+                if (d <= RS_R) tstart[d] = ex;
+                ex += loc[i];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < RS_ITEMS; j++) {
+            unsigned pos = tstart[dg[j]] + myh[dg[j]] + rk[j];
+            sk[pos] = k[j];
+            if (VALS) sv[pos] = v[j];
+        }
+        __syncthreads();
+        for (unsigned p = tid; p < tile_n; p += RS_BLOCK) {
+            uint64_t kk = sk[p];
+            unsigned d = (unsigned)(kk >> shift) & mask;
+            unsigned o = run[d] + (p - tstart[d]);
+            kout[o] = kk;
+            if (VALS) vout[o] = sv[p];
+        }
+        __syncthreads();
+        for (int d = tid; d < RS_R; d += RS_BLOCK) run[d] += tcount[d];
+        __syncthreads();
+    }
+}
+
+size_t rs_smem(bool vals) {
+    return (size_t)RS_TILE * 8 + (vals ? (size_t)RS_TILE * 4 : 0) +
+           (size_t)RS_WARPS * (RS_R + 1) * 4 + 2 * (size_t)(RS_R + 1) * 4 + (size_t)RS_R * 4;
+}
+
+// ------------------------------------------------------------------- scans
+
+constexpr int SC_BLOCK = 256;
+constexpr int SC_ITEMS = 16;
+constexpr long long SC_CHUNK = (long long)SC_BLOCK * SC_ITEMS;
+
+template <typename Tin>
+__global__ void __launch_bounds__(SC_BLOCK) scan_reduce(const Tin *__restrict__ in, long long n,
+                                                        unsigned long long *__restrict__ part) {
+    __shared__ unsigned long long sh[33];
+    long long beg = (long long)blockIdx.x * SC_CHUNK;
+    long long end = min(n, beg + SC_CHUNK);
+    unsigned long long s = 0;
+    for (long long i = beg + threadIdx.x; i < end; i += SC_BLOCK) s += in[i];
+    unsigned long long tot;
+    block_excl64<SC_BLOCK>(s, sh, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+// Exclusive scan of part[0..nb) in place, part[nb] = total. One block.
+__global__ void __launch_bounds__(1024) scan_partials(unsigned long long *part, long long nb) {
+    __shared__ unsigned long long sh[33];
+    unsigned long long carry = 0;
+    for (long long base = 0; base < nb; base += 1024) {
+        long long i = base + threadIdx.x;
+        unsigned long long v = i < nb ? part[i] : 0ull;
+        unsigned long long tot;
+        unsigned long long ex = block_excl64<1024>(v, sh, &tot);
+        if (i < nb) part[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) part[nb] = carry;
+}
+
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(SC_BLOCK) scan_down(const Tin *__restrict__ in,
+                                                      Tout *__restrict__ out, long long n,
+                                                      const unsigned long long *__restrict__ part,
+                                                      long long nb) {
+    __shared__ unsigned long long sh[33];
+    long long beg = (long long)blockIdx.x * SC_CHUNK;
+    long long end = min(n, beg + SC_CHUNK);
+    unsigned long long carry = part[blockIdx.x];
+    for (long long base = beg; base < end; base += SC_BLOCK) {
+        long long i = base + threadIdx.x;
+        unsigned long long v = i < end ? (unsigned long long)in[i] : 0ull;
+        unsigned long long tot;
+        unsigned long long ex = block_excl64<SC_BLOCK>(v, sh, &tot);
+        if (i < end) out[i] = (Tout)(carry + ex);
+        carry += tot;
+    }
+    if (blockIdx.x == nb - 1 && threadIdx.x == 0) out[n] = (Tout)part[nb];
+}
+
+template <typename Tin, typename Tout>
+cudaError_t scan_impl(const Tin *in, Tout *out, long long n, void *tmp, cudaStream_t st) {
+    long long nb = (n + SC_CHUNK - 1) / SC_CHUNK;
+    unsigned long long *part = reinterpret_cast<unsigned long long *>(tmp);
+    if (n == 0) {
+        cudaMemsetAsync(out, 0, sizeof(Tout), st);
+        return cudaGetLastError();
+    }
+    scan_reduce<Tin><<<(unsigned)nb, SC_BLOCK, 0, st>>>(in, n, part);
+    scan_partials<<<1, 1024, 0, st>>>(part, nb);
+    scan_down<Tin, Tout><<<(unsigned)nb, SC_BLOCK, 0, st>>>(in, out, n, part, nb);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- HSP sort
+
+__global__ void hsp_keys(const Hsp *__restrict__ h, long long n, int qbits, uint64_t *keys,
+                         unsigned *idx) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Hsp x = h[i];
+    keys[i] = ((uint64_t)(uint32_t)x.strand << 62) | ((uint64_t)(uint32_t)x.tpos << qbits) |
+              (uint64_t)(uint32_t)x.qpos;
+    idx[i] = (unsigned)i;
+}
+
+__global__ void hsp_gather(const Hsp *__restrict__ h, const unsigned *__restrict__ idx,
+                           long long n, Hsp *__restrict__ out) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = h[idx[i]];
+}
+
+__device__ __forceinline__ bool hsp_less(const Hsp &a, const Hsp &b) {
+    if (a.len != b.len) return a.len < b.len;
+    return a.score < b.score;
+}
+
+// Runs of equal (strand, tpos, qpos) are ordered by (len, score); such runs
+// are short (they need two HSPs that start at the same cell), so each run is
+// insertion-sorted by the thread at its head.
+__global__ void hsp_fix_runs(Hsp *__restrict__ h, const uint64_t *__restrict__ keys, long long n) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (i > 0 && keys[i - 1] == keys[i]) return;
+    long long j = i + 1;
+    while (j < n && keys[j] == keys[i]) j++;
+    for (long long a = i + 1; a < j; a++) {
+        Hsp x = h[a];
+        long long b = a - 1;
+        while (b >= i && hsp_less(x, h[b])) {
+            h[b + 1] = h[b];
+            b--;
+        }
+        h[b + 1] = x;
+    }
+}
+
+unsigned grid_for(long long n, int block = BLOCK) { return (unsigned)((n + block - 1) / block); }
+
+}  // namespace
+
+size_t radix_sort_temp_bytes(long long n) {
+    RsGeom g = rs_geom(n > 0 ? n : 1);
+    return (size_t)RS_R * g.G * 4 + RS_R * 4 + 256;
+}
+
+cudaError_t radix_sort(uint64_t *keys_a, uint64_t *keys_b, uint32_t *vals_a, uint32_t *vals_b,
+                       long long n, int lo, int hi, void *tmp, bool *result_in_b,
+                       cudaStream_t st) {
+    *result_in_b = false;
+    if (n <= 1 || hi <= lo) return cudaSuccess;
+    if (n >= (1LL << 32)) return cudaErrorInvalidValue;
+    RsGeom g = rs_geom(n);
+    unsigned *counts = reinterpret_cast<unsigned *>(tmp);
+    unsigned *totals = counts + (size_t)RS_R * g.G;
+    const bool vals = vals_a != nullptr;
+    size_t smem = rs_smem(vals);
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[vals]) {
+        cudaError_t e = vals ? cudaFuncSetAttribute(rs_scatter<true>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)smem)
+                             : cudaFuncSetAttribute(rs_scatter<false>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set[vals] = true;
+    }
+    uint64_t *kin = keys_a, *kout = keys_b;
+    uint32_t *vin = vals_a, *vout = vals_b;
+    bool in_b = false;
+    for (int shift = lo; shift < hi; shift += 8) {
+        int bits = min(8, hi - shift);
+        unsigned mask = (1u << bits) - 1u;
+        cudaMemsetAsync(totals, 0, RS_R * 4, st);
+        rs_hist<<<g.G, RS_BLOCK, 0, st>>>(kin, n, shift, mask, g.chunk, counts, totals, g.G);
+        rs_offsets<<<RS_R, RS_BLOCK, 0, st>>>(counts, totals, g.G);
+        if (vals)
+            rs_scatter<true><<<g.G, RS_BLOCK, smem, st>>>(kin, kout, vin, vout, n, shift, mask,
+                                                          g.chunk, counts, g.G);
+        else
+            rs_scatter<false><<<g.G, RS_BLOCK, smem, st>>>(kin, kout, nullptr, nullptr, n, shift,
+                                                           mask, g.chunk, counts, g.G);
+        uint64_t *tk = kin;
+        kin = kout;
+        kout = tk;
+        uint32_t *tv = vin;
+        vin = vout;
+        vout = tv;
+        in_b = !in_b;
+    }
+    *result_in_b = in_b;
+    return cudaGetLastError();
+}
+
+size_t scan_temp_bytes(long long n) {
+    long long nb = (n + SC_CHUNK - 1) / SC_CHUNK;
+    return (size_t)(nb + 1) * 8 + 256;
+}
+
+cudaError_t scan_u32_to_u64(const uint32_t *in, unsigned long long *out, long long n, void *tmp,
+                            cudaStream_t st) {
+    return scan_impl<uint32_t, unsigned long long>(in, out, n, tmp, st);
+}
+
+cudaError_t scan_u32_to_u32(const uint32_t *in, uint32_t *out, long long n, void *tmp,
+                            cudaStream_t st) {
+    return scan_impl<uint32_t, uint32_t>(in, out, n, tmp, st);
+}
+
+size_t hsp_sort_temp_bytes(long long n) {
+    n = n > 0 ? n : 1;
+    return (size_t)n * (8 + 8 + 4 + 4 + sizeof(Hsp)) + radix_sort_temp_bytes(n) + 1024;
+}
+
+cudaError_t hsp_sort(Hsp *hsps, long long n, int tbits, int qbits, void *tmp, cudaStream_t st) {
+    if (n <= 1) return cudaSuccess;
+    char *p = reinterpret_cast<char *>(tmp);
+    auto take = [&](size_t bytes) {
+        char *r = p;
+        p += (bytes + 255) & ~(size_t)255;
+        return r;
+    };
+    uint64_t *ka = reinterpret_cast<uint64_t *>(take((size_t)n * 8));
+    uint64_t *kb = reinterpret_cast<uint64_t *>(take((size_t)n * 8));
+    unsigned *va = reinterpret_cast<unsigned *>(take((size_t)n * 4));
+    unsigned *vb = reinterpret_cast<unsigned *>(take((size_t)n * 4));
+    Hsp *hb = reinterpret_cast<Hsp *>(take((size_t)n * sizeof(Hsp)));
+    void *rt = take(radix_sort_temp_bytes(n));
+    hsp_keys<<<grid_for(n), BLOCK, 0, st>>>(hsps, n, qbits, ka, va);
+    bool in_b = false;
+    // strand sits at bit 62; tpos and qpos below it
+    cudaError_t e = radix_sort(ka, kb, va, vb, n, 0, qbits + tbits, rt, &in_b, st);
+    if (e != cudaSuccess) return e;
+    uint64_t *k1 = in_b ? kb : ka, *k2 = in_b ? ka : kb;
+    unsigned *v1 = in_b ? vb : va, *v2 = in_b ? va : vb;
+    e = radix_sort(k1, k2, v1, v2, n, 62, 63, rt, &in_b, st);
+    if (e != cudaSuccess) return e;
+    uint64_t *kf = in_b ? k2 : k1;
+    unsigned *vf = in_b ? v2 : v1;
+    hsp_gather<<<grid_for(n), BLOCK, 0, st>>>(hsps, vf, n, hb);
+    hsp_fix_runs<<<grid_for(n), BLOCK, 0, st>>>(hb, kf, n);
+    cudaMemcpyAsync(hsps, hb, (size_t)n * sizeof(Hsp), cudaMemcpyDeviceToDevice, st);
+    return cudaGetLastError();
+}
+
+}  // namespace sfe

@@ -1,0 +1,263 @@
+"""Python binding of libsfe: argument marshalling only.
+
+Every step of the filter stage runs in the library's CUDA kernels; this module
+converts numpy arrays, bytes and PyTorch tensors into pointers and sizes,
+calls the C ABI declared in include/sfe.h and wraps the results. It fails
+loudly when the library has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsfe.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW = 0, -1, -2, -3, -4, -5
+SKIP_PASSING_ONLY = 1
+
+HIT_DTYPE = np.dtype([("strand", "<i4"), ("tpos", "<i4"), ("qpos", "<i4")])
+HSP_DTYPE = np.dtype([("strand", "<i4"), ("tpos", "<i4"), ("qpos", "<i4"), ("len", "<i4"),
+                      ("score", "<i4")])
+
+
+class SfeError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [("seed_pattern", C.c_char_p), ("transition", C.c_int32),
+                ("strands", C.c_int32), ("scores", C.c_int32 * 16), ("xdrop", C.c_int32),
+                ("hsp_thresh", C.c_int32), ("flags", C.c_int32), ("input_codes", C.c_int32),
+                ("lane_cap", C.c_int32), ("reserved", C.c_int32), ("tile_hits", C.c_int64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("hits", C.c_int64), ("extended", C.c_int64), ("cells", C.c_int64),
+                ("hsps", C.c_int64), ("lane_tasks", C.c_int64), ("warp_tasks", C.c_int64),
+                ("tiles", C.c_int64), ("reserved", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """The loaded libsfe (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libsfe.so is not built ({LIB_PATH}); run "
+                              "paper_2606_06811_gb300.build.build() or __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        L.sfe_params_default.argtypes = [C.POINTER(Params)]
+        L.sfe_strerror.argtypes = [C.c_int]
+        L.sfe_strerror.restype = C.c_char_p
+        L.sfe_last_error.argtypes = []
+        L.sfe_last_error.restype = C.c_char_p
+        L.sfe_ctx_create.argtypes = [C.c_int, C.POINTER(vp)]
+        L.sfe_ctx_set_stream.argtypes = [vp, vp]
+        L.sfe_ctx_destroy.argtypes = [vp]
+        L.sfe_ctx_destroy.restype = None
+        L.sfe_index_build.argtypes = [vp, vp, i64, C.POINTER(Params), C.POINTER(vp)]
+        L.sfe_index_free.argtypes = [vp]
+        L.sfe_index_free.restype = None
+        L.sfe_seed_hits.argtypes = [vp, vp, vp, i64, i32, vp, i64, C.POINTER(i64)]
+        L.sfe_ungapped_xdrop.argtypes = [vp, vp, vp, i64, vp, i64, C.POINTER(C.c_int32 * 16), i32,
+                                         i32, vp, i64, C.POINTER(i64), C.POINTER(Stats)]
+        L.sfe_run.argtypes = [vp, vp, i64, vp, i64, C.POINTER(Params), vp, i64, C.POINTER(i64),
+                              C.POINTER(Stats)]
+        for f in ("sfe_params_default", "sfe_ctx_create", "sfe_ctx_set_stream", "sfe_index_build",
+                  "sfe_seed_hits", "sfe_ungapped_xdrop", "sfe_run"):
+            getattr(L, f).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(code: int) -> int:
+    if code != OK:
+        raise SfeError(code, lib().sfe_last_error().decode(errors="replace") or
+                       lib().sfe_strerror(code).decode())
+    return code
+
+
+def default_params(**kw) -> Params:
+    """sfe_params_default(), then the given fields (scores may be a 4x4 or 16 array)."""
+    p = Params()
+    _check(lib().sfe_params_default(C.byref(p)))
+    for k, v in kw.items():
+        if k == "scores":
+            p.scores[:] = [int(x) for x in np.asarray(v, dtype=np.int64).reshape(16)]
+        elif k == "seed_pattern":
+            p._pattern_keep = v.encode() if isinstance(v, str) else v
+            p.seed_pattern = p._pattern_keep
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def _buf(x):
+    """(pointer, number of elements, keep-alive) of a torch tensor, numpy array or bytes."""
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            if not x.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            return x.data_ptr(), x.numel(), x
+    except ImportError:
+        pass
+    if isinstance(x, (bytes, bytearray, memoryview)):
+        x = np.frombuffer(x, dtype=np.uint8)
+    a = np.ascontiguousarray(x)
+    if a.size == 0:
+        a = np.zeros(1, dtype=a.dtype)
+        return a.ctypes.data, 0, a
+    return a.ctypes.data, a.size, a
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class Context:
+    """A device context (stream + scratch arena) of libsfe."""
+
+    def __init__(self, device: int = 0, stream=None):
+        h = C.c_void_p()
+        _check(lib().sfe_ctx_create(int(device), C.byref(h)))
+        self.h = h
+        self.device = int(device)
+        if stream is not None:
+            self.set_stream(stream)
+
+    def set_stream(self, stream) -> None:
+        _check(lib().sfe_ctx_set_stream(self.h, _stream_handle(stream)))
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            lib().sfe_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ------------------------------------------------------------ calls
+
+    def index_build(self, target, params: Params | None = None) -> "Index":
+        p = params or default_params()
+        ptr, n, keep = _buf(target)
+        h = C.c_void_p()
+        _check(lib().sfe_index_build(self.h, ptr, n, C.byref(p), C.byref(h)))
+        return Index(h, n)
+
+    def seed_hits(self, index: "Index", query, strands: int = 3, cap: int | None = None,
+                  out=None):
+        """Hits sorted by (strand, diagonal, tpos); numpy HIT_DTYPE unless `out` is given."""
+        ptr, n, keep = _buf(query)
+        nh = C.c_int64(0)
+        if out is not None:
+            optr, ocap, _ = _buf(out)
+            _check(lib().sfe_seed_hits(self.h, index.h, ptr, n, int(strands), optr, ocap // 3,
+                                       C.byref(nh)))
+            return out, int(nh.value)
+        cap = 1 << 16 if cap is None else int(cap)
+        while True:
+            buf = np.zeros(max(cap, 1), dtype=HIT_DTYPE)
+            code = lib().sfe_seed_hits(self.h, index.h, ptr, n, int(strands), buf.ctypes.data,
+                                       cap, C.byref(nh))
+            if code == EOVERFLOW and nh.value > cap:
+                cap = int(nh.value)
+                continue
+            _check(code)
+            return buf[: nh.value]
+
+    def ungapped_xdrop(self, index: "Index", query, hits, scores, X: int, thresh: int,
+                       cap: int | None = None):
+        """(HSPs as numpy HSP_DTYPE sorted, stats dict) for a hit list."""
+        qptr, qn, qkeep = _buf(query)
+        if isinstance(hits, np.ndarray) and hits.dtype == HIT_DTYPE:
+            hits = hits.view(np.int32).reshape(-1)
+        hptr, hn, hkeep = _buf(hits)
+        nhits = hn // 3
+        sc = (C.c_int32 * 16)(*[int(x) for x in np.asarray(scores, dtype=np.int64).reshape(16)])
+        return self._retry(cap, lambda buf, cp, nout, st: lib().sfe_ungapped_xdrop(
+            self.h, index.h, qptr, qn, hptr, nhits, C.byref(sc), int(X), int(thresh), buf, cp,
+            nout, st))
+
+    def run(self, target, query, params: Params | None = None, cap: int | None = None,
+            out=None):
+        """The whole filter stage. Returns (HSPs, stats); HSPs are numpy HSP_DTYPE, or the
+        first rows of `out` (an int32 tensor of shape (cap, 5)) when it is given."""
+        p = params or default_params()
+        tptr, tn, tkeep = _buf(target)
+        qptr, qn, qkeep = _buf(query)
+        if out is not None:
+            optr, on, _ = _buf(out)
+            nout = C.c_int64(0)
+            st = Stats()
+            _check(lib().sfe_run(self.h, tptr, tn, qptr, qn, C.byref(p), optr, on // 5,
+                                 C.byref(nout), C.byref(st)))
+            return out[: nout.value], st.as_dict()
+        return self._retry(cap, lambda buf, cp, nout, st: lib().sfe_run(
+            self.h, tptr, tn, qptr, qn, C.byref(p), buf, cp, nout, st))
+
+    def _retry(self, cap, call):
+        cap = 1 << 16 if cap is None else int(cap)
+        nout = C.c_int64(0)
+        st = Stats()
+        while True:
+            buf = np.zeros(max(cap, 1), dtype=HSP_DTYPE)
+            code = call(buf.ctypes.data, cap, C.byref(nout), C.byref(st))
+            if code == EOVERFLOW and nout.value > cap:
+                cap = int(nout.value)
+                continue
+            _check(code)
+            return buf[: nout.value], st.as_dict()
+
+
+class Index:
+    """A seeding index over one target (owned device memory)."""
+
+    def __init__(self, h, tlen: int):
+        self.h = h
+        self.tlen = tlen
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            lib().sfe_index_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def exported_symbols() -> list[str]:
+    """Names of the functions declared in include/sfe.h."""
+    import re
+    hdr = os.path.join(os.path.dirname(_HERE), "include", "sfe.h")
+    txt = open(hdr).read()
+    return sorted(set(re.findall(r"\b(sfe_[a-z_]+)\s*\(", txt)))

@@ -1,0 +1,205 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bit-exact: the sorted HSP lists (strand, tpos, qpos, len, int32 score) and the
+work counters (hits, extended hits, cells) must be identical.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import bruteforce as bf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2606_06811_gb300 as P
+    return P
+
+
+@pytest.fixture(scope="module")
+def ctx(pkg):
+    c = pkg.Context(0)
+    yield c
+    c.close()
+
+
+def as_i32(h) -> np.ndarray:
+    return np.ascontiguousarray(h).view(np.int32).reshape(-1, 5)
+
+
+def assert_same(got, st, ref):
+    a, b = as_i32(got), as_i32(ref.hsps)
+    assert a.shape == b.shape, (a.shape, b.shape)
+    if a.size:
+        bad = np.flatnonzero((a != b).any(1))
+        assert bad.size == 0, f"first mismatch at {bad[0]}: gpu {a[bad[0]]} oracle {b[bad[0]]}"
+    assert (st["hits"], st["extended"], st["cells"]) == (ref.hits, ref.extended, ref.cells), \
+        (st, ref.stats)
+
+
+def run_both(pkg, ctx, T, Q, **kw):
+    okw = {k: v for k, v in kw.items() if k in ("pattern", "transition", "strands", "scores",
+                                                 "X", "thresh", "flags")}
+    ref = oracle.run(T, Q, **okw)
+    pmap = {"pattern": "seed_pattern", "X": "xdrop", "thresh": "hsp_thresh"}
+    pkw = {pmap.get(k, k): v for k, v in kw.items()}
+    pkw.setdefault("input_codes", 1)
+    got, st = ctx.run(T, Q, pkg.default_params(**pkw))
+    return got, st, ref
+
+
+def test_tiny_pair_full(pkg, ctx):
+    p = synth.tiny_pair(1)
+    got, st, ref = run_both(pkg, ctx, p.T, p.Q)
+    assert_same(got, st, ref)
+    assert len(got) >= 50
+
+
+@pytest.mark.parametrize("lane_cap", [1, 16, 40, 1 << 30])
+def test_lane_cap_does_not_change_output(pkg, ctx, lane_cap):
+    p = synth.tiny_pair(2, length=60_000, n_blocks=15)
+    got, st, ref = run_both(pkg, ctx, p.T, p.Q, lane_cap=lane_cap)
+    assert_same(got, st, ref)
+
+
+@pytest.mark.parametrize("tile_hits", [1, 777, 5000])
+def test_query_tiles_carry_the_skip_state(pkg, ctx, tile_hits):
+    p = synth.tiny_pair(3, length=50_000, n_blocks=12)
+    got, st, ref = run_both(pkg, ctx, p.T, p.Q, tile_hits=tile_hits)
+    assert_same(got, st, ref)
+    assert st["tiles"] > 1
+
+
+def _pair(seed, n, m, gc=0.5, blocks=4):
+    st = synth.Stream(seed, "gpu")
+    T = synth.iid_bases(st.child("T"), n, gc)
+    Q = synth.iid_bases(st.child("Q"), m, gc)
+    if blocks and n > 2000 and m > 2000:
+        synth.plant_blocks(st.child("b"), T, Q, blocks, 300, 1500, 0.80, 0.97, 0.5, 0.01, gc)
+    return T, Q
+
+
+def _asym(seed):
+    st = synth.Stream(seed, "scores")
+    M = st.integers(-60, 40, 16).reshape(4, 4).astype(np.int32)
+    M[np.arange(4), np.arange(4)] = st.integers(50, 120, 4)
+    return M
+
+
+@pytest.mark.parametrize("case", [
+    dict(), dict(transition=False), dict(pattern="1101011"), dict(pattern="11011", transition=False),
+    dict(pattern="111010010100110111"), dict(X=0), dict(X=50), dict(X=5000),
+    dict(thresh=0), dict(thresh=-100000), dict(flags=1, thresh=1000), dict(strands=1),
+    dict(strands=2), dict(scores="asym", X=300, thresh=500),
+], ids=lambda c: ",".join(f"{k}={v}" for k, v in c.items()) or "default")
+def test_parameters(pkg, ctx, case):
+    case = dict(case)
+    if case.get("scores") == "asym":
+        case["scores"] = _asym(5)
+    T, Q = _pair(11, 9_001, 7_333)
+    got, st, ref = run_both(pkg, ctx, T, Q, **case)
+    assert_same(got, st, ref)
+
+
+@pytest.mark.parametrize("n,m", [(0, 100), (100, 0), (0, 0), (18, 18), (19, 19), (19, 40),
+                                 (33, 17), (1, 1000), (4097, 65), (16, 16), (31, 47)])
+def test_ragged_and_degenerate_lengths(pkg, ctx, n, m):
+    T, Q = _pair(n * 7 + m, n, m, blocks=0)
+    got, st, ref = run_both(pkg, ctx, T, Q, thresh=-100000)
+    assert_same(got, st, ref)
+
+
+def test_identical_sequences_long_extensions(pkg, ctx):
+    st = synth.Stream(31, "ident")
+    T = synth.iid_bases(st, 20_000, 0.5)
+    got, stt, ref = run_both(pkg, ctx, T, T.copy())
+    assert_same(got, stt, ref)
+    assert stt["warp_tasks"] > 0
+
+
+def test_poly_a_hit_explosion(pkg, ctx):
+    T = np.zeros(3000, np.uint8)
+    Q = np.zeros(2500, np.uint8)
+    Q[1000] = 2
+    got, st, ref = run_both(pkg, ctx, T, Q, thresh=0)
+    assert_same(got, st, ref)
+
+
+def test_period19_repeats(pkg, ctx):
+    st = synth.Stream(5, "p19")
+    unit = synth.iid_bases(st, 19, 0.5)
+    T = np.tile(unit, 300)
+    Q = np.tile(unit, 200)[7:]
+    got, stt, ref = run_both(pkg, ctx, T, Q, thresh=0)
+    assert_same(got, stt, ref)
+
+
+def test_plain_generator_scaled(pkg, ctx):
+    p = synth.plain_pair_10mb(2, scale=0.02)  # 200 kb with repeats and rc blocks
+    got, st, ref = run_both(pkg, ctx, p.T, p.Q)
+    assert_same(got, st, ref)
+
+
+def test_ascii_input_and_host_device_buffers(pkg, ctx):
+    import torch
+    p = synth.tiny_pair(4, length=40_000, n_blocks=10)
+    Ta = np.frombuffer(synth.decode(p.T), np.uint8).copy()
+    Qa = np.frombuffer(synth.decode(p.Q), np.uint8).copy()
+    Qa[::7] += 32  # lower case is accepted
+    ref = oracle.run(p.T, p.Q)
+    params = pkg.default_params()
+    for T, Q in ((Ta, Qa), (torch.from_numpy(Ta).cuda(), torch.from_numpy(Qa).cuda())):
+        got, st = ctx.run(T, Q, params)
+        assert_same(got, st, ref)
+    # device output buffer
+    out = torch.zeros((4096, 5), dtype=torch.int32, device="cuda")
+    o, st = ctx.run(torch.from_numpy(Ta).cuda(), torch.from_numpy(Qa).cuda(), params, out=out)
+    assert np.array_equal(o.cpu().numpy(), as_i32(ref.hsps))
+
+
+def test_bad_symbol_is_rejected(pkg, ctx):
+    T = np.frombuffer(b"ACGTNACGT" * 10, np.uint8).copy()
+    with pytest.raises(pkg.SfeError) as e:
+        ctx.run(T, T, pkg.default_params())
+    assert e.value.code == -1
+
+
+def test_small_hsp_capacity_reports_needed_count(pkg, ctx):
+    p = synth.tiny_pair(1)
+    ref = oracle.run(p.T, p.Q)
+    got, st = ctx.run(p.T, p.Q, pkg.default_params(input_codes=1), cap=3)  # retries on overflow
+    assert np.array_equal(as_i32(got), as_i32(ref.hsps))
+
+
+def test_seed_hits_api(pkg, ctx):
+    T, Q = _pair(21, 12_000, 9_000)
+    ix = ctx.index_build(T, pkg.default_params(input_codes=1))
+    hits = ctx.seed_hits(ix, Q, strands=3)
+    for s, Qs in ((0, Q), (1, bf.revcomp(Q))):
+        t, q = oracle.seed_hits(T, Qs)
+        h = hits[hits["strand"] == s]
+        assert np.array_equal(h["tpos"], t) and np.array_equal(h["qpos"], q)
+    ix.close()
+
+
+def test_ungapped_xdrop_api_on_shuffled_oracle_hits(pkg, ctx):
+    T, Q = _pair(22, 15_000, 11_000)
+    ix = ctx.index_build(T, pkg.default_params(input_codes=1))
+    recs = []
+    for s, Qs in ((0, Q), (1, bf.revcomp(Q))):
+        t, q = oracle.seed_hits(T, Qs)
+        recs.append(np.stack([np.full(t.size, s), t, q], 1))
+    H = np.concatenate(recs).astype(np.int32)
+    H = H[synth.Stream(3, "perm").integers(0, 1 << 30, H.shape[0]).argsort(kind="stable")]
+    got, st = ctx.ungapped_xdrop(ix, Q, np.ascontiguousarray(H), oracle.HOXD70, 910, 3000)
+    ref = oracle.run(T, Q)
+    assert_same(got, st, ref)
+    ix.close()
