@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Throughput of the filter stage (spaced-seed hits -> per-diagonal skip ->
+ungapped X-drop -> sorted HSPs) on one or more GB300s.
+
+One step = one whole pass of the stage over the 10 Mb x 10 Mb plain workload
+(41% GC, 5% repeats, 2000 planted blocks, both strands, 12of19 seed with one
+transition, HOXD70, X = 910, threshold 3000): pack, index build, hit count and
+write, diagonal grouping, lane and warp walks, HSP sort. Inputs (ASCII bytes)
+are resident in HBM when the timed region starts; each step is timed with CUDA
+events on the library's stream, with a 256 MiB write between steps to flush L2.
+
+Prints one JSON line (rank 0). `value` is GCUPS: the oracle-defined cells
+(seed span plus bases scored on both sides of every extended hit) per second.
+`--impl reference` times the CPU oracle instead on a bounded sample of the
+same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ungapped X-drop GCUPS (oracle-defined cells/s), HSPs/s and hits/s"
+WORKLOAD = "plain_pair_10mb"
+OPS_PER_CELL = 4  # score lookup, add, running max, X-drop compare
+L2_FLUSH_BYTES = 256 << 20
+
+
+def args_parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sfe", choices=["sfe", "reference"])
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = 10 Mb)")
+    ap.add_argument("--lane-cap", type=int, default=0)
+    ap.add_argument("--tile-hits", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target CPU time of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------- helpers
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0)),
+                "source": "measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+def alu_peak_tops(sm_count: int, sm_mhz: float) -> float:
+    """Issue-limited int32 peak: every SM issues one warp instruction per clock on each
+    of its 4 sub-partitions, 32 lanes each (128 lane-ops per SM per clock)."""
+    return sm_count * 128 * sm_mhz * 1e6 / 1e12
+
+
+def kernel_traffic(kernel: str) -> float | None:
+    """DRAM bytes per launch from the committed ncu summary of `kernel`, if the kernel's
+    source has not changed since (the summary records the source hash)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_plain_pair_10mb.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
+    t = re.search(r"dram_bytes_per_launch_full:\s*([0-9.eE+]+)", txt)
+    src = os.path.join(ROOT, "paper_2606_06811_gb300", "csrc", "xdrop.cu")
+    if not (m and t and os.path.exists(src)):
+        return None
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != m.group(1):
+        return None
+    return float(t.group(1))
+
+
+# ------------------------------------------------------------ workloads
+
+def make_workload(seed: int, scale: float):
+    import synth
+    pair = synth.plain_pair_10mb(seed, scale=scale)
+    return pair, np.frombuffer(synth.decode(pair.T), np.uint8), np.frombuffer(
+        synth.decode(pair.Q), np.uint8)
+
+
+def oracle_sample(pair, seconds: float):
+    """Time the CPU oracle, as it stands, on the full target against a query prefix
+    sized so the run takes about `seconds`. Returns (cells, hsps, hits, secs, qlen)."""
+    import oracle
+    qlen = min(pair.qlen, 20_000)
+    while True:
+        t0 = time.perf_counter()
+        r = oracle.run(pair.T, pair.Q[:qlen])
+        dt = time.perf_counter() - t0
+        if dt >= 0.6 * seconds or qlen >= pair.qlen:
+            return r.cells, int(r.hsps.size), r.hits, dt, qlen
+        grow = max(2.0, 0.9 * seconds / max(dt, 1e-3))
+        qlen = int(min(pair.qlen, qlen * grow))
+
+
+# ------------------------------------------------------------------ arms
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return 0
+    pair, _, _ = make_workload(a.seed, a.scale)
+    per = max(2.0, a.cpu_seconds / max(1, a.steps + a.warmup))
+    cells = hsps = hits = 0
+    secs = 0.0
+    qlen = 0
+    for i in range(a.warmup + a.steps):
+        c, h, ht, dt, qlen = oracle_sample(pair, per)
+        if i >= a.warmup:
+            cells += c
+            hsps += h
+            hits += ht
+            secs += dt
+    gcups = cells / secs / 1e9
+    sample = (f"full {pair.tlen:,} bp target x {qlen:,} bp query prefix of {WORKLOAD}, "
+              "both strands, per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gcups, "unit": "GCUPS",
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": secs / a.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "tlen": pair.tlen, "qlen_sample": qlen,
+                   "seed_pattern": "1110100110010101111", "transition": 1, "strands": 2,
+                   "xdrop": 910, "hsp_thresh": 3000},
+        "hsps_per_s": hsps / secs, "hits_per_s": hits / secs,
+        "cpu_baseline": {"value": gcups, "unit": "GCUPS", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": gcups, "unit": "GCUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_sfe(a, rank, world, local):
+    import torch
+    import paper_2606_06811_gb300 as pkg
+    from paper_2606_06811_gb300 import build as cuda_build
+
+    cuda_build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    pair, Ta, Qa = make_workload(a.seed, a.scale)
+    T = torch.from_numpy(Ta.copy()).to(dev)
+    Q = torch.from_numpy(Qa.copy()).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = pkg.Context(local, stream=stream)
+    params = pkg.default_params(flags=pkg.TIME_STAGES, lane_cap=a.lane_cap,
+                                tile_hits=a.tile_hits)
+    cap = 1 << 22
+    out = torch.zeros((cap, 5), dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    def step():
+        with torch.cuda.stream(stream):
+            flush.fill_(1)  # evicts L2 between steps, outside the events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hs, st = ctx.run(T, Q, params, out=out)
+        e1.record(stream)
+        return e0, e1, st, int(hs.shape[0])
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    recs = [step() for _ in range(a.steps)]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - w0
+    clk = clocks.stop()
+
+    step_ms = [e0.elapsed_time(e1) for e0, e1, _, _ in recs]
+    total_ms = float(sum(step_ms))
+    stats = [st for _, _, st, _ in recs]
+    cells = sum(s["cells"] for s in stats)
+    hsps = sum(n for *_, n in recs)
+    hits = sum(s["hits"] for s in stats)
+    launches = sum(s["launches"] for s in stats)
+    stage_ms = {k: sum(s["stage_ms"][k] for s in stats) / a.steps for k in pkg.STAGES}
+    stage_launch = {k: sum(s["stage_launches"][k] for s in stats) / a.steps for k in pkg.STAGES}
+
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        tot = torch.tensor([cells, hsps, hits], dtype=torch.float64, device=dev)
+        dist.all_reduce(tot)
+        cells, hsps, hits = (float(x) for x in tot.tolist())
+
+    secs = total_ms / 1e3
+    gcups = cells / secs / 1e9
+    s0 = stats[0]
+
+    # dominant kernel: the lane walk (skip + X-drop), integer-ALU bound
+    peaks = measured_peaks()
+    lane_ms = stage_ms["walk_lanes"] / max(1.0, stage_launch["walk_lanes"])
+    lane_cells = (s0["cells"] - s0["warp_cells"]) / max(1.0, stage_launch["walk_lanes"])
+    achieved = lane_cells * OPS_PER_CELL / (lane_ms / 1e3) / 1e12
+    peak = alu_peak_tops(sm_count, peaks["sm_max_mhz"])
+    roofline = {"kernel": "walk_lanes_kernel", "bound": "alu", "achieved": achieved,
+                "peak": peak, "unit": "Tops/s (int32)", "frac": achieved / peak,
+                "traffic": kernel_traffic("walk_lanes"),
+                "peak_source": (f"{sm_count} SMs x 128 int32 lanes/clk x "
+                                f"{peaks['sm_max_mhz']:.0f} MHz (issue limit)"),
+                "ops_per_cell": OPS_PER_CELL,
+                "ms_per_launch": lane_ms, "launches_per_step": stage_launch["walk_lanes"]}
+    dom = max(stage_ms, key=stage_ms.get)
+
+    line = {
+        "metric": METRIC, "value": gcups, "unit": "GCUPS", "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_ms / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "tlen": pair.tlen, "qlen": pair.qlen,
+                   "seed_pattern": "1110100110010101111", "transition": 1, "strands": 2,
+                   "scores": "HOXD70", "xdrop": 910, "hsp_thresh": 3000,
+                   "lane_cap": a.lane_cap or "default", "parallelism": f"replicas{world}",
+                   "l2": "256 MiB write between steps, outside the per-step events",
+                   "input": "ASCII bytes resident in HBM"},
+        "hsps_per_s": hsps / secs, "hits_per_s": hits / secs,
+        "per_step": {"cells": s0["cells"], "hits": s0["hits"], "extended": s0["extended"],
+                     "hsps": recs[0][3], "warp_tasks": s0["warp_tasks"],
+                     "warp_cells": s0["warp_cells"], "tiles": s0["tiles"]},
+        "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+        "dominant_stage": dom,
+        "roofline": roofline,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "wall_s": wall,
+    }
+
+    if not a.no_e2e:
+        Th = torch.from_numpy(Ta.copy()).pin_memory()
+        Qh = torch.from_numpy(Qa.copy()).pin_memory()
+        hout = np.zeros(cap, dtype=pkg.HSP_DTYPE)
+        pe = pkg.default_params(lane_cap=a.lane_cap, tile_hits=a.tile_hits)
+        ctx.run(Th, Qh, pe, out=hout)  # warm the host path
+        ts = []
+        e_cells = 0
+        nh = 0
+        for _ in range(a.steps):
+            t0 = time.perf_counter()
+            hs, st = ctx.run(Th, Qh, pe, out=hout)  # H2D inside, HSPs read back to host
+            ts.append(time.perf_counter() - t0)
+            e_cells += st["cells"]
+            nh = int(hs.shape[0])
+        line["e2e"] = {"value": e_cells / sum(ts) / 1e9, "unit": "GCUPS",
+                       "h2d_bytes_per_step": int(Ta.size + Qa.size),
+                       "d2h_bytes_per_step": int(nh * 20 + 8 * 24),
+                       "path": "sfe_run with pinned host buffers (host wall clock)"}
+
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        c, h, ht, dt, qlen = oracle_sample(pair, a.cpu_seconds)
+        line["cpu_baseline"] = {
+            "value": c / dt / 1e9, "unit": "GCUPS", "cores": 1, "kind": "oracle",
+            "sample": f"full {pair.tlen:,} bp target x {qlen:,} bp query prefix, both strands, "
+                      f"{dt:.1f} s single-threaded"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = args_parse()
+    rank, world, local = dist_env()
+    if a.impl == "reference":
+        return run_reference(a, rank, world)
+    return run_sfe(a, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -59,6 +59,21 @@ extern "C" {
 
 /* sfe_params.flags */
 #define SFE_SKIP_PASSING_ONLY 1 /* advance E only for HSPs with score >= hsp_thresh */
+#define SFE_TIME_STAGES 2       /* time each stage with CUDA events on the context's stream */
+
+/* Stages of a call, indexes of sfe_stats.stage_ms / stage_launches. */
+enum {
+    SFE_STAGE_PACK = 0,       /* 2-bit packing and reverse complement */
+    SFE_STAGE_INDEX = 1,      /* spaced keys, radix sort, CSR table */
+    SFE_STAGE_COUNT = 2,      /* hits per query position and their scan */
+    SFE_STAGE_WRITE = 3,      /* hit records */
+    SFE_STAGE_SORT = 4,       /* grouping of hits by diagonal */
+    SFE_STAGE_SEGMENTS = 5,   /* diagonal segment heads */
+    SFE_STAGE_WALK_LANES = 6, /* skip + X-drop, one lane per diagonal */
+    SFE_STAGE_WALK_WARPS = 7, /* skip + X-drop, one warp per handed-off diagonal */
+    SFE_STAGE_OUTPUT = 8,     /* HSP sort and copy-out */
+    SFE_NSTAGES = 9
+};
 
 typedef struct sfe_ctx sfe_ctx;
 typedef struct sfe_index sfe_index;
@@ -88,7 +103,7 @@ typedef struct {
     int32_t flags;            /* SFE_SKIP_PASSING_ONLY */
     int32_t input_codes;      /* 0: ASCII ACGTacgt, 1: codes 0..3 */
     int32_t lane_cap;         /* bases per side a lane extends before handing the diagonal to a warp; 0 = default */
-    int32_t reserved;
+    int32_t lanes_per_sm;     /* lane-tier threads per SM sharing a tile's hits (sizes their hit ranges); 0 = default */
     int64_t tile_hits;        /* hits per query tile (bounds scratch memory); 0 = default */
 } sfe_params;
 
@@ -101,8 +116,11 @@ typedef struct {
     int64_t hsps;       /* HSPs with score >= hsp_thresh */
     int64_t lane_tasks; /* diagonals walked by single lanes */
     int64_t warp_tasks; /* diagonals handed to whole warps */
+    int64_t warp_cells; /* cells scored by the warp tier (the rest by lanes) */
     int64_t tiles;      /* query tiles processed */
-    int64_t reserved;
+    int64_t launches;   /* kernels this call launched */
+    double stage_ms[SFE_NSTAGES];        /* device time per stage (with SFE_TIME_STAGES) */
+    int64_t stage_launches[SFE_NSTAGES]; /* kernels launched per stage (with SFE_TIME_STAGES) */
 } sfe_stats;
 
 /* Fill *p with the defaults: 12of19 with one transition, both strands,

@@ -11,6 +11,8 @@
 
 using namespace sfe;
 
+unsigned long long sfe::g_launches = 0;
+
 namespace {
 
 thread_local std::string g_err;
@@ -46,7 +48,7 @@ constexpr unsigned long long kQueueMax = 1ull << 22;
 
 enum Slot {
     SL_TIN, SL_QIN, SL_TP, SL_QP, SL_QM, SL_KEYS_A, SL_KEYS_B, SL_BCOUNT, SL_OFFS, SL_POS,
-    SL_COUNTS, SL_STARTS, SL_HITS_A, SL_HITS_B, SL_FLAGS, SL_SEGSCAN, SL_SEGSTART, SL_QUEUE,
+    SL_COUNTS, SL_STARTS, SL_HITS_A, SL_HITS_B, SL_QUEUE,
     SL_HSPS, SL_TMP, SL_ECARRY, SL_PUB, SL_BOUNDS, NSLOT
 };
 
@@ -68,6 +70,19 @@ int bits_for(long long v) {
 
 }  // namespace
 
+// CUDA-event spans of the stages of one call (SFE_TIME_STAGES).
+struct StageTimer {
+    struct Span {
+        int stage;
+        cudaEvent_t a, b;
+        unsigned long long l0, l1;
+    };
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    std::vector<Span> spans;
+};
+
 struct sfe_ctx {
     int device = 0;
     cudaStream_t own = nullptr;
@@ -76,6 +91,8 @@ struct sfe_ctx {
     size_t cap[NSLOT] = {};
     Small *small = nullptr;       // device
     Small *host_small = nullptr;  // pinned mirror
+    StageTimer tm;
+    unsigned long long launches0 = 0;
 };
 
 struct sfe_index {
@@ -121,6 +138,38 @@ int ensure_t(sfe_ctx *c, int slot, size_t count, T **out) {
     return SFE_OK;
 }
 
+cudaEvent_t next_event(sfe_ctx *c) {
+    StageTimer &t = c->tm;
+    if (t.used < t.pool.size()) return t.pool[t.used++];
+    if (t.pool.size() >= 8192) return nullptr;
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    t.pool.push_back(e);
+    t.used++;
+    return e;
+}
+
+// RAII span: events recorded on the context's stream around one stage.
+struct Span {
+    sfe_ctx *c;
+    int stage;
+    cudaEvent_t a = nullptr;
+    unsigned long long l0;
+    Span(sfe_ctx *ctx, int s) : c(ctx), stage(s), l0(g_launches) {
+        if (c->tm.on && (a = next_event(c))) cudaEventRecord(a, c->st);
+    }
+    ~Span() {
+        if (!a) return;
+        cudaEvent_t b = next_event(c);
+        if (!b) return;
+        cudaEventRecord(b, c->st);
+        c->tm.spans.push_back({stage, a, b, l0, g_launches});
+    }
+};
+
 bool is_device_ptr(const void *p) {
     if (!p) return false;
     cudaPointerAttributes a;
@@ -153,6 +202,7 @@ int check_params(const sfe_params *p) {
     if (p->xdrop < 0 || p->xdrop >= (1 << 30)) return fail(SFE_EINVAL, "xdrop must be in [0, 2^30)");
     if (p->strands < 1 || p->strands > 3) return fail(SFE_EINVAL, "strands must be 1, 2 or 3");
     if (p->lane_cap < 0) return fail(SFE_EINVAL, "lane_cap must be >= 0");
+    if (p->lanes_per_sm < 0) return fail(SFE_EINVAL, "lanes_per_sm must be >= 0");
     if (p->tile_hits < 0) return fail(SFE_EINVAL, "tile_hits must be >= 0");
     if (p->input_codes != 0 && p->input_codes != 1) return fail(SFE_EINVAL, "input_codes must be 0 or 1");
     for (int i = 0; i < 16; i++)
@@ -167,9 +217,13 @@ int check_len(long long n, const char *what) {
     return SFE_OK;
 }
 
-int begin(sfe_ctx *c) {
+int begin(sfe_ctx *c, int flags = 0) {
     if (!c) return fail(SFE_EINVAL, "context is NULL");
     CK(cudaSetDevice(c->device));
+    c->tm.on = (flags & SFE_TIME_STAGES) != 0;
+    c->tm.used = 0;
+    c->tm.spans.clear();
+    c->launches0 = g_launches;
     CK(cudaMemsetAsync(c->small, 0, sizeof(Small), c->st));
     return SFE_OK;
 }
@@ -222,6 +276,7 @@ int check_status(uint32_t st) {
     if (st & ST_BAD_SYMBOL) return fail(SFE_EINVAL, "sequence holds a symbol outside ACGTacgt");
     if (st & ST_BAD_HIT) return fail(SFE_EINVAL, "a hit's seed span leaves the sequences");
     if (st & ST_SCORE_OVERFLOW) return fail(SFE_EOVERFLOW, "an HSP score left the int32 range");
+    if (st & ST_TIMEOUT) return fail(SFE_ETIMEOUT, "a bounded device wait ran out");
     return SFE_OK;
 }
 
@@ -250,7 +305,7 @@ int build_index(sfe_ctx *c, const uint32_t *T, long long tlen, const SeedPattern
         TRY(ensure_t(c, SL_KEYS_B, (size_t)npos, &kb));
         CK(launch_seed_keys(T, tlen, pat, ka, c->st));
         bool in_b = false;
-        CK(radix_sort(ka, kb, nullptr, nullptr, npos, 32, 32 + 2 * pat.weight, tmp, &in_b, c->st));
+        CK(radix_sort(ka, kb, nullptr, nullptr, npos, 32, 32 + 2 * pat.weight, tmp, &in_b, &c->small->status, c->st));
         CK(launch_csr_counts(in_b ? kb : ka, npos, counts, pos, c->st));
     }
     CK(scan_u32_to_u32(counts, offs, nbuckets, tmp, c->st));
@@ -337,20 +392,12 @@ struct WalkSetup {
     unsigned long long hsp_cap;
 };
 
-// Segments of hits sorted by (diagonal, t), then the lane and warp walks.
+// Lane and warp walks of hits sorted by (diagonal, t).
 int walk_sorted(sfe_ctx *c, const uint64_t *hits, long long n, const WalkSetup &ws) {
     if (n <= 0) return SFE_OK;
-    uint32_t *flags = nullptr, *seg_start = nullptr;
-    unsigned long long *segscan = nullptr;
     uint4 *queue = nullptr;
-    void *tmp = nullptr;
-    TRY(ensure_t(c, SL_FLAGS, (size_t)n, &flags));
-    TRY(ensure_t(c, SL_SEGSCAN, (size_t)n + 1, &segscan));
-    TRY(ensure_t(c, SL_SEGSTART, (size_t)n + 1, &seg_start));
     const unsigned long long qcap = std::min<unsigned long long>((unsigned long long)n, kQueueMax);
     TRY(ensure_t(c, SL_QUEUE, (size_t)qcap, &queue));
-    TRY(ensure(c, SL_TMP, segments_temp_bytes(n), &tmp));
-    CK(launch_segments(hits, n, flags, segscan, seg_start, tmp, c->st));
     CK(cudaMemsetAsync(&c->small->queue_len, 0, 4, c->st));
     WalkParams wp;
     wp.T = ws.T;
@@ -372,8 +419,14 @@ int walk_sorted(sfe_ctx *c, const uint64_t *hits, long long n, const WalkSetup &
     wp.queue = queue;
     wp.queue_cap = qcap;
     wp.queue_len = &c->small->queue_len;
-    CK(launch_walk_lanes(hits, seg_start, segscan + n, n, wp, c->st));
-    CK(launch_walk_warps(hits, seg_start, wp, 0, c->st));
+    {
+        Span sp(c, SFE_STAGE_WALK_LANES);
+        CK(launch_walk_lanes(hits, n, wp, ws.p->lanes_per_sm, c->st));
+    }
+    {
+        Span sp(c, SFE_STAGE_WALK_WARPS);
+        CK(launch_walk_warps(hits, n, wp, 0, c->st));
+    }
     return SFE_OK;
 }
 
@@ -385,7 +438,7 @@ int finish_hsps(sfe_ctx *c, Hsp *dev, unsigned long long found, long long tlen, 
     if (found == 0) return SFE_OK;
     void *tmp = nullptr;
     TRY(ensure(c, SL_TMP, hsp_sort_temp_bytes((long long)found), &tmp));
-    CK(hsp_sort(dev, (long long)found, bits_for(tlen), bits_for(qlen), tmp, c->st));
+    CK(hsp_sort(dev, (long long)found, bits_for(tlen), bits_for(qlen), tmp, &c->small->status, c->st));
     const bool dev_out = is_device_ptr(out);
     CK(cudaMemcpyAsync(out, dev, found * sizeof(Hsp),
                        dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st));
@@ -402,7 +455,21 @@ void fill_stats(const Small &s, sfe_stats *st, long long hits, long long tiles) 
     st->hsps = (int64_t)s.ctr.hsps;
     st->lane_tasks = (int64_t)s.ctr.lane_tasks;
     st->warp_tasks = (int64_t)s.ctr.warp_tasks;
+    st->warp_cells = (int64_t)s.ctr.warp_cells;
     st->tiles = tiles;
+}
+
+// Stage times and launch counts (after the stream has been synchronised).
+void add_timings(sfe_ctx *c, sfe_stats *st) {
+    if (!st) return;
+    st->launches = (int64_t)(g_launches - c->launches0);
+    for (const auto &sp : c->tm.spans) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, sp.a, sp.b) == cudaSuccess) st->stage_ms[sp.stage] += ms;
+        else cudaGetLastError();
+        st->stage_launches[sp.stage] += (int64_t)(sp.l1 - sp.l0);
+    }
+    c->tm.spans.clear();
 }
 
 int upload_scores(sfe_ctx *c, const int32_t *scores) {
@@ -478,6 +545,7 @@ void sfe_ctx_destroy(sfe_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->st);
+    for (cudaEvent_t e : c->tm.pool) cudaEventDestroy(e);
     for (int i = 0; i < NSLOT; i++)
         if (c->buf[i]) cudaFreeAsync(c->buf[i], c->st);
     cudaStreamSynchronize(c->st);
@@ -594,7 +662,7 @@ int sfe_seed_hits(sfe_ctx *c, const sfe_index *ix, const uint8_t *query, int64_t
         hp.qoff = qlen - v.pat.span;
         CK(launch_hit_write(s ? Qm : Qp, hp, v.offs, v.pos, 0, nq, starts, 0, ha, c->st));
         bool in_b = false;
-        CK(radix_sort(ha, hb, nullptr, nullptr, (long long)t2, 32, 32 + DB, tmp, &in_b, c->st));
+        CK(radix_sort(ha, hb, nullptr, nullptr, (long long)t2, 32, 32 + DB, tmp, &in_b, &c->small->status, c->st));
         CK(launch_hits_to_public(in_b ? hb : ha, (long long)t2, s, hp.qoff, dst + at, c->st));
         at += t2;
     }
@@ -641,13 +709,16 @@ int sfe_ungapped_xdrop(sfe_ctx *c, const sfe_index *ix, const uint8_t *query, in
     const int DB = bits_for(v.tlen + qlen);
     uint64_t *cur = ha, *oth = hb;
     bool in_b = false;
-    CK(radix_sort(cur, oth, nullptr, nullptr, nhits, 0, TB, tmp, &in_b, c->st));
+    CK(radix_sort(cur, oth, nullptr, nullptr, nhits, 0, TB, tmp, &in_b, &c->small->status, c->st));
     if (in_b) std::swap(cur, oth);
-    CK(radix_sort(cur, oth, nullptr, nullptr, nhits, 32, 32 + DB, tmp, &in_b, c->st));
+    CK(radix_sort(cur, oth, nullptr, nullptr, nhits, 32, 32 + DB, tmp, &in_b, &c->small->status, c->st));
     if (in_b) std::swap(cur, oth);
-    CK(radix_sort(cur, oth, nullptr, nullptr, nhits, 63, 64, tmp, &in_b, c->st));
+    CK(radix_sort(cur, oth, nullptr, nullptr, nhits, 63, 64, tmp, &in_b, &c->small->status, c->st));
     if (in_b) std::swap(cur, oth);
-    if (nhits > 0) strand_split_kernel<<<1, 1, 0, c->st>>>(cur, nhits, &c->small->split);
+    if (nhits > 0) {
+        g_launches++;
+        strand_split_kernel<<<1, 1, 0, c->st>>>(cur, nhits, &c->small->split);
+    }
     CK(cudaGetLastError());
     TRY(sync_small(c));
     const long long split = nhits > 0 ? (long long)c->host_small->split : 0;
@@ -668,7 +739,9 @@ int sfe_ungapped_xdrop(sfe_ctx *c, const sfe_index *ix, const uint8_t *query, in
     Small sm = *c->host_small;
     TRY(check_status(sm.ctr.status));
     fill_stats(sm, stats, nhits, 1);
-    return finish_hsps(c, hd, sm.ctr.hsps, v.tlen, qlen, hsps, cap, nhsps);
+    int r = finish_hsps(c, hd, sm.ctr.hsps, v.tlen, qlen, hsps, cap, nhsps);
+    add_timings(c, stats);
+    return r;
 }
 
 int sfe_run(sfe_ctx *c, const uint8_t *target, int64_t tlen, const uint8_t *query, int64_t qlen,
@@ -680,20 +753,28 @@ int sfe_run(sfe_ctx *c, const uint8_t *target, int64_t tlen, const uint8_t *quer
     TRY(check_len(qlen, "query"));
     SeedPattern pat;
     TRY(parse_pattern(params->seed_pattern, &pat));
-    TRY(begin(c));
+    TRY(begin(c, params->flags));
     TRY(upload_scores(c, params->scores));
-    const void *tdev = nullptr, *qdev = nullptr;
-    TRY(stage(c, SL_TIN, target, (size_t)tlen, &tdev));
-    TRY(stage(c, SL_QIN, query, (size_t)qlen, &qdev));
     uint32_t *Tp = nullptr, *Qp = nullptr, *Qm = nullptr;
-    TRY(pack_slot(c, SL_TP, reinterpret_cast<const uint8_t *>(tdev), tlen, params->input_codes, &Tp));
-    TRY(pack_slot(c, SL_QP, reinterpret_cast<const uint8_t *>(qdev), qlen, params->input_codes, &Qp));
-    if (params->strands & 2) TRY(rc_slot(c, SL_QM, Qp, qlen, &Qm));
+    {
+        Span sp(c, SFE_STAGE_PACK);
+        const void *tdev = nullptr, *qdev = nullptr;
+        TRY(stage(c, SL_TIN, target, (size_t)tlen, &tdev));
+        TRY(stage(c, SL_QIN, query, (size_t)qlen, &qdev));
+        TRY(pack_slot(c, SL_TP, reinterpret_cast<const uint8_t *>(tdev), tlen, params->input_codes,
+                      &Tp));
+        TRY(pack_slot(c, SL_QP, reinterpret_cast<const uint8_t *>(qdev), qlen, params->input_codes,
+                      &Qp));
+        if (params->strands & 2) TRY(rc_slot(c, SL_QM, Qp, qlen, &Qm));
+    }
     const long long npos = std::max(0LL, (long long)tlen - pat.span + 1);
     uint32_t *offs = nullptr, *pos = nullptr;
     TRY(ensure_t(c, SL_OFFS, (size_t)(1LL << (2 * pat.weight)) + 1, &offs));
     TRY(ensure_t(c, SL_POS, (size_t)std::max(1LL, npos), &pos));
-    TRY(build_index(c, Tp, tlen, pat, offs, pos));
+    {
+        Span sp(c, SFE_STAGE_INDEX);
+        TRY(build_index(c, Tp, tlen, pat, offs, pos));
+    }
     IndexView v{Tp, tlen, pat, params->transition, offs, pos};
 
     const long long tile_hits = params->tile_hits > 0 ? params->tile_hits : kDefaultTileHits;
@@ -711,7 +792,10 @@ int sfe_run(sfe_ctx *c, const uint8_t *target, int64_t tlen, const uint8_t *quer
             const uint32_t *Qs = s ? Qm : Qp;
             unsigned long long *starts = nullptr, total = 0;
             long long nq = 0;
-            TRY(count_hits(c, v, Qs, qlen, &starts, &nq, &total));
+            {
+                Span sp(c, SFE_STAGE_COUNT);
+                TRY(count_hits(c, v, Qs, qlen, &starts, &nq, &total));
+            }
             hits_total += (long long)total;
             if (total == 0) continue;
             // query tiles of at most ~tile_hits hits each
@@ -727,6 +811,7 @@ int sfe_run(sfe_ctx *c, const uint8_t *target, int64_t tlen, const uint8_t *quer
                 long long *bd = nullptr;
                 TRY(ensure_t(c, SL_BOUNDS, (size_t)(2 * (ntiles + 1)), &bd));
                 unsigned long long *bs = reinterpret_cast<unsigned long long *>(bd + ntiles + 1);
+                g_launches++;
                 tile_bounds_kernel<<<(unsigned)((ntiles + 1 + 255) / 256), 256, 0, c->st>>>(
                     starts, nq, (unsigned long long)tile_hits, ntiles, bd, bs);
                 CK(cudaGetLastError());
@@ -757,10 +842,16 @@ int sfe_run(sfe_ctx *c, const uint8_t *target, int64_t tlen, const uint8_t *quer
                 const long long nh = (long long)(hb[k + 1] - hb[k]);
                 if (nh == 0) continue;
                 tiles_total++;
-                CK(launch_hit_write(Qs, hp, offs, pos, qb[k], qb[k + 1], starts + qb[k], hb[k], ha,
-                                    c->st));
+                {
+                    Span sp(c, SFE_STAGE_WRITE);
+                    CK(launch_hit_write(Qs, hp, offs, pos, qb[k], qb[k + 1], starts + qb[k], hb[k],
+                                        ha, c->st));
+                }
                 bool in_b = false;
-                CK(radix_sort(ha, hbuf, nullptr, nullptr, nh, 32, 32 + DB, tmp, &in_b, c->st));
+                {
+                    Span sp(c, SFE_STAGE_SORT);
+                    CK(radix_sort(ha, hbuf, nullptr, nullptr, nh, 32, 32 + DB, tmp, &in_b, &c->small->status, c->st));
+                }
                 WalkSetup ws{Tp, tlen, Qs, qlen, s, pat.span, params, Ecarry, hd, hcap};
                 TRY(walk_sorted(c, in_b ? hbuf : ha, nh, ws));
             }
@@ -772,7 +863,14 @@ int sfe_run(sfe_ctx *c, const uint8_t *target, int64_t tlen, const uint8_t *quer
     Small sm = *c->host_small;
     TRY(check_status(sm.status | sm.ctr.status));
     fill_stats(sm, stats, hits_total, tiles_total);
-    return finish_hsps(c, hd, sm.ctr.hsps, tlen, qlen, hsps, cap, nhsps);
+    int r;
+    {
+        Span sp(c, SFE_STAGE_OUTPUT);
+        r = finish_hsps(c, hd, sm.ctr.hsps, tlen, qlen, hsps, cap, nhsps);
+    }
+    CK(cudaStreamSynchronize(c->st));
+    add_timings(c, stats);
+    return r;
 }
 
 }  // extern "C"

@@ -23,6 +23,25 @@ __device__ __forceinline__ uint32_t spaced_key(const uint32_t *__restrict__ S, l
     return k;
 }
 
+constexpr int MAX_PROBES = MAX_WEIGHT + 1;
+
+// Bucket bounds of every probe of query position q, loaded together so the
+// independent CSR reads overlap. Probe 0 is the exact key, probe i > 0 flips
+// care position i - 1 to its transition partner.
+__device__ __forceinline__ int probe_bounds(const uint32_t *__restrict__ Qs, long long q,
+                                            const HitParams &hp, const uint32_t *__restrict__ off,
+                                            uint32_t (&a)[MAX_PROBES], uint32_t (&b)[MAX_PROBES]) {
+    const uint32_t k = spaced_key(Qs, q, hp.pat);
+    const int nprobe = hp.transition ? hp.pat.weight + 1 : 1;
+#pragma unroll
+    for (int i = 0; i < MAX_PROBES; i++) {
+        const uint32_t pk = i == 0 ? k : k ^ (2u << (2 * (i - 1)));
+        a[i] = i < nprobe ? __ldg(off + pk) : 0u;
+        b[i] = i < nprobe ? __ldg(off + pk + 1) : 0u;
+    }
+    return nprobe;
+}
+
 __global__ void __launch_bounds__(BLOCK) hit_count_kernel(const uint32_t *__restrict__ Qs,
                                                           HitParams hp,
                                                           const uint32_t *__restrict__ off,
@@ -30,17 +49,16 @@ __global__ void __launch_bounds__(BLOCK) hit_count_kernel(const uint32_t *__rest
                                                           uint32_t *__restrict__ counts) {
     long long q = q0 + blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (q >= q1) return;
-    uint32_t k = spaced_key(Qs, q, hp.pat);
-    uint32_t c = __ldg(off + k + 1) - __ldg(off + k);
-    if (hp.transition) {
-        for (int i = 0; i < hp.pat.weight; i++) {
-            uint32_t pk = k ^ (2u << (2 * i));
-            c += __ldg(off + pk + 1) - __ldg(off + pk);
-        }
-    }
+    uint32_t a[MAX_PROBES], b[MAX_PROBES];
+    probe_bounds(Qs, q, hp, off, a, b);
+    uint32_t c = 0;
+#pragma unroll
+    for (int i = 0; i < MAX_PROBES; i++) c += b[i] - a[i];
     counts[q - q0] = c;
 }
 
+// Hits go out with evict-first stores: the stream of hit records must not push
+// the CSR table out of L2.
 __global__ void __launch_bounds__(BLOCK) hit_write_kernel(
     const uint32_t *__restrict__ Qs, HitParams hp, const uint32_t *__restrict__ off,
     const uint32_t *__restrict__ pos, long long q0, long long q1,
@@ -48,16 +66,16 @@ __global__ void __launch_bounds__(BLOCK) hit_write_kernel(
     uint64_t *__restrict__ hits) {
     long long q = q0 + blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (q >= q1) return;
-    uint32_t k = spaced_key(Qs, q, hp.pat);
+    uint32_t a[MAX_PROBES], b[MAX_PROBES];
+    probe_bounds(Qs, q, hp, off, a, b);
     unsigned long long o = starts[q - q0] - base;
     const long long dq = hp.qoff - q;  // D = t + dq
-    int nprobe = hp.transition ? hp.pat.weight + 1 : 1;
-    for (int i = 0; i < nprobe; i++) {
-        uint32_t pk = i == 0 ? k : k ^ (2u << (2 * (i - 1)));
-        uint32_t a = __ldg(off + pk), b = __ldg(off + pk + 1);
-        for (uint32_t j = a; j < b; j++) {
-            uint32_t t = __ldg(pos + j);
-            hits[o++] = make_hit((uint32_t)(t + dq), t);
+#pragma unroll
+    for (int i = 0; i < MAX_PROBES; i++) {  // unused probes have empty buckets
+        for (uint32_t j = a[i]; j < b[i]; j++) {
+            const uint32_t t = __ldg(pos + j);
+            __stcs(reinterpret_cast<unsigned long long *>(hits) + o++,
+                   (unsigned long long)make_hit((uint32_t)(t + dq), t));
         }
     }
 }
@@ -69,6 +87,7 @@ inline unsigned grid_for(long long n) { return (unsigned)((n + BLOCK - 1) / BLOC
 cudaError_t launch_hit_count(const uint32_t *Qs, HitParams hp, const uint32_t *offsets,
                              long long q0, long long q1, uint32_t *counts, cudaStream_t st) {
     if (q1 <= q0) return cudaSuccess;
+    g_launches++;
     hit_count_kernel<<<grid_for(q1 - q0), BLOCK, 0, st>>>(Qs, hp, offsets, q0, q1, counts);
     return cudaGetLastError();
 }
@@ -78,6 +97,7 @@ cudaError_t launch_hit_write(const uint32_t *Qs, HitParams hp, const uint32_t *o
                              const unsigned long long *starts, unsigned long long base,
                              uint64_t *hits, cudaStream_t st) {
     if (q1 <= q0) return cudaSuccess;
+    g_launches++;
     hit_write_kernel<<<grid_for(q1 - q0), BLOCK, 0, st>>>(Qs, hp, offsets, positions, q0, q1,
                                                           starts, base, hits);
     return cudaGetLastError();

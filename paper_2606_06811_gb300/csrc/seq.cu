@@ -138,6 +138,7 @@ cudaError_t launch_pack(const uint8_t *src, long long n, int codes, uint32_t *ds
                         uint32_t *status, cudaStream_t st) {
     long long nwords = (n + 15) / 16;
     long long total = nwords + 2 * SEQ_PAD;
+    g_launches++;
     pack_kernel<<<grid_for(total), BLOCK, 0, st>>>(src, n, codes, dst, nwords, status);
     return cudaGetLastError();
 }
@@ -145,6 +146,7 @@ cudaError_t launch_pack(const uint8_t *src, long long n, int codes, uint32_t *ds
 cudaError_t launch_revcomp(const uint32_t *src, long long n, uint32_t *dst, cudaStream_t st) {
     long long nwords = (n + 15) / 16;
     long long total = nwords + 2 * SEQ_PAD;
+    g_launches++;
     revcomp_kernel<<<grid_for(total), BLOCK, 0, st>>>(src, n, dst, nwords);
     return cudaGetLastError();
 }
@@ -153,6 +155,7 @@ cudaError_t launch_seed_keys(const uint32_t *S, long long n, SeedPattern pat, ui
                              cudaStream_t st) {
     long long npos = n - pat.span + 1;
     if (npos <= 0) return cudaSuccess;
+    g_launches++;
     seed_keys_kernel<<<grid_for(npos), BLOCK, 0, st>>>(S, npos, pat, keys);
     return cudaGetLastError();
 }
@@ -160,6 +163,7 @@ cudaError_t launch_seed_keys(const uint32_t *S, long long n, SeedPattern pat, ui
 cudaError_t launch_csr_counts(const uint64_t *sorted, long long m, uint32_t *counts,
                              uint32_t *positions, cudaStream_t st) {
     if (m <= 0) return cudaSuccess;
+    g_launches++;
     csr_count_kernel<<<grid_for(m), BLOCK, 0, st>>>(sorted, m, counts, positions);
     return cudaGetLastError();
 }
@@ -167,6 +171,7 @@ cudaError_t launch_csr_counts(const uint64_t *sorted, long long m, uint32_t *cou
 cudaError_t launch_hits_to_public(const uint64_t *hits, long long n, int strand, long long qoff,
                                   sfe_hit *out, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
+    g_launches++;
     hits_to_public_kernel<<<grid_for(n), BLOCK, 0, st>>>(hits, n, strand, qoff, out);
     return cudaGetLastError();
 }
@@ -174,6 +179,7 @@ cudaError_t launch_hits_to_public(const uint64_t *hits, long long n, int strand,
 cudaError_t launch_public_to_walk(const sfe_hit *in, long long n, long long tlen, long long qlen,
                                   int span, uint64_t *out, uint32_t *status, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
+    g_launches++;
     public_to_walk_kernel<<<grid_for(n), BLOCK, 0, st>>>(in, n, tlen, qlen, span, out, status);
     return cudaGetLastError();
 }

@@ -26,6 +26,7 @@ constexpr uint32_t ST_SCORE_OVERFLOW = 2u;
 constexpr uint32_t ST_HSP_OVERFLOW = 4u;
 constexpr uint32_t ST_QUEUE_OVERFLOW = 8u;
 constexpr uint32_t ST_BAD_HIT = 16u;
+constexpr uint32_t ST_TIMEOUT = 32u;  // a bounded device wait ran out
 
 struct SeedPattern {
     int span;
@@ -40,6 +41,7 @@ struct DevCounters {
     unsigned long long hsps;       // HSPs found (may exceed the HSP buffer)
     unsigned long long lane_tasks;
     unsigned long long warp_tasks; // queue entries
+    unsigned long long warp_cells; // cells scored by the warp tier
     unsigned int status;
     unsigned int pad;
 };
@@ -70,6 +72,10 @@ __device__ __forceinline__ uint32_t base_at(const uint32_t *__restrict__ S, long
 // ------------------------------------------------------------ host launchers
 // All launchers queue work on `st` and return cudaGetLastError().
 
+// Kernels launched by this library since it was loaded (host-side count,
+// incremented at every launch site).
+extern unsigned long long g_launches;
+
 // bytes -> packed words (n bases). codes: 0 = ASCII, 1 = 2-bit codes.
 // dst points at the word of base 0 of a buffer with SEQ_PAD words on each side;
 // the padding is zeroed too. Bad symbols set ST_BAD_SYMBOL in *status.
@@ -85,12 +91,13 @@ cudaError_t launch_seed_keys(const uint32_t *S, long long n, SeedPattern pat, ui
 cudaError_t launch_csr_counts(const uint64_t *sorted, long long m, uint32_t *counts,
                               uint32_t *positions, cudaStream_t st);
 
-// Stable LSD radix sort of n uint64 keys by bits [lo, hi), optional uint32
-// values carried along. Uses (a, b) ping-pong and returns in *result_in_b
-// whether the sorted data ended in the b buffers. tmp: radix_sort_temp_bytes(n).
+// Stable LSD radix sort of n (< 2^32) uint64 keys by bits [lo, hi), optional
+// uint32 values carried along. Uses (a, b) ping-pong and returns in
+// *result_in_b whether the sorted data ended in the b buffers.
+// tmp: radix_sort_temp_bytes(n). `status` receives device error bits.
 size_t radix_sort_temp_bytes(long long n);
 cudaError_t radix_sort(uint64_t *keys_a, uint64_t *keys_b, uint32_t *vals_a, uint32_t *vals_b,
-                       long long n, int lo, int hi, void *tmp, bool *result_in_b,
+                       long long n, int lo, int hi, void *tmp, bool *result_in_b, uint32_t *status,
                        cudaStream_t st);
 
 // Exclusive scan of n uint32 into uint64 (out has n + 1 entries: out[n] = total).
@@ -114,13 +121,6 @@ cudaError_t launch_hit_write(const uint32_t *Qs, HitParams hp, const uint32_t *o
                              const unsigned long long *starts, unsigned long long base,
                              uint64_t *hits, cudaStream_t st);
 
-// Segment heads of hits sorted by the high word: seg_start[0..nseg], nseg
-// written to *nseg_dev. tmp: segments_temp_bytes(n).
-size_t segments_temp_bytes(long long n);
-cudaError_t launch_segments(const uint64_t *hits, long long n, uint32_t *flags,
-                            unsigned long long *scan, uint32_t *seg_start, void *tmp,
-                            cudaStream_t st);
-
 struct WalkParams {
     const uint32_t *T;   // packed target (base 0)
     const uint32_t *Q;   // packed query strand (base 0)
@@ -137,21 +137,23 @@ struct WalkParams {
     Hsp *hsps;
     unsigned long long hsp_cap;
     DevCounters *ctr;
-    uint4 *queue;        // hand-off queue: (segment, hit index, E, unused)
+    uint4 *queue;        // hand-off queue: (hit index, E, unused, unused)
     unsigned long long queue_cap;
     unsigned int *queue_len;
 };
-// nseg_dev: device count of segments (<= nseg_max, which sizes the grid).
-cudaError_t launch_walk_lanes(const uint64_t *hits, const uint32_t *seg_start,
-                              const unsigned long long *nseg_dev, long long nseg_max,
-                              WalkParams wp, cudaStream_t st);
-cudaError_t launch_walk_warps(const uint64_t *hits, const uint32_t *seg_start, WalkParams wp,
-                              int grid_warps, cudaStream_t st);
+// Walks of hits sorted by (diagonal word, t): lanes own contiguous hit ranges
+// (lanes_per_sm sizes the ranges; 0 = default); warps finish the diagonals
+// the lanes handed off.
+cudaError_t launch_walk_lanes(const uint64_t *hits, long long n, WalkParams wp, int lanes_per_sm,
+                              cudaStream_t st);
+cudaError_t launch_walk_warps(const uint64_t *hits, long long n, WalkParams wp, int grid_warps,
+                              cudaStream_t st);
 
 // Sort HSPs in place by (strand, tpos, qpos, len, score); tpos < 2^tbits,
 // qpos < 2^qbits, tbits + qbits <= 62. tmp: hsp_sort_temp_bytes(n).
 size_t hsp_sort_temp_bytes(long long n);
-cudaError_t hsp_sort(Hsp *hsps, long long n, int tbits, int qbits, void *tmp, cudaStream_t st);
+cudaError_t hsp_sort(Hsp *hsps, long long n, int tbits, int qbits, void *tmp, uint32_t *status,
+                     cudaStream_t st);
 
 // Conversions between the public hit record and the walk layout.
 cudaError_t launch_hits_to_public(const uint64_t *hits, long long n, int strand, long long qoff,

@@ -304,6 +304,7 @@ cudaError_t scan_impl(const Tin *in, Tout *out, long long n, void *tmp, cudaStre
         cudaMemsetAsync(out, 0, sizeof(Tout), st);
         return cudaGetLastError();
     }
+    g_launches += 3;
     scan_reduce<Tin><<<(unsigned)nb, SC_BLOCK, 0, st>>>(in, n, part);
     scan_partials<<<1, 1024, 0, st>>>(part, nb);
     scan_down<Tin, Tout><<<(unsigned)nb, SC_BLOCK, 0, st>>>(in, out, n, part, nb);
@@ -364,8 +365,9 @@ size_t radix_sort_temp_bytes(long long n) {
 }
 
 cudaError_t radix_sort(uint64_t *keys_a, uint64_t *keys_b, uint32_t *vals_a, uint32_t *vals_b,
-                       long long n, int lo, int hi, void *tmp, bool *result_in_b,
+                       long long n, int lo, int hi, void *tmp, bool *result_in_b, uint32_t *status,
                        cudaStream_t st) {
+    (void)status;  // no device-side waits in this sort
     *result_in_b = false;
     if (n <= 1 || hi <= lo) return cudaSuccess;
     if (n >= (1LL << 32)) return cudaErrorInvalidValue;
@@ -392,6 +394,7 @@ cudaError_t radix_sort(uint64_t *keys_a, uint64_t *keys_b, uint32_t *vals_a, uin
         int bits = min(8, hi - shift);
         unsigned mask = (1u << bits) - 1u;
         cudaMemsetAsync(totals, 0, RS_R * 4, st);
+        g_launches += 3;
         rs_hist<<<g.G, RS_BLOCK, 0, st>>>(kin, n, shift, mask, g.chunk, counts, totals, g.G);
         rs_offsets<<<RS_R, RS_BLOCK, 0, st>>>(counts, totals, g.G);
         if (vals)
@@ -432,7 +435,8 @@ size_t hsp_sort_temp_bytes(long long n) {
     return (size_t)n * (8 + 8 + 4 + 4 + sizeof(Hsp)) + radix_sort_temp_bytes(n) + 1024;
 }
 
-cudaError_t hsp_sort(Hsp *hsps, long long n, int tbits, int qbits, void *tmp, cudaStream_t st) {
+cudaError_t hsp_sort(Hsp *hsps, long long n, int tbits, int qbits, void *tmp, uint32_t *status,
+                     cudaStream_t st) {
     if (n <= 1) return cudaSuccess;
     char *p = reinterpret_cast<char *>(tmp);
     auto take = [&](size_t bytes) {
@@ -446,17 +450,19 @@ cudaError_t hsp_sort(Hsp *hsps, long long n, int tbits, int qbits, void *tmp, cu
     unsigned *vb = reinterpret_cast<unsigned *>(take((size_t)n * 4));
     Hsp *hb = reinterpret_cast<Hsp *>(take((size_t)n * sizeof(Hsp)));
     void *rt = take(radix_sort_temp_bytes(n));
+    g_launches++;
     hsp_keys<<<grid_for(n), BLOCK, 0, st>>>(hsps, n, qbits, ka, va);
     bool in_b = false;
     // strand sits at bit 62; tpos and qpos below it
-    cudaError_t e = radix_sort(ka, kb, va, vb, n, 0, qbits + tbits, rt, &in_b, st);
+    cudaError_t e = radix_sort(ka, kb, va, vb, n, 0, qbits + tbits, rt, &in_b, status, st);
     if (e != cudaSuccess) return e;
     uint64_t *k1 = in_b ? kb : ka, *k2 = in_b ? ka : kb;
     unsigned *v1 = in_b ? vb : va, *v2 = in_b ? va : vb;
-    e = radix_sort(k1, k2, v1, v2, n, 62, 63, rt, &in_b, st);
+    e = radix_sort(k1, k2, v1, v2, n, 62, 63, rt, &in_b, status, st);
     if (e != cudaSuccess) return e;
     uint64_t *kf = in_b ? k2 : k1;
     unsigned *vf = in_b ? v2 : v1;
+    g_launches += 2;
     hsp_gather<<<grid_for(n), BLOCK, 0, st>>>(hsps, vf, n, hb);
     hsp_fix_runs<<<grid_for(n), BLOCK, 0, st>>>(hb, kf, n);
     cudaMemcpyAsync(hsps, hb, (size_t)n * sizeof(Hsp), cudaMemcpyDeviceToDevice, st);

@@ -32,113 +32,11 @@ namespace {
 constexpr int W_BLOCK = 256;
 constexpr int SCORE_LIMIT = 1 << 30;  // a best score above this flags overflow
 
-__global__ void seg_flags_kernel(const uint64_t *__restrict__ hits, long long n,
-                                 uint32_t *__restrict__ flags) {
-    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    flags[i] = (i == 0) || ((hits[i] >> 32) != (hits[i - 1] >> 32));
-}
-
-__global__ void seg_write_kernel(const uint32_t *__restrict__ flags,
-                                 const unsigned long long *__restrict__ scan, long long n,
-                                 uint32_t *__restrict__ seg_start) {
-    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < n && flags[i]) seg_start[scan[i]] = (uint32_t)i;
-    if (i == n) seg_start[scan[n]] = (uint32_t)n;
-}
-
 struct Side {
     int best;    // maximum of the running sum (0 for the empty extension)
     int blen;    // earliest length at which `best` is reached
     int scored;  // bases scored
 };
-
-// Lane tier, right side: bases pt+n, pq+n for n = 0 .. avail-1.
-// Returns false when `cap` bases were scored without a stop (hand-off).
-__device__ __forceinline__ bool lane_right(const uint32_t *__restrict__ T,
-                                           const uint32_t *__restrict__ Q, long long pt,
-                                           long long pq, int avail, int X, int cap,
-                                           const int *lut, Side &r, uint32_t &status) {
-    int sum = 0, best = 0, blen = 0, n = 0;
-    while (n < avail) {
-        if (n >= cap) return false;
-        uint32_t tw = win16(T, pt + n), qw = win16(Q, pq + n);
-        int m = min(16, avail - n);
-        int stop = -1;
-#pragma unroll
-        for (int j = 0; j < 16; j++) {
-            if (j >= m) break;
-            int s = lut[((tw >> (2 * j)) & 3u) * 4u + ((qw >> (2 * j)) & 3u)];
-            sum += s;
-            if (sum > best) {
-                best = sum;
-                blen = n + j + 1;
-            }
-            if (best - sum > X) {
-                stop = j;
-                break;
-            }
-        }
-        if (best > SCORE_LIMIT) status |= ST_SCORE_OVERFLOW;
-        if (stop >= 0) {
-            n += stop + 1;
-            r = {best, blen, n};
-            return true;
-        }
-        n += m;
-    }
-    r = {best, blen, n};
-    return true;
-}
-
-// Lane tier, left side: bases pt-1-n, pq-1-n for n = 0 .. avail-1.
-__device__ __forceinline__ bool lane_left(const uint32_t *__restrict__ T,
-                                          const uint32_t *__restrict__ Q, long long pt,
-                                          long long pq, int avail, int X, int cap,
-                                          const int *lut, Side &r, uint32_t &status) {
-    int sum = 0, best = 0, blen = 0, n = 0;
-    while (n < avail) {
-        if (n >= cap) return false;
-        // bases [p-15, p] with p = pt-1-n: base p sits in bits 30-31
-        uint32_t tw = win16(T, pt - 16 - n), qw = win16(Q, pq - 16 - n);
-        int m = min(16, avail - n);
-        int stop = -1;
-#pragma unroll
-        for (int j = 0; j < 16; j++) {
-            if (j >= m) break;
-            int s = lut[((tw >> (30 - 2 * j)) & 3u) * 4u + ((qw >> (30 - 2 * j)) & 3u)];
-            sum += s;
-            if (sum > best) {
-                best = sum;
-                blen = n + j + 1;
-            }
-            if (best - sum > X) {
-                stop = j;
-                break;
-            }
-        }
-        if (best > SCORE_LIMIT) status |= ST_SCORE_OVERFLOW;
-        if (stop >= 0) {
-            n += stop + 1;
-            r = {best, blen, n};
-            return true;
-        }
-        n += m;
-    }
-    r = {best, blen, n};
-    return true;
-}
-
-__device__ __forceinline__ int lane_span(const uint32_t *__restrict__ T,
-                                         const uint32_t *__restrict__ Q, long long t, long long q,
-                                         int span, const int *lut) {
-    uint64_t tv = (uint64_t)win16(T, t) | ((uint64_t)win16(T, t + 16) << 32);
-    uint64_t qv = (uint64_t)win16(Q, q) | ((uint64_t)win16(Q, q + 16) << 32);
-    int s = 0;
-    for (int k = 0; k < span; k++)
-        s += lut[((tv >> (2 * k)) & 3u) * 4u + ((qv >> (2 * k)) & 3u)];
-    return s;
-}
 
 __device__ __forceinline__ void emit(const WalkParams &wp, long long t, long long q, int lblen,
                                      int rblen, long long score, uint32_t &status) {
@@ -156,61 +54,218 @@ __device__ __forceinline__ void emit(const WalkParams &wp, long long t, long lon
     }
 }
 
-__global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(
-    const uint64_t *__restrict__ hits, const uint32_t *__restrict__ seg_start,
-    const unsigned long long *__restrict__ nseg_ptr, WalkParams wp) {
+// 2-bit groups of x in reverse order (group i -> group 15 - i).
+__device__ __forceinline__ uint32_t rev2(uint32_t x) {
+    x = __brev(x);
+    return ((x >> 1) & 0x55555555u) | ((x & 0x55555555u) << 1);
+}
+
+__device__ __forceinline__ uint32_t diag_of(uint64_t h) { return (uint32_t)(h >> 32); }
+
+// First index j in [i, n) whose diagonal word differs from `d` (hits are sorted
+// by diagonal word, so this is an upper bound search).
+__device__ __forceinline__ uint32_t segment_end(const uint64_t *__restrict__ hits, uint32_t i,
+                                                uint32_t n, uint32_t d) {
+    uint32_t lo = i, hi = n;
+    while (lo < hi) {
+        uint32_t mid = lo + (hi - lo) / 2;
+        if (diag_of(hits[mid]) <= d)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Score of the seed span [t, t + span) from a table of pair sums: entry
+// (ta | tb << 2 | qa << 4 | qb << 6) = M[ta][qa] + M[tb][qb].
+__device__ __forceinline__ int span_score(const uint32_t *__restrict__ T,
+                                          const uint32_t *__restrict__ Q, long long t, long long q,
+                                          int span, const int *psum, const int *lut) {
+    const uint64_t tv = (uint64_t)win16(T, t) | ((uint64_t)win16(T, t + 16) << 32);
+    const uint64_t qv = (uint64_t)win16(Q, q) | ((uint64_t)win16(Q, q + 16) << 32);
+    int s = 0;
+    const int pairs = span >> 1;
+    for (int m = 0; m < pairs; m++)
+        s += psum[((uint32_t)(tv >> (4 * m)) & 15u) | (((uint32_t)(qv >> (4 * m)) & 15u) << 4)];
+    if (span & 1) {
+        const int k = span - 1;
+        s += lut[((uint32_t)(tv >> (2 * k)) & 3u) * 4u + ((uint32_t)(qv >> (2 * k)) & 3u)];
+    }
+    return s;
+}
+
+// State of one extension side in the lane tier.
+struct LaneSide {
+    int n;     // bases scored
+    int sum;   // running sum
+    int best;  // running maximum (0 for the empty extension)
+    int blen;  // earliest length reaching `best`
+    bool done;
+};
+
+// Scores the next 16 bases of a side whose next base is (pt, pq) going `dir`
+// (+1 forward, -1 backward; a backward window is read bit-reversed). The 16
+// cells are straight-line selects: a stopped side adds zeros, which leaves
+// its sum, maximum and argmax unchanged.
+__device__ __forceinline__ void lane_window(const uint32_t *__restrict__ T,
+                                            const uint32_t *__restrict__ Q, long long pt,
+                                            long long pq, int dir, int avail, int X,
+                                            const int *lut, LaneSide &sd) {
+    const long long wt = dir > 0 ? pt + sd.n : pt - sd.n - 16;
+    const long long wq = dir > 0 ? pq + sd.n : pq - sd.n - 16;
+    uint32_t tw = win16(T, wt), qw = win16(Q, wq);
+    if (dir < 0) {
+        tw = rev2(tw);
+        qw = rev2(qw);
+    }
+    const int lim = avail - sd.n;
+    bool alive = true;
+    int cnt = 0, bj = -1, sum = sd.sum, best = sd.best;
+    if (lim >= 16) {
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            const int sc = lut[((tw >> (2 * j)) & 3u) * 4u + ((qw >> (2 * j)) & 3u)];
+            cnt = alive ? j + 1 : cnt;
+            sum += alive ? sc : 0;
+            const bool nb = sum > best;
+            best = nb ? sum : best;
+            bj = nb ? j : bj;
+            alive = alive && (best - sum <= X);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            const int sc = lut[((tw >> (2 * j)) & 3u) * 4u + ((qw >> (2 * j)) & 3u)];
+            const bool ok = alive && j < lim;
+            cnt = ok ? j + 1 : cnt;
+            sum += ok ? sc : 0;
+            const bool nb = sum > best;
+            best = nb ? sum : best;
+            bj = nb ? j : bj;
+            alive = alive && (best - sum <= X);
+        }
+    }
+    if (bj >= 0) sd.blen = sd.n + bj + 1;
+    sd.n += cnt;
+    sd.sum = sum;
+    sd.best = best;
+    sd.done = !alive || sd.n >= avail;
+}
+
+// Lane tier. Lane k owns the diagonals that start in hit range
+// [k*chunk, (k+1)*chunk) and streams through its hits in order, with the next
+// hit prefetched. The lanes of a warp advance in lock step, one iteration at
+// a time: (1) lanes without a hit in progress fetch their next extendable hit
+// (skipping hits with t < E, closing a diagonal when the diagonal word
+// changes) and score its seed span from a pair-sum table; (2) every lane whose
+// right side is still open scores its next 16 bases; (3) the same for the left
+// sides; (4) lanes whose two sides are closed emit the HSP and advance E. Most
+// hits finish in one iteration, so the warp stays converged while its lanes
+// work on different hits and diagonals. A side that passes `lane_cap` bases
+// hands the rest of its diagonal to the warp tier.
+__global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__restrict__ hits,
+                                                             uint32_t n, uint32_t chunk,
+                                                             WalkParams wp) {
     __shared__ int lut[16];
+    __shared__ int psum[256];
     if (threadIdx.x < 16) lut[threadIdx.x] = wp.scores[threadIdx.x];
+    {
+        const int e = threadIdx.x;  // W_BLOCK == 256 entries
+        psum[e] = wp.scores[(e & 3) * 4 + ((e >> 4) & 3)] +
+                  wp.scores[((e >> 2) & 3) * 4 + ((e >> 6) & 3)];
+    }
     __syncthreads();
-    const unsigned long long nseg = *nseg_ptr;
-    const long long stride = (long long)gridDim.x * blockDim.x;
+    const int span = wp.span, X = wp.xdrop;
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long lo64 = tid * (long long)chunk;
+    const uint32_t range_end = (uint32_t)min((long long)n, lo64 + chunk);
+
+    uint32_t i = (uint32_t)min((long long)n, lo64);
+    // a diagonal that started before this range belongs to the previous lane
+    if (i > 0 && i < range_end && diag_of(hits[i]) == diag_of(hits[i - 1]))
+        i = segment_end(hits, i, n, diag_of(hits[i]));
+    uint64_t cur = i < n ? hits[i] : ~0ull, nxt = ~0ull;
+    bool in_seg = false, handed = false, busy = false, done = i >= range_end;
+    uint32_t D = 0;
+    long long t = 0, q = 0;
+    int E = INT_MIN, cap = wp.lane_cap, s0 = 0, ravail = 0, lavail = 0;
+    LaneSide R{0, 0, 0, 0, true}, L{0, 0, 0, 0, true};
     unsigned long long ext = 0, cells = 0, tasks = 0;
     uint32_t status = 0;
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < (long long)nseg;
-         s += stride) {
-        tasks++;
-        uint32_t i = seg_start[s], end = seg_start[s + 1];
-        const long long D = (long long)((hits[i] >> 32) & 0x7FFFFFFFu);
-        int E = wp.Ecarry ? wp.Ecarry[D] : INT_MIN;
-        bool handed = false;
-        int cap = wp.lane_cap;
-        while (i < end) {
-            const long long t = (long long)(uint32_t)hits[i];
-            if (t < E) {
-                i++;
-                continue;
-            }
-            const long long q = t - D + wp.qoff;
-            const long long pt = t + wp.span, pq = q + wp.span;
-            Side r, l;
-            int ravail = (int)min(wp.tlen - pt, wp.qlen - pq);
-            int lavail = (int)min(t, q);
-            bool ok = lane_right(wp.T, wp.Q, pt, pq, ravail, wp.xdrop, cap, lut, r, status) &&
-                      lane_left(wp.T, wp.Q, t, q, lavail, wp.xdrop, cap, lut, l, status);
-            if (!ok) {
-                unsigned int slot = atomicAdd(wp.queue_len, 1u);
-                if (slot < wp.queue_cap) {
-                    wp.queue[slot] = make_uint4((uint32_t)s, i, (uint32_t)E, 0u);
-                    handed = true;
+
+    while (true) {
+        // (1) fetch
+        while (!busy && !done) {
+            if (!in_seg) {
+                if (i >= range_end) {
+                    done = true;
                     break;
                 }
-                // queue full: this lane finishes the diagonal itself
-                cap = INT_MAX;
+                D = diag_of(cur);
+                E = wp.Ecarry ? wp.Ecarry[D & 0x7FFFFFFFu] : INT_MIN;
+                in_seg = true;
+                handed = false;
+                cap = wp.lane_cap;
+                tasks++;
+            }
+            if (i >= n || diag_of(cur) != D) {
+                if (!handed && wp.Ecarry) wp.Ecarry[D & 0x7FFFFFFFu] = E;
+                in_seg = false;
                 continue;
             }
-            const int s0 = lane_span(wp.T, wp.Q, t, q, wp.span, lut);
-            const long long score = (long long)s0 + r.best + l.best;
+            t = (long long)(uint32_t)cur;
+            nxt = (i + 1 < n) ? hits[i + 1] : ~0ull;  // consumed when this hit is done
+            if (t < E) {
+                i++;
+                cur = nxt;
+                continue;
+            }
+            q = t - (long long)(D & 0x7FFFFFFFu) + wp.qoff;
+            s0 = span_score(wp.T, wp.Q, t, q, span, psum, lut);
+            ravail = (int)min(wp.tlen - t - span, wp.qlen - q - span);
+            lavail = (int)min(t, q);
+            R = LaneSide{0, 0, 0, 0, ravail == 0};
+            L = LaneSide{0, 0, 0, 0, lavail == 0};
+            busy = true;
+        }
+        if (__all_sync(0xffffffffu, done)) break;
+        // (2) right sides
+        const bool needR = busy && !R.done;
+        if (__any_sync(0xffffffffu, needR) && needR)
+            lane_window(wp.T, wp.Q, t + span, q + span, 1, ravail, X, lut, R);
+        // (3) left sides
+        const bool needL = busy && !L.done;
+        if (__any_sync(0xffffffffu, needL) && needL)
+            lane_window(wp.T, wp.Q, t, q, -1, lavail, X, lut, L);
+        if (busy && (R.best > SCORE_LIMIT || L.best > SCORE_LIMIT)) status |= ST_SCORE_OVERFLOW;
+        // (4) finish or hand off
+        if (busy && R.done && L.done) {
+            const long long score = (long long)s0 + R.best + L.best;
             if (score > INT_MAX) status |= ST_SCORE_OVERFLOW;
             ext++;
-            cells += (unsigned long long)(wp.span + r.scored + l.scored);
+            cells += (unsigned long long)(span + R.n + L.n);
             const bool pass = score >= wp.thresh;
-            if (pass) emit(wp, t, q, l.blen, r.blen, score, status);
-            if (pass || !(wp.flags & SFE_SKIP_PASSING_ONLY)) E = (int)(t + wp.span + r.blen);
+            if (pass) emit(wp, t, q, L.blen, R.blen, score, status);
+            if (pass || !(wp.flags & SFE_SKIP_PASSING_ONLY)) E = (int)(t + span + R.blen);
             i++;
+            cur = nxt;
+            busy = false;
+        } else if (busy && (R.n >= cap || L.n >= cap)) {
+            // a long extension: the rest of this diagonal goes to a warp
+            unsigned int slot = atomicAdd(wp.queue_len, 1u);
+            if (slot < wp.queue_cap) {
+                wp.queue[slot] = make_uint4(i, (uint32_t)E, 0u, 0u);
+                handed = true;
+                i = segment_end(hits, i, n, D);
+                cur = i < n ? hits[i] : ~0ull;
+                in_seg = false;
+                busy = false;
+            } else {
+                cap = INT_MAX;  // queue full: this lane finishes the diagonal itself
+            }
         }
-        if (!handed && wp.Ecarry) wp.Ecarry[D] = E;
     }
-    // one atomic per warp for each counter
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         ext += __shfl_down_sync(0xffffffffu, ext, o);
@@ -284,8 +339,7 @@ __device__ __forceinline__ Side warp_side(const uint32_t *__restrict__ T,
 }
 
 __global__ void __launch_bounds__(W_BLOCK) walk_warps_kernel(const uint64_t *__restrict__ hits,
-                                                             const uint32_t *__restrict__ seg_start,
-                                                             WalkParams wp) {
+                                                             uint32_t nhits, WalkParams wp) {
     __shared__ int lut[16];
     if (threadIdx.x < 16) lut[threadIdx.x] = wp.scores[threadIdx.x];
     __syncthreads();
@@ -298,12 +352,14 @@ __global__ void __launch_bounds__(W_BLOCK) walk_warps_kernel(const uint64_t *__r
     for (long long e = warp; e < (long long)nq; e += nwarps) {
         const uint4 it = wp.queue[e];
         tasks++;
-        uint32_t i = it.y;
-        const uint32_t end = seg_start[it.x + 1];
-        int E = (int)it.z;
-        const long long D = (long long)((hits[i] >> 32) & 0x7FFFFFFFu);
-        while (i < end) {
-            const long long t = (long long)(uint32_t)hits[i];
+        uint32_t i = it.x;
+        int E = (int)it.y;
+        const uint32_t dword = diag_of(hits[i]);
+        const long long D = (long long)(dword & 0x7FFFFFFFu);
+        while (i < nhits) {
+            const uint64_t h = hits[i];
+            if (diag_of(h) != dword) break;
+            const long long t = (long long)(uint32_t)h;
             if (t < E) {
                 i++;
                 continue;
@@ -333,7 +389,10 @@ __global__ void __launch_bounds__(W_BLOCK) walk_warps_kernel(const uint64_t *__r
     }
     if (lane == 0) {
         if (ext) atomicAdd(&wp.ctr->extended, ext);
-        if (cells) atomicAdd(&wp.ctr->cells, cells);
+        if (cells) {
+            atomicAdd(&wp.ctr->cells, cells);
+            atomicAdd(&wp.ctr->warp_cells, cells);
+        }
         if (tasks) atomicAdd(&wp.ctr->warp_tasks, tasks);
     }
 #pragma unroll
@@ -358,34 +417,27 @@ int sms() {
 
 }  // namespace
 
-size_t segments_temp_bytes(long long n) { return scan_temp_bytes(n); }
-
-cudaError_t launch_segments(const uint64_t *hits, long long n, uint32_t *flags,
-                            unsigned long long *scan, uint32_t *seg_start, void *tmp,
-                            cudaStream_t st) {
-    if (n > 0) seg_flags_kernel<<<grid_for(n), BLOCK, 0, st>>>(hits, n, flags);
-    cudaError_t e = scan_u32_to_u64(flags, scan, n, tmp, st);
-    if (e != cudaSuccess) return e;
-    seg_write_kernel<<<grid_for(n + 1), BLOCK, 0, st>>>(flags, scan, n, seg_start);
+cudaError_t launch_walk_lanes(const uint64_t *hits, long long n, WalkParams wp, int lanes_per_sm,
+                              cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    // about two resident waves of lanes, each owning a contiguous hit range
+    long long lanes = (long long)sms() * (lanes_per_sm > 0 ? lanes_per_sm : 4096);
+    long long chunk = (n + lanes - 1) / lanes;
+    if (chunk < 16) chunk = 16;
+    long long nthreads = (n + chunk - 1) / chunk;
+    g_launches++;
+    walk_lanes_kernel<<<grid_for(nthreads, W_BLOCK), W_BLOCK, 0, st>>>(hits, (uint32_t)n,
+                                                                        (uint32_t)chunk, wp);
     return cudaGetLastError();
 }
 
-cudaError_t launch_walk_lanes(const uint64_t *hits, const uint32_t *seg_start,
-                              const unsigned long long *nseg_dev, long long nseg_max,
-                              WalkParams wp, cudaStream_t st) {
-    if (nseg_max <= 0) return cudaSuccess;
-    long long want = grid_for(nseg_max, W_BLOCK);
-    long long cap = 16LL * sms();
-    unsigned grid = (unsigned)(want < cap ? want : cap);
-    walk_lanes_kernel<<<grid, W_BLOCK, 0, st>>>(hits, seg_start, nseg_dev, wp);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_walk_warps(const uint64_t *hits, const uint32_t *seg_start, WalkParams wp,
-                              int grid_warps, cudaStream_t st) {
+cudaError_t launch_walk_warps(const uint64_t *hits, long long n, WalkParams wp, int grid_warps,
+                              cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
     if (grid_warps <= 0) grid_warps = 8 * sms() * (W_BLOCK / 32);
     unsigned grid = (unsigned)((grid_warps * 32 + W_BLOCK - 1) / W_BLOCK);
-    walk_warps_kernel<<<grid, W_BLOCK, 0, st>>>(hits, seg_start, wp);
+    g_launches++;
+    walk_warps_kernel<<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, wp);
     return cudaGetLastError();
 }
 

@@ -18,6 +18,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsfe.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW = 0, -1, -2, -3, -4, -5
 SKIP_PASSING_ONLY = 1
+TIME_STAGES = 2
+STAGES = ("pack", "index", "count", "write", "sort", "segments", "walk_lanes", "walk_warps",
+          "output")
 
 HIT_DTYPE = np.dtype([("strand", "<i4"), ("tpos", "<i4"), ("qpos", "<i4")])
 HSP_DTYPE = np.dtype([("strand", "<i4"), ("tpos", "<i4"), ("qpos", "<i4"), ("len", "<i4"),
@@ -34,16 +37,21 @@ class Params(C.Structure):
     _fields_ = [("seed_pattern", C.c_char_p), ("transition", C.c_int32),
                 ("strands", C.c_int32), ("scores", C.c_int32 * 16), ("xdrop", C.c_int32),
                 ("hsp_thresh", C.c_int32), ("flags", C.c_int32), ("input_codes", C.c_int32),
-                ("lane_cap", C.c_int32), ("reserved", C.c_int32), ("tile_hits", C.c_int64)]
+                ("lane_cap", C.c_int32), ("lanes_per_sm", C.c_int32), ("tile_hits", C.c_int64)]
 
 
 class Stats(C.Structure):
     _fields_ = [("hits", C.c_int64), ("extended", C.c_int64), ("cells", C.c_int64),
                 ("hsps", C.c_int64), ("lane_tasks", C.c_int64), ("warp_tasks", C.c_int64),
-                ("tiles", C.c_int64), ("reserved", C.c_int64)]
+                ("warp_cells", C.c_int64), ("tiles", C.c_int64), ("launches", C.c_int64),
+                ("stage_ms", C.c_double * len(STAGES)),
+                ("stage_launches", C.c_int64 * len(STAGES))]
 
     def as_dict(self) -> dict:
-        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
+        d = {k: int(getattr(self, k)) for k, _ in self._fields_[:9]}
+        d["stage_ms"] = {n: float(self.stage_ms[i]) for i, n in enumerate(STAGES)}
+        d["stage_launches"] = {n: int(self.stage_launches[i]) for i, n in enumerate(STAGES)}
+        return d
 
 
 _lib = None
@@ -105,13 +113,13 @@ def default_params(**kw) -> Params:
 
 
 def _buf(x):
-    """(pointer, number of elements, keep-alive) of a torch tensor, numpy array or bytes."""
+    """(pointer, size in bytes, keep-alive) of a torch tensor, numpy array or bytes."""
     try:
         import torch
         if isinstance(x, torch.Tensor):
             if not x.is_contiguous():
                 raise ValueError("tensor must be contiguous")
-            return x.data_ptr(), x.numel(), x
+            return x.data_ptr(), x.numel() * x.element_size(), x
     except ImportError:
         pass
     if isinstance(x, (bytes, bytearray, memoryview)):
@@ -120,7 +128,7 @@ def _buf(x):
     if a.size == 0:
         a = np.zeros(1, dtype=a.dtype)
         return a.ctypes.data, 0, a
-    return a.ctypes.data, a.size, a
+    return a.ctypes.data, a.nbytes, a
 
 
 def _stream_handle(stream) -> int | None:
@@ -178,8 +186,8 @@ class Context:
         nh = C.c_int64(0)
         if out is not None:
             optr, ocap, _ = _buf(out)
-            _check(lib().sfe_seed_hits(self.h, index.h, ptr, n, int(strands), optr, ocap // 3,
-                                       C.byref(nh)))
+            _check(lib().sfe_seed_hits(self.h, index.h, ptr, n, int(strands), optr,
+                                       ocap // HIT_DTYPE.itemsize, C.byref(nh)))
             return out, int(nh.value)
         cap = 1 << 16 if cap is None else int(cap)
         while True:
@@ -199,7 +207,7 @@ class Context:
         if isinstance(hits, np.ndarray) and hits.dtype == HIT_DTYPE:
             hits = hits.view(np.int32).reshape(-1)
         hptr, hn, hkeep = _buf(hits)
-        nhits = hn // 3
+        nhits = hn // HIT_DTYPE.itemsize
         sc = (C.c_int32 * 16)(*[int(x) for x in np.asarray(scores, dtype=np.int64).reshape(16)])
         return self._retry(cap, lambda buf, cp, nout, st: lib().sfe_ungapped_xdrop(
             self.h, index.h, qptr, qn, hptr, nhits, C.byref(sc), int(X), int(thresh), buf, cp,
@@ -216,8 +224,8 @@ class Context:
             optr, on, _ = _buf(out)
             nout = C.c_int64(0)
             st = Stats()
-            _check(lib().sfe_run(self.h, tptr, tn, qptr, qn, C.byref(p), optr, on // 5,
-                                 C.byref(nout), C.byref(st)))
+            _check(lib().sfe_run(self.h, tptr, tn, qptr, qn, C.byref(p), optr,
+                                 on // HSP_DTYPE.itemsize, C.byref(nout), C.byref(st)))
             return out[: nout.value], st.as_dict()
         return self._retry(cap, lambda buf, cp, nout, st: lib().sfe_run(
             self.h, tptr, tn, qptr, qn, C.byref(p), buf, cp, nout, st))
