@@ -56,6 +56,7 @@ extern "C" {
 #define SFE_ECUDA (-3)     /* a CUDA call failed */
 #define SFE_ETIMEOUT (-4)  /* a bounded device wait ran out */
 #define SFE_EOVERFLOW (-5) /* output capacity too small (needed count returned), or a score left int32 */
+#define SFE_ELIMIT (-6)    /* input larger than the fixed scratch of sfe_ungapped_xdrop_static */
 
 /* sfe_params.flags */
 #define SFE_SKIP_PASSING_ONLY 1 /* advance E only for HSPs with score >= hsp_thresh */
@@ -182,6 +183,47 @@ int sfe_ungapped_xdrop(sfe_ctx *ctx, const sfe_index *index, const uint8_t *quer
 int sfe_run(sfe_ctx *ctx, const uint8_t *target, int64_t tlen, const uint8_t *query, int64_t qlen,
             const sfe_params *params, sfe_hsp *hsps, int64_t cap, int64_t *nhsps,
             sfe_stats *stats);
+
+/*
+ * Allocation-free variant of sfe_ungapped_xdrop (the paper has no counterpart:
+ * this entry point exists for callers of the library, not for the method).
+ *
+ * For callers that cannot allocate device memory: code running inside
+ * another framework's memory pool or under a hard memory budget, plugins whose
+ * host owns every device allocation, and latency-critical paths where an
+ * allocation and its implicit synchronisation are not allowed. The call never
+ * allocates: no cudaMalloc, cudaFree, stream-ordered allocation or context.
+ * Its scratch is one statically sized device array in the library (about
+ * 13 MiB), which every GPU that loads the library holds until the process
+ * exits.
+ *
+ * Limits: tlen and qlen at most 2^20 bases each, nhits at most 2^17; larger
+ * inputs return SFE_ELIMIT before any GPU work.
+ *
+ * Arguments: target (tlen bases), query (qlen bases) and hits (nhits records,
+ * any order) must be device pointers; bases are ASCII (input_codes = 0) or
+ * codes 0..3 (input_codes = 1); seed_pattern NULL means 12of19 (only its span
+ * is used). scores, X and hsp_thresh as in sfe_ungapped_xdrop. hsps: device
+ * buffer of cap records, filled with the HSPs sorted by (strand, tpos, qpos,
+ * len, score); if more than cap are found, *nhsps receives the needed count,
+ * the buffer's contents are unspecified and SFE_EOVERFLOW is returned. stats
+ * may be NULL. Work is queued on `stream` (a cudaStream_t; NULL is the legacy
+ * default stream) and the call returns after it completes. The output equals
+ * sfe_ungapped_xdrop's on the same inputs.
+ *
+ * The first call on a device looks up the array's device address for that
+ * device (with that device current); make that first call before capturing
+ * the stream into a graph. Every call shares the one array and the call clears
+ * the parts that must start at zero, so calls whose GPU work overlaps (two host
+ * threads, or two streams of one device) race on it and must be serialised by
+ * the caller. Errors are reported through the return code only (this call sets
+ * no message for sfe_last_error).
+ */
+int sfe_ungapped_xdrop_static(const uint8_t *target, int64_t tlen, const uint8_t *query,
+                              int64_t qlen, const char *seed_pattern, int32_t input_codes,
+                              const sfe_hit *hits, int64_t nhits, const int32_t scores[16],
+                              int32_t X, int32_t hsp_thresh, sfe_hsp *hsps, int64_t cap,
+                              int64_t *nhsps, sfe_stats *stats, void *stream);
 
 #ifdef __cplusplus
 }

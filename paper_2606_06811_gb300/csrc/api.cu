@@ -503,6 +503,7 @@ const char *sfe_strerror(int code) {
     case SFE_ECUDA: return "CUDA error";
     case SFE_ETIMEOUT: return "bounded device wait ran out";
     case SFE_EOVERFLOW: return "output capacity or int32 range exceeded";
+    case SFE_ELIMIT: return "input larger than the fixed scratch of the allocation-free call";
     default: return "unknown error";
     }
 }
