@@ -95,19 +95,33 @@ __device__ __forceinline__ int span_score(const uint32_t *__restrict__ T,
     return s;
 }
 
-// State of one extension side in the lane tier.
+// State of one extension side in the lane tier: the running maximum, the
+// running sum's drop below it (d = best - sum >= 0), the earliest length that
+// reached the maximum and the bases scored.
 struct LaneSide {
     int n;     // bases scored
-    int sum;   // running sum
+    int d;     // best - running sum
     int best;  // running maximum (0 for the empty extension)
     int blen;  // earliest length reaching `best`
     bool done;
 };
 
+// Largest X for which the packed-key window below cannot overflow int32.
+constexpr int PACKED_X_LIMIT = 1 << 26;
+
 // Scores the next 16 bases of a side whose next base is (pt, pq) going `dir`
-// (+1 forward, -1 backward; a backward window is read bit-reversed). The 16
-// cells are straight-line selects: a stopped side adds zeros, which leaves
-// its sum, maximum and argmax unchanged.
+// (+1 forward, -1 backward; a backward window is read bit-reversed).
+//
+// The window works on sums relative to the current maximum, so its values stay
+// within X + 16 max|score| whatever the side's length. With PACKED, cell j
+// keeps the maximum and its earliest position in one key, 16 * sum + (15 - j):
+// a larger key is a larger sum, or the same sum reached earlier, so one max
+// tracks both, and ties keep the older maximum. The stop test becomes
+// key_max - 16 * sum >= 16 * (X + 1). The running sum, the keys and the test
+// are multiply-adds (the FMA pipe), which leaves the integer ALU pipe (the
+// walk's limit) with the table index, the max and the compare. A stopped
+// side multiplies its scores by zero, which leaves its state unchanged.
+template <bool PACKED>
 __device__ __forceinline__ void lane_window(const uint32_t *__restrict__ T,
                                             const uint32_t *__restrict__ Q, long long pt,
                                             long long pq, int dir, int avail, int X,
@@ -120,37 +134,57 @@ __device__ __forceinline__ void lane_window(const uint32_t *__restrict__ T,
         qw = rev2(qw);
     }
     const int lim = avail - sd.n;
-    bool alive = true;
-    int cnt = 0, bj = -1, sum = sd.sum, best = sd.best;
-    if (lim >= 16) {
+    int sum = -sd.d;  // relative to the current maximum
+    int cnt = 0, a = 1, bj = -1, gain = 0;
+    if (PACKED) {
+        const int thr = 16 * (X + 1);
+        int bk = 15;  // key of the current maximum (relative sum 0, oldest position)
+        if (lim >= 16) {
 #pragma unroll
-        for (int j = 0; j < 16; j++) {
-            const int sc = lut[((tw >> (2 * j)) & 3u) * 4u + ((qw >> (2 * j)) & 3u)];
-            cnt = alive ? j + 1 : cnt;
-            sum += alive ? sc : 0;
-            const bool nb = sum > best;
-            best = nb ? sum : best;
-            bj = nb ? j : bj;
-            alive = alive && (best - sum <= X);
+            for (int j = 0; j < 16; j++) {
+                const int sc = lut[((tw >> (2 * j)) & 3u) * 4u + ((qw >> (2 * j)) & 3u)];
+                sum = sc * a + sum;
+                cnt += a;
+                bk = max(bk, sum * 16 + (15 - j));
+                a = (bk - sum * 16 < thr) ? a : 0;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                const int sc = lut[((tw >> (2 * j)) & 3u) * 4u + ((qw >> (2 * j)) & 3u)];
+                a = j < lim ? a : 0;
+                sum = sc * a + sum;
+                cnt += a;
+                bk = max(bk, sum * 16 + (15 - j));
+                a = (bk - sum * 16 < thr) ? a : 0;
+            }
+        }
+        if (bk != 15) {
+            gain = bk >> 4;
+            bj = 15 - (bk & 15);
         }
     } else {
+        int lbest = 0;
 #pragma unroll
         for (int j = 0; j < 16; j++) {
             const int sc = lut[((tw >> (2 * j)) & 3u) * 4u + ((qw >> (2 * j)) & 3u)];
-            const bool ok = alive && j < lim;
-            cnt = ok ? j + 1 : cnt;
-            sum += ok ? sc : 0;
-            const bool nb = sum > best;
-            best = nb ? sum : best;
+            a = j < lim ? a : 0;
+            sum = sc * a + sum;
+            cnt += a;
+            const bool nb = sum > lbest;
+            lbest = nb ? sum : lbest;
             bj = nb ? j : bj;
-            alive = alive && (best - sum <= X);
+            a = (lbest - sum <= X) ? a : 0;
         }
+        gain = lbest;
     }
-    if (bj >= 0) sd.blen = sd.n + bj + 1;
+    if (bj >= 0) {
+        sd.blen = sd.n + bj + 1;
+        sd.best += gain;
+    }
+    sd.d = gain - sum;
     sd.n += cnt;
-    sd.sum = sum;
-    sd.best = best;
-    sd.done = !alive || sd.n >= avail;
+    sd.done = a == 0 || sd.n >= avail;
 }
 
 // Lane tier. Lane k owns the diagonals that start in hit range
@@ -164,6 +198,7 @@ __device__ __forceinline__ void lane_window(const uint32_t *__restrict__ T,
 // hits finish in one iteration, so the warp stays converged while its lanes
 // work on different hits and diagonals. A side that passes `lane_cap` bases
 // hands the rest of its diagonal to the warp tier.
+template <bool PACKED>
 __global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__restrict__ hits,
                                                              uint32_t n, uint32_t chunk,
                                                              WalkParams wp) {
@@ -233,11 +268,11 @@ __global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__r
         // (2) right sides
         const bool needR = busy && !R.done;
         if (__any_sync(0xffffffffu, needR) && needR)
-            lane_window(wp.T, wp.Q, t + span, q + span, 1, ravail, X, lut, R);
+            lane_window<PACKED>(wp.T, wp.Q, t + span, q + span, 1, ravail, X, lut, R);
         // (3) left sides
         const bool needL = busy && !L.done;
         if (__any_sync(0xffffffffu, needL) && needL)
-            lane_window(wp.T, wp.Q, t, q, -1, lavail, X, lut, L);
+            lane_window<PACKED>(wp.T, wp.Q, t, q, -1, lavail, X, lut, L);
         if (busy && (R.best > SCORE_LIMIT || L.best > SCORE_LIMIT)) status |= ST_SCORE_OVERFLOW;
         // (4) finish or hand off
         if (busy && R.done && L.done) {
@@ -426,8 +461,12 @@ cudaError_t launch_walk_lanes(const uint64_t *hits, long long n, WalkParams wp, 
     if (chunk < 16) chunk = 16;
     long long nthreads = (n + chunk - 1) / chunk;
     g_launches++;
-    walk_lanes_kernel<<<grid_for(nthreads, W_BLOCK), W_BLOCK, 0, st>>>(hits, (uint32_t)n,
-                                                                        (uint32_t)chunk, wp);
+    if (wp.xdrop < PACKED_X_LIMIT)
+        walk_lanes_kernel<true><<<grid_for(nthreads, W_BLOCK), W_BLOCK, 0, st>>>(
+            hits, (uint32_t)n, (uint32_t)chunk, wp);
+    else
+        walk_lanes_kernel<false><<<grid_for(nthreads, W_BLOCK), W_BLOCK, 0, st>>>(
+            hits, (uint32_t)n, (uint32_t)chunk, wp);
     return cudaGetLastError();
 }
 
