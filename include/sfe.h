@@ -185,6 +185,22 @@ int sfe_run(sfe_ctx *ctx, const uint8_t *target, int64_t tlen, const uint8_t *qu
             sfe_stats *stats);
 
 /*
+ * The filter stage over a batch of independent target/query pairs (the
+ * uneven, independent tasks of Section 8's load-balancing discussion, run as
+ * one batch). targets / queries: the pairs' sequences back to back (host or
+ * device); toff / qoff: host arrays of npairs + 1 offsets into them (toff[0] =
+ * qoff[0] = 0, non-decreasing). Each pair is seeded against its own index and
+ * extended within its own bounds, exactly as sfe_run would do it alone.
+ * hsps: cap records (host or device) sorted by (pair, strand, tpos, qpos,
+ * len, score), coordinates local to the pair. Limits: npairs <= 65536, every
+ * sequence shorter than 2^20 bases, at most 2^32 - 1 hits in the batch.
+ */
+int sfe_run_batch(sfe_ctx *ctx, const uint8_t *targets, const int64_t *toff,
+                  const uint8_t *queries, const int64_t *qoff, int32_t npairs,
+                  const sfe_params *params, sfe_batch_hsp *hsps, int64_t cap, int64_t *nhsps,
+                  sfe_stats *stats);
+
+/*
  * Allocation-free variant of sfe_ungapped_xdrop (the paper has no counterpart:
  * this entry point exists for callers of the library, not for the method).
  *

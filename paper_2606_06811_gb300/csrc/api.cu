@@ -48,7 +48,7 @@ constexpr unsigned long long kQueueMax = 1ull << 22;
 
 enum Slot {
     SL_TIN, SL_QIN, SL_TP, SL_QP, SL_QM, SL_KEYS_A, SL_KEYS_B, SL_BCOUNT, SL_OFFS, SL_POS,
-    SL_COUNTS, SL_STARTS, SL_HITS_A, SL_HITS_B, SL_QUEUE,
+    SL_COUNTS, SL_STARTS, SL_HITS_A, SL_HITS_B, SL_QUEUE, SL_PAIRS, SL_BENTRIES,
     SL_HSPS, SL_TMP, SL_ECARRY, SL_PUB, SL_BOUNDS, NSLOT
 };
 
@@ -399,7 +399,7 @@ int walk_sorted(sfe_ctx *c, const uint64_t *hits, long long n, const WalkSetup &
     const unsigned long long qcap = std::min<unsigned long long>((unsigned long long)n, kQueueMax);
     TRY(ensure_t(c, SL_QUEUE, (size_t)qcap, &queue));
     CK(cudaMemsetAsync(&c->small->queue_len, 0, 4, c->st));
-    WalkParams wp;
+    WalkParams wp{};
     wp.T = ws.T;
     wp.Q = ws.Qs;
     wp.tlen = ws.tlen;
@@ -868,6 +868,171 @@ int sfe_run(sfe_ctx *c, const uint8_t *target, int64_t tlen, const uint8_t *quer
     {
         Span sp(c, SFE_STAGE_OUTPUT);
         r = finish_hsps(c, hd, sm.ctr.hsps, tlen, qlen, hsps, cap, nhsps);
+    }
+    CK(cudaStreamSynchronize(c->st));
+    add_timings(c, stats);
+    return r;
+}
+
+int sfe_run_batch(sfe_ctx *c, const uint8_t *targets, const int64_t *toff, const uint8_t *queries,
+                  const int64_t *qoff, int32_t npairs, const sfe_params *params,
+                  sfe_batch_hsp *hsps, int64_t cap, int64_t *nhsps, sfe_stats *stats) {
+    if (!nhsps || !toff || !qoff) return fail(SFE_EINVAL, "nhsps, toff or qoff is NULL");
+    if (npairs < 1 || npairs > (1 << 16)) return fail(SFE_EINVAL, "npairs must be 1..65536");
+    TRY(check_params(params));
+    SeedPattern pat;
+    TRY(parse_pattern(params->seed_pattern, &pat));
+    if (toff[0] != 0 || qoff[0] != 0) return fail(SFE_EINVAL, "offsets must start at 0");
+    long long maxsum = 1, maxlen = 1;
+    for (int p = 0; p < npairs; p++) {
+        const long long tl = toff[p + 1] - toff[p], ql = qoff[p + 1] - qoff[p];
+        if (tl < 0 || ql < 0) return fail(SFE_EINVAL, "offsets must not decrease");
+        if (tl >= (1LL << 20) || ql >= (1LL << 20))
+            return fail(SFE_EINVAL, "batch sequences must be shorter than 2^20 bases");
+        maxsum = std::max(maxsum, tl + ql);
+        maxlen = std::max(maxlen, std::max(tl, ql));
+    }
+    const long long ttot = toff[npairs], qtot = qoff[npairs];
+    TRY(check_len(ttot, "concatenated target"));
+    TRY(check_len(qtot, "concatenated query"));
+    const int dbits = bits_for(maxsum), pbits = bits_for(npairs - 1);
+    if (pbits + 1 + dbits > 32) return fail(SFE_EINVAL, "too many pairs for their lengths");
+    TRY(begin(c, params->flags));
+    TRY(upload_scores(c, params->scores));
+
+    // pairs and the layout of their index buckets
+    std::vector<PairInfo> P(npairs);
+    long long nbuckets = 0;
+    const int kbits = 2 * pat.weight;
+    for (int p = 0; p < npairs; p++) {
+        PairInfo &x = P[p];
+        x.toff = toff[p];
+        x.qoff = qoff[p];
+        x.qoff_rc = qtot - qoff[p + 1];
+        x.tlen = (int)(toff[p + 1] - toff[p]);
+        x.qlen = (int)(qoff[p + 1] - qoff[p]);
+        const long long npos = std::max(1LL, (long long)x.tlen - pat.span + 1);
+        x.bbits = std::min(kbits, std::max(4, bits_for(npos - 1)));
+        x.boff = nbuckets;
+        x.pad = 0;
+        nbuckets += 1LL << x.bbits;
+    }
+    PairInfo *dpairs = nullptr;
+    TRY(ensure_t(c, SL_PAIRS, (size_t)npairs, &dpairs));
+    CK(cudaMemcpyAsync(dpairs, P.data(), (size_t)npairs * sizeof(PairInfo), cudaMemcpyHostToDevice,
+                       c->st));
+
+    uint32_t *Tp = nullptr, *Qp = nullptr, *Qm = nullptr;
+    {
+        Span sp(c, SFE_STAGE_PACK);
+        const void *tdev = nullptr, *qdev = nullptr;
+        TRY(stage(c, SL_TIN, targets, (size_t)ttot, &tdev));
+        TRY(stage(c, SL_QIN, queries, (size_t)qtot, &qdev));
+        TRY(pack_slot(c, SL_TP, reinterpret_cast<const uint8_t *>(tdev), ttot, params->input_codes,
+                      &Tp));
+        TRY(pack_slot(c, SL_QP, reinterpret_cast<const uint8_t *>(qdev), qtot, params->input_codes,
+                      &Qp));
+        TRY(rc_slot(c, SL_QM, Qp, qtot, &Qm));
+    }
+    uint32_t *bcnt = nullptr, *boffs = nullptr;
+    uint64_t *entries = nullptr;
+    void *tmp = nullptr;
+    {
+        Span sp(c, SFE_STAGE_INDEX);
+        TRY(ensure_t(c, SL_BCOUNT, (size_t)nbuckets, &bcnt));
+        TRY(ensure_t(c, SL_OFFS, (size_t)nbuckets + 1, &boffs));
+        TRY(ensure_t(c, SL_BENTRIES, (size_t)std::max(1LL, ttot), &entries));
+        TRY(ensure(c, SL_TMP, std::max(scan_temp_bytes(nbuckets), scan_temp_bytes(2 * qtot)), &tmp));
+        CK(launch_batch_index(Tp, dpairs, npairs, pat, bcnt, nbuckets, boffs, entries, tmp, c->st));
+    }
+    uint32_t *counts = nullptr;
+    unsigned long long *starts = nullptr, total = 0;
+    {
+        Span sp(c, SFE_STAGE_COUNT);
+        TRY(ensure_t(c, SL_COUNTS, (size_t)std::max(1LL, 2 * qtot), &counts));
+        TRY(ensure_t(c, SL_STARTS, (size_t)(2 * qtot + 1), &starts));
+        CK(launch_batch_hit_count(Qp, Qm, dpairs, npairs, params->strands, pat, params->transition,
+                                  dbits, qtot, boffs, entries, counts, c->st));
+        CK(scan_u32_to_u64(counts, starts, 2 * qtot, tmp, c->st));
+        CK(cudaMemcpyAsync(&total, starts + 2 * qtot, 8, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+    }
+    if (total >= (1ull << 32)) return fail(SFE_EINVAL, "a batch may hold at most 2^32 - 1 hits");
+    const long long nh = (long long)total;
+    uint64_t *ha = nullptr, *hb = nullptr;
+    TRY(ensure_t(c, SL_HITS_A, (size_t)std::max(1LL, nh), &ha));
+    TRY(ensure_t(c, SL_HITS_B, (size_t)std::max(1LL, nh), &hb));
+    TRY(ensure(c, SL_TMP, radix_sort_temp_bytes(nh), &tmp));
+    {
+        Span sp(c, SFE_STAGE_WRITE);
+        CK(launch_batch_hit_write(Qp, Qm, dpairs, npairs, params->strands, pat,
+                                  params->transition, dbits, qtot, boffs, entries, starts, ha,
+                                  c->st));
+    }
+    bool in_b = false;
+    {
+        Span sp(c, SFE_STAGE_SORT);
+        CK(radix_sort(ha, hb, nullptr, nullptr, nh, 32, 32 + pbits + 1 + dbits, tmp, &in_b,
+                      &c->small->status, c->st));
+    }
+    const uint64_t *sorted = in_b ? hb : ha;
+    BatchHsp *hd = nullptr;
+    unsigned long long hcap = std::max<unsigned long long>(1ull << 16, (unsigned long long)cap);
+    if (c->cap[SL_HSPS] / sizeof(BatchHsp) > hcap) hcap = c->cap[SL_HSPS] / sizeof(BatchHsp);
+    for (int attempt = 0; attempt < 2; attempt++) {
+        TRY(ensure_t(c, SL_HSPS, (size_t)hcap, &hd));
+        CK(cudaMemsetAsync(&c->small->ctr, 0, sizeof(DevCounters), c->st));
+        uint4 *queue = nullptr;
+        const unsigned long long qcap =
+            std::min<unsigned long long>((unsigned long long)std::max(1LL, nh), kQueueMax);
+        TRY(ensure_t(c, SL_QUEUE, (size_t)qcap, &queue));
+        CK(cudaMemsetAsync(&c->small->queue_len, 0, 4, c->st));
+        WalkParams wp{};
+        wp.T = Tp;
+        wp.Q = Qp;
+        wp.Qrc = Qm;
+        wp.pairs = dpairs;
+        wp.dbits = dbits;
+        wp.span = pat.span;
+        wp.xdrop = params->xdrop;
+        wp.thresh = params->hsp_thresh;
+        wp.flags = params->flags;
+        wp.lane_cap = params->lane_cap > 0 ? params->lane_cap : kDefaultLaneCap;
+        wp.scores = c->small->scores;
+        wp.bhsps = hd;
+        wp.hsp_cap = hcap;
+        wp.ctr = &c->small->ctr;
+        wp.queue = queue;
+        wp.queue_cap = qcap;
+        wp.queue_len = &c->small->queue_len;
+        {
+            Span sp(c, SFE_STAGE_WALK_LANES);
+            CK(launch_walk_lanes(sorted, nh, wp, params->lanes_per_sm, c->st));
+        }
+        {
+            Span sp(c, SFE_STAGE_WALK_WARPS);
+            CK(launch_walk_warps(sorted, nh, wp, 0, c->st));
+        }
+        TRY(sync_small(c));
+        if (c->host_small->ctr.hsps <= hcap) break;
+        hcap = c->host_small->ctr.hsps;
+    }
+    Small sm = *c->host_small;
+    TRY(check_status(sm.status | sm.ctr.status));
+    fill_stats(sm, stats, nh, 1);
+    const unsigned long long found = sm.ctr.hsps;
+    *nhsps = (int64_t)found;
+    int r = SFE_OK;
+    if ((long long)found > cap) {
+        r = fail(SFE_EOVERFLOW, "HSP buffer too small");
+    } else if (found > 0) {
+        Span sp(c, SFE_STAGE_OUTPUT);
+        TRY(ensure(c, SL_TMP, batch_hsp_sort_temp_bytes((long long)found), &tmp));
+        CK(batch_hsp_sort(hd, (long long)found, pbits, bits_for(maxlen), tmp, &c->small->status,
+                          c->st));
+        const bool dev_out = is_device_ptr(hsps);
+        CK(cudaMemcpyAsync(hsps, hd, found * sizeof(BatchHsp),
+                           dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st));
     }
     CK(cudaStreamSynchronize(c->st));
     add_timings(c, stats);

@@ -51,6 +51,23 @@ struct Hsp {
     int32_t strand, tpos, qpos, len, score;
 };
 
+// HSP of a batch of pairs (same layout as sfe_batch_hsp).
+struct BatchHsp {
+    int32_t pair, strand, tpos, qpos, len, score;
+};
+
+// One pair of a batch: where its sequences sit in the concatenated packed
+// buffers and where its seeding buckets sit in the batch index.
+struct PairInfo {
+    long long toff;     // first base of the target in the packed targets
+    long long qoff;     // first base of the query in the packed queries
+    long long qoff_rc;  // first base of its reverse complement in the packed rc buffer
+    long long boff;     // first bucket of its index
+    int tlen, qlen;
+    int bbits;          // its index has 2^bbits buckets (top bits of the seed key)
+    int pad;
+};
+
 // A hit in the walk layout: high word = diagonal index D = t - q + (qlen - span),
 // low word = t. Sorting by the high word (stably, from query order) groups a
 // diagonal's hits in increasing t.
@@ -140,6 +157,12 @@ struct WalkParams {
     uint4 *queue;        // hand-off queue: (hit index, E, unused, unused)
     unsigned long long queue_cap;
     unsigned int *queue_len;
+    // batch of pairs (pairs == nullptr for a single pair): the hit word is
+    // pair << (dbits + 1) | strand << dbits | local diagonal
+    const PairInfo *pairs;
+    const uint32_t *Qrc;  // packed reverse complements of the queries
+    int dbits;
+    BatchHsp *bhsps;
 };
 // Walks of hits sorted by (diagonal word, t): lanes own contiguous hit ranges
 // (lanes_per_sm sizes the ranges; 0 = default); warps finish the diagonals
@@ -154,6 +177,26 @@ cudaError_t launch_walk_warps(const uint64_t *hits, long long n, WalkParams wp, 
 size_t hsp_sort_temp_bytes(long long n);
 cudaError_t hsp_sort(Hsp *hsps, long long n, int tbits, int qbits, void *tmp, uint32_t *status,
                      cudaStream_t st);
+
+// Batch of pairs: per-pair hashed seeding index (cnt and off hold nbuckets and
+// nbuckets + 1 entries, entries one per target seed position), per-pair hit
+// count and write over (strand, query position), and the HSP order (pair,
+// strand, tpos, qpos, len, score) with pairs < 2^pbits, positions < 2^lbits.
+cudaError_t launch_batch_index(const uint32_t *T, const PairInfo *pairs, int npairs,
+                               SeedPattern pat, uint32_t *cnt, long long nbuckets, uint32_t *off,
+                               uint64_t *entries, void *tmp, cudaStream_t st);
+cudaError_t launch_batch_hit_count(const uint32_t *Q, const uint32_t *Qrc, const PairInfo *pairs,
+                                   int npairs, int strands_mask, SeedPattern pat, int transition,
+                                   int dbits, long long qtotal, const uint32_t *off,
+                                   const uint64_t *entries, uint32_t *counts, cudaStream_t st);
+cudaError_t launch_batch_hit_write(const uint32_t *Q, const uint32_t *Qrc, const PairInfo *pairs,
+                                   int npairs, int strands_mask, SeedPattern pat, int transition,
+                                   int dbits, long long qtotal, const uint32_t *off,
+                                   const uint64_t *entries, const unsigned long long *starts,
+                                   uint64_t *hits, cudaStream_t st);
+size_t batch_hsp_sort_temp_bytes(long long n);
+cudaError_t batch_hsp_sort(BatchHsp *h, long long n, int pbits, int lbits, void *tmp,
+                           uint32_t *status, cudaStream_t st);
 
 // Conversions between the public hit record and the walk layout.
 cudaError_t launch_hits_to_public(const uint64_t *hits, long long n, int strand, long long qoff,

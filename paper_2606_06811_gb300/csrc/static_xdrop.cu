@@ -187,7 +187,7 @@ extern "C" int sfe_ungapped_xdrop_static(const uint8_t *target, int64_t tlen,
     if (r != SFE_OK) return r;
     const long long split = nhits > 0 ? (long long)hs.split : 0;
 
-    WalkParams wp;
+    WalkParams wp{};
     wp.T = Tp;
     wp.tlen = tlen;
     wp.qlen = qlen;

@@ -38,17 +38,65 @@ struct Side {
     int scored;  // bases scored
 };
 
-__device__ __forceinline__ void emit(const WalkParams &wp, long long t, long long q, int lblen,
-                                     int rblen, long long score, uint32_t &status) {
+// Where one diagonal's hits live: its pair's sequences and lengths, and its
+// strand. For a single pair everything comes from the launch parameters.
+struct SegCtx {
+    const uint32_t *Q;  // packed query strand buffer
+    long long tb, qb;   // global base of the pair's target and query strand
+    long long tlen, qlen, qoff;
+    long long D;        // local diagonal index
+    int strand, pair;
+};
+
+template <bool BATCH>
+__device__ __forceinline__ void seg_ctx(const WalkParams &wp, uint32_t word, SegCtx &c) {
+    if (BATCH) {
+        c.pair = (int)(word >> (wp.dbits + 1));
+        c.strand = (int)((word >> wp.dbits) & 1u);
+        c.D = (long long)(word & ((1u << wp.dbits) - 1u));
+        const PairInfo P = wp.pairs[c.pair];
+        c.tb = P.toff;
+        c.qb = c.strand ? P.qoff_rc : P.qoff;
+        c.tlen = P.tlen;
+        c.qlen = P.qlen;
+        c.Q = c.strand ? wp.Qrc : wp.Q;
+    } else {
+        c.pair = 0;
+        c.strand = wp.strand;
+        c.D = (long long)(word & 0x7FFFFFFFu);
+        c.tb = 0;
+        c.qb = 0;
+        c.tlen = wp.tlen;
+        c.qlen = wp.qlen;
+        c.Q = wp.Q;
+    }
+    c.qoff = c.qlen - wp.span;
+}
+
+template <bool BATCH>
+__device__ __forceinline__ void emit(const WalkParams &wp, const SegCtx &c, long long t,
+                                     long long q, int lblen, int rblen, long long score,
+                                     uint32_t &status) {
     unsigned long long idx = atomicAdd(&wp.ctr->hsps, 1ull);
     if (idx < wp.hsp_cap) {
-        Hsp h;
-        h.strand = wp.strand;
-        h.tpos = (int32_t)(t - lblen);
-        h.qpos = (int32_t)(q - lblen);
-        h.len = wp.span + lblen + rblen;
-        h.score = (int32_t)score;
-        wp.hsps[idx] = h;
+        if (BATCH) {
+            BatchHsp h;
+            h.pair = c.pair;
+            h.strand = c.strand;
+            h.tpos = (int32_t)(t - lblen);
+            h.qpos = (int32_t)(q - lblen);
+            h.len = wp.span + lblen + rblen;
+            h.score = (int32_t)score;
+            wp.bhsps[idx] = h;
+        } else {
+            Hsp h;
+            h.strand = c.strand;
+            h.tpos = (int32_t)(t - lblen);
+            h.qpos = (int32_t)(q - lblen);
+            h.len = wp.span + lblen + rblen;
+            h.score = (int32_t)score;
+            wp.hsps[idx] = h;
+        }
     } else {
         status |= ST_HSP_OVERFLOW;
     }
@@ -198,7 +246,7 @@ __device__ __forceinline__ void lane_window(const uint32_t *__restrict__ T,
 // hits finish in one iteration, so the warp stays converged while its lanes
 // work on different hits and diagonals. A side that passes `lane_cap` bases
 // hands the rest of its diagonal to the warp tier.
-template <bool PACKED>
+template <bool PACKED, bool BATCH>
 __global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__restrict__ hits,
                                                              uint32_t n, uint32_t chunk,
                                                              WalkParams wp) {
@@ -223,6 +271,8 @@ __global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__r
     uint64_t cur = i < n ? hits[i] : ~0ull, nxt = ~0ull;
     bool in_seg = false, handed = false, busy = false, done = i >= range_end;
     uint32_t D = 0;
+    SegCtx c;
+    seg_ctx<BATCH>(wp, 0u, c);
     long long t = 0, q = 0;
     int E = INT_MIN, cap = wp.lane_cap, s0 = 0, ravail = 0, lavail = 0;
     LaneSide R{0, 0, 0, 0, true}, L{0, 0, 0, 0, true};
@@ -238,6 +288,7 @@ __global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__r
                     break;
                 }
                 D = diag_of(cur);
+                if (BATCH) seg_ctx<BATCH>(wp, D, c);
                 E = wp.Ecarry ? wp.Ecarry[D & 0x7FFFFFFFu] : INT_MIN;
                 in_seg = true;
                 handed = false;
@@ -256,9 +307,9 @@ __global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__r
                 cur = nxt;
                 continue;
             }
-            q = t - (long long)(D & 0x7FFFFFFFu) + wp.qoff;
-            s0 = span_score(wp.T, wp.Q, t, q, span, psum, lut);
-            ravail = (int)min(wp.tlen - t - span, wp.qlen - q - span);
+            q = t - (BATCH ? c.D : (long long)(D & 0x7FFFFFFFu)) + c.qoff;
+            s0 = span_score(wp.T, c.Q, c.tb + t, c.qb + q, span, psum, lut);
+            ravail = (int)min(c.tlen - t - span, c.qlen - q - span);
             lavail = (int)min(t, q);
             R = LaneSide{0, 0, 0, 0, ravail == 0};
             L = LaneSide{0, 0, 0, 0, lavail == 0};
@@ -268,11 +319,11 @@ __global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__r
         // (2) right sides
         const bool needR = busy && !R.done;
         if (__any_sync(0xffffffffu, needR) && needR)
-            lane_window<PACKED>(wp.T, wp.Q, t + span, q + span, 1, ravail, X, lut, R);
+            lane_window<PACKED>(wp.T, c.Q, c.tb + t + span, c.qb + q + span, 1, ravail, X, lut, R);
         // (3) left sides
         const bool needL = busy && !L.done;
         if (__any_sync(0xffffffffu, needL) && needL)
-            lane_window<PACKED>(wp.T, wp.Q, t, q, -1, lavail, X, lut, L);
+            lane_window<PACKED>(wp.T, c.Q, c.tb + t, c.qb + q, -1, lavail, X, lut, L);
         if (busy && (R.best > SCORE_LIMIT || L.best > SCORE_LIMIT)) status |= ST_SCORE_OVERFLOW;
         // (4) finish or hand off
         if (busy && R.done && L.done) {
@@ -281,7 +332,7 @@ __global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__r
             ext++;
             cells += (unsigned long long)(span + R.n + L.n);
             const bool pass = score >= wp.thresh;
-            if (pass) emit(wp, t, q, L.blen, R.blen, score, status);
+            if (pass) emit<BATCH>(wp, c, t, q, L.blen, R.blen, score, status);
             if (pass || !(wp.flags & SFE_SKIP_PASSING_ONLY)) E = (int)(t + span + R.blen);
             i++;
             cur = nxt;
@@ -373,6 +424,7 @@ __device__ __forceinline__ Side warp_side(const uint32_t *__restrict__ T,
     return {best, blen, scored};
 }
 
+template <bool BATCH>
 __global__ void __launch_bounds__(W_BLOCK) walk_warps_kernel(const uint64_t *__restrict__ hits,
                                                              uint32_t nhits, WalkParams wp) {
     __shared__ int lut[16];
@@ -390,7 +442,9 @@ __global__ void __launch_bounds__(W_BLOCK) walk_warps_kernel(const uint64_t *__r
         uint32_t i = it.x;
         int E = (int)it.y;
         const uint32_t dword = diag_of(hits[i]);
-        const long long D = (long long)(dword & 0x7FFFFFFFu);
+        SegCtx c;
+        seg_ctx<BATCH>(wp, dword, c);
+        const long long D = c.D;
         while (i < nhits) {
             const uint64_t h = hits[i];
             if (diag_of(h) != dword) break;
@@ -399,24 +453,26 @@ __global__ void __launch_bounds__(W_BLOCK) walk_warps_kernel(const uint64_t *__r
                 i++;
                 continue;
             }
-            const long long q = t - D + wp.qoff;
+            const long long q = t - D + c.qoff;
             // seed span: lanes 0..span-1
             int s = 0;
-            if (lane < wp.span) s = lut[base_at(wp.T, t + lane) * 4u + base_at(wp.Q, q + lane)];
+            if (lane < wp.span)
+                s = lut[base_at(wp.T, c.tb + t + lane) * 4u + base_at(c.Q, c.qb + q + lane)];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             const long long pt = t + wp.span, pq = q + wp.span;
-            const int ravail = (int)min(wp.tlen - pt, wp.qlen - pq);
+            const int ravail = (int)min(c.tlen - pt, c.qlen - pq);
             const int lavail = (int)min(t, q);
-            const Side r = warp_side(wp.T, wp.Q, pt, pq, +1, ravail, wp.xdrop, lut, lane, status);
-            const Side l = warp_side(wp.T, wp.Q, t - 1, q - 1, -1, lavail, wp.xdrop, lut, lane,
-                                     status);
+            const Side r = warp_side(wp.T, c.Q, c.tb + pt, c.qb + pq, +1, ravail, wp.xdrop, lut,
+                                     lane, status);
+            const Side l = warp_side(wp.T, c.Q, c.tb + t - 1, c.qb + q - 1, -1, lavail, wp.xdrop,
+                                     lut, lane, status);
             const long long score = (long long)s + r.best + l.best;
             if (score > INT_MAX) status |= ST_SCORE_OVERFLOW;
             ext++;
             cells += (unsigned long long)(wp.span + r.scored + l.scored);
             const bool pass = score >= wp.thresh;
-            if (pass && lane == 0) emit(wp, t, q, l.blen, r.blen, score, status);
+            if (pass && lane == 0) emit<BATCH>(wp, c, t, q, l.blen, r.blen, score, status);
             if (pass || !(wp.flags & SFE_SKIP_PASSING_ONLY)) E = (int)(t + wp.span + r.blen);
             i++;
         }
@@ -461,12 +517,16 @@ cudaError_t launch_walk_lanes(const uint64_t *hits, long long n, WalkParams wp, 
     if (chunk < 16) chunk = 16;
     long long nthreads = (n + chunk - 1) / chunk;
     g_launches++;
-    if (wp.xdrop < PACKED_X_LIMIT)
-        walk_lanes_kernel<true><<<grid_for(nthreads, W_BLOCK), W_BLOCK, 0, st>>>(
-            hits, (uint32_t)n, (uint32_t)chunk, wp);
+    const unsigned grid = grid_for(nthreads, W_BLOCK);
+    const bool packed = wp.xdrop < PACKED_X_LIMIT, batch = wp.pairs != nullptr;
+    if (packed && !batch)
+        walk_lanes_kernel<true, false><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, (uint32_t)chunk, wp);
+    else if (!packed && !batch)
+        walk_lanes_kernel<false, false><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, (uint32_t)chunk, wp);
+    else if (packed)
+        walk_lanes_kernel<true, true><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, (uint32_t)chunk, wp);
     else
-        walk_lanes_kernel<false><<<grid_for(nthreads, W_BLOCK), W_BLOCK, 0, st>>>(
-            hits, (uint32_t)n, (uint32_t)chunk, wp);
+        walk_lanes_kernel<false, true><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, (uint32_t)chunk, wp);
     return cudaGetLastError();
 }
 
@@ -476,7 +536,10 @@ cudaError_t launch_walk_warps(const uint64_t *hits, long long n, WalkParams wp, 
     if (grid_warps <= 0) grid_warps = 8 * sms() * (W_BLOCK / 32);
     unsigned grid = (unsigned)((grid_warps * 32 + W_BLOCK - 1) / W_BLOCK);
     g_launches++;
-    walk_warps_kernel<<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, wp);
+    if (wp.pairs)
+        walk_warps_kernel<true><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, wp);
+    else
+        walk_warps_kernel<false><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, wp);
     return cudaGetLastError();
 }
 

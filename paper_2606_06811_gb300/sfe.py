@@ -25,6 +25,8 @@ STAGES = ("pack", "index", "count", "write", "sort", "segments", "walk_lanes", "
 HIT_DTYPE = np.dtype([("strand", "<i4"), ("tpos", "<i4"), ("qpos", "<i4")])
 HSP_DTYPE = np.dtype([("strand", "<i4"), ("tpos", "<i4"), ("qpos", "<i4"), ("len", "<i4"),
                       ("score", "<i4")])
+BATCH_HSP_DTYPE = np.dtype([("pair", "<i4"), ("strand", "<i4"), ("tpos", "<i4"), ("qpos", "<i4"),
+                            ("len", "<i4"), ("score", "<i4")])
 
 
 class SfeError(RuntimeError):
@@ -83,8 +85,10 @@ def lib() -> C.CDLL:
                                          i32, vp, i64, C.POINTER(i64), C.POINTER(Stats)]
         L.sfe_run.argtypes = [vp, vp, i64, vp, i64, C.POINTER(Params), vp, i64, C.POINTER(i64),
                               C.POINTER(Stats)]
+        L.sfe_run_batch.argtypes = [vp, vp, vp, vp, vp, i32, C.POINTER(Params), vp, i64,
+                                    C.POINTER(i64), C.POINTER(Stats)]
         for f in ("sfe_params_default", "sfe_ctx_create", "sfe_ctx_set_stream", "sfe_index_build",
-                  "sfe_seed_hits", "sfe_ungapped_xdrop", "sfe_run"):
+                  "sfe_seed_hits", "sfe_ungapped_xdrop", "sfe_run", "sfe_run_batch"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -229,6 +233,37 @@ class Context:
             return out[: nout.value], st.as_dict()
         return self._retry(cap, lambda buf, cp, nout, st: lib().sfe_run(
             self.h, tptr, tn, qptr, qn, C.byref(p), buf, cp, nout, st))
+
+    def run_batch(self, targets, toff, queries, qoff, params: Params | None = None,
+                  cap: int | None = None, out=None):
+        """Filter stage over a batch of pairs given back to back with int64 offsets (host).
+        Returns (HSPs as numpy BATCH_HSP_DTYPE sorted by pair first, stats), or the first
+        rows of `out` (int32 tensor of shape (cap, 6)) when it is given."""
+        p = params or default_params()
+        tptr, _, tkeep = _buf(targets)
+        qptr, _, qkeep = _buf(queries)
+        to = np.ascontiguousarray(toff, dtype=np.int64)
+        qo = np.ascontiguousarray(qoff, dtype=np.int64)
+        npairs = int(to.size - 1)
+        nout = C.c_int64(0)
+        st = Stats()
+        if out is not None:
+            optr, on, _ = _buf(out)
+            _check(lib().sfe_run_batch(self.h, tptr, to.ctypes.data, qptr, qo.ctypes.data, npairs,
+                                       C.byref(p), optr, on // BATCH_HSP_DTYPE.itemsize,
+                                       C.byref(nout), C.byref(st)))
+            return out[: nout.value], st.as_dict()
+        cap = 1 << 16 if cap is None else int(cap)
+        while True:
+            buf = np.zeros(max(cap, 1), dtype=BATCH_HSP_DTYPE)
+            code = lib().sfe_run_batch(self.h, tptr, to.ctypes.data, qptr, qo.ctypes.data, npairs,
+                                       C.byref(p), buf.ctypes.data, cap, C.byref(nout),
+                                       C.byref(st))
+            if code == EOVERFLOW and nout.value > cap:
+                cap = int(nout.value)
+                continue
+            _check(code)
+            return buf[: nout.value], st.as_dict()
 
     def _retry(self, cap, call):
         cap = 1 << 16 if cap is None else int(cap)

@@ -1,0 +1,75 @@
+"""Batch of uneven pairs (sfe_run_batch) against the oracle run pair by pair.
+
+Bit-exact per pair: the batch HSP list, split by pair, equals the oracle's
+list for that pair; hits, extended hits and cells add up to the oracle's.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth.workloads import concat_batch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2606_06811_gb300 as P
+    return P
+
+
+def oracle_batch(pairs, **kw):
+    rows, hits, ext, cells = [], 0, 0, 0
+    for i, p in enumerate(pairs):
+        r = oracle.run(p.T, p.Q, **kw)
+        h = r.hsps.view(np.int32).reshape(-1, 5)
+        rows.append(np.concatenate([np.full((h.shape[0], 1), i, np.int32), h], 1))
+        hits, ext, cells = hits + r.hits, ext + r.extended, cells + r.cells
+    H = np.concatenate(rows) if rows else np.zeros((0, 6), np.int32)
+    return H, hits, ext, cells
+
+
+def gpu_batch(P, pairs, **kw):
+    T, toff, Q, qoff = concat_batch(pairs)
+    with P.Context(0) as ctx:
+        h, st = ctx.run_batch(T, toff, Q, qoff, P.default_params(input_codes=1, **kw))
+    return np.ascontiguousarray(h).view(np.int32).reshape(-1, 6), st
+
+
+def check(P, pairs, **kw):
+    okw = {("thresh" if k == "hsp_thresh" else k): v for k, v in kw.items()
+           if k not in ("lane_cap", "lanes_per_sm", "tile_hits")}
+    H, hits, ext, cells = oracle_batch(pairs, **okw)
+    G, st = gpu_batch(P, pairs, **kw)
+    assert G.shape == H.shape and np.array_equal(G, H)
+    assert (st["hits"], st["extended"], st["cells"]) == (hits, ext, cells)
+    return G
+
+
+def test_batch_uneven_pairs(pkg):
+    pairs = synth.batch_pairs(seed=3, n_pairs=96, len_lo=1000, len_hi=40_000)
+    G = check(pkg, pairs)
+    assert len(np.unique(G[:, 0])) > 10
+
+
+def test_batch_with_degenerate_pairs(pkg):
+    st = synth.Stream(8, "deg")
+    pairs = []
+    for i, (n, m) in enumerate([(0, 50), (18, 18), (19, 19), (5000, 10), (3000, 3000), (1, 1),
+                                (700, 900)]):
+        T = synth.iid_bases(st.child("T", i), n, 0.5)
+        Q = T[:m].copy() if n >= m else synth.iid_bases(st.child("Q", i), m, 0.5)
+        pairs.append(synth.Pair(T, Q))
+    check(pkg, pairs, hsp_thresh=0)
+
+
+def test_batch_single_strand_and_lane_cap(pkg):
+    pairs = synth.batch_pairs(seed=4, n_pairs=40, len_lo=2000, len_hi=30_000)
+    check(pkg, pairs, strands=2, lane_cap=16)
+    check(pkg, pairs, strands=1)
