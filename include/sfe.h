@@ -69,7 +69,7 @@ enum {
     SFE_STAGE_COUNT = 2,      /* hits per query position and their scan */
     SFE_STAGE_WRITE = 3,      /* hit records */
     SFE_STAGE_SORT = 4,       /* grouping of hits by diagonal */
-    SFE_STAGE_SEGMENTS = 5,   /* diagonal segment heads */
+    SFE_STAGE_SCHEDULE = 5,   /* order of the persistent walk's work chunks */
     SFE_STAGE_WALK_LANES = 6, /* skip + X-drop, one lane per diagonal */
     SFE_STAGE_WALK_WARPS = 7, /* skip + X-drop, one warp per handed-off diagonal */
     SFE_STAGE_OUTPUT = 8,     /* HSP sort and copy-out */
@@ -106,7 +106,21 @@ typedef struct {
     int32_t lane_cap;         /* bases per side a lane extends before handing the diagonal to a warp; 0 = default */
     int32_t lanes_per_sm;     /* lane-tier threads per SM sharing a tile's hits (sizes their hit ranges); 0 = default */
     int64_t tile_hits;        /* hits per query tile (bounds scratch memory); 0 = default */
+    int32_t walk_chunk;       /* hits a lane takes per grab from the work counter; 0 = default (32) */
+    int32_t walk_mode;        /* SFE_WALK_PERSISTENT (default) or SFE_WALK_TWO_LAUNCHES */
+    int32_t walk_schedule;    /* order in which the persistent walk hands out chunks (SFE_SCHED_*) */
+    int32_t reserved2;
 } sfe_params;
+
+/* sfe_params.walk_schedule: the order of work never changes the output, only
+ * how evenly it spreads over the warps */
+#define SFE_SCHED_NATURAL 0       /* chunks in hit order */
+#define SFE_SCHED_LARGEST_FIRST 1 /* chunks starting in larger diagonals (more hits) first */
+
+/* sfe_params.walk_mode */
+#define SFE_WALK_PERSISTENT 0   /* one launch: lanes pull chunks from a device counter, then
+                                   the same warps drain the hand-off queue */
+#define SFE_WALK_TWO_LAUNCHES 1 /* lanes own fixed hit ranges; a second launch drains the queue */
 
 /* Statistics of one call. cells is the work measure of the method: seed span
  * plus the bases scored on both sides, summed over hits that were extended. */

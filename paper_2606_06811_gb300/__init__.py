@@ -6,6 +6,6 @@ include/sfe.h. `sfe` is the Python binding (argument marshalling only);
 `build` compiles the library in-tree.
 """
 from .sfe import (  # noqa: F401
-    BATCH_HSP_DTYPE, HIT_DTYPE, HSP_DTYPE, SKIP_PASSING_ONLY, STAGES, TIME_STAGES, Context, Index, Params, SfeError, Stats,
+    BATCH_HSP_DTYPE, HIT_DTYPE, HSP_DTYPE, SKIP_PASSING_ONLY, STAGES, TIME_STAGES, WALK_PERSISTENT, WALK_TWO_LAUNCHES, SCHED_NATURAL, SCHED_LARGEST_FIRST, Context, Index, Params, SfeError, Stats,
     default_params, exported_symbols, lib,
 )

@@ -44,11 +44,11 @@ const char *kDefaultPattern = "1110100110010101111";
 
 constexpr int kDefaultLaneCap = 96;
 constexpr long long kDefaultTileHits = 1LL << 28;
-constexpr unsigned long long kQueueMax = 1ull << 22;
+constexpr unsigned long long kQueueMax = 1ull << 20;
 
 enum Slot {
     SL_TIN, SL_QIN, SL_TP, SL_QP, SL_QM, SL_KEYS_A, SL_KEYS_B, SL_BCOUNT, SL_OFFS, SL_POS,
-    SL_COUNTS, SL_STARTS, SL_HITS_A, SL_HITS_B, SL_QUEUE, SL_PAIRS, SL_BENTRIES,
+    SL_COUNTS, SL_STARTS, SL_HITS_A, SL_HITS_B, SL_QUEUE, SL_PAIRS, SL_BENTRIES, SL_SCHED,
     SL_HSPS, SL_TMP, SL_ECARRY, SL_PUB, SL_BOUNDS, NSLOT
 };
 
@@ -59,7 +59,11 @@ struct Small {
     uint32_t status;       // pack / conversion status
     uint32_t queue_len;
     unsigned long long split;
-    unsigned long long pad[4];
+    uint32_t work_next;    // persistent walk: next chunk ticket
+    uint32_t warps_done;   // persistent walk: warps out of lane work
+    uint32_t queue_take;   // persistent walk: next queue entry to consume
+    uint32_t pad0;
+    unsigned long long pad[2];
 };
 
 int bits_for(long long v) {
@@ -91,6 +95,8 @@ struct sfe_ctx {
     size_t cap[NSLOT] = {};
     Small *small = nullptr;       // device
     Small *host_small = nullptr;  // pinned mirror
+    uint32_t epoch = 0;           // tag of the current call's hand-off queue entries
+    unsigned long long batch_hits_hint = 0;  // hits of the last batch (room for the next)
     StageTimer tm;
     unsigned long long launches0 = 0;
 };
@@ -203,6 +209,11 @@ int check_params(const sfe_params *p) {
     if (p->strands < 1 || p->strands > 3) return fail(SFE_EINVAL, "strands must be 1, 2 or 3");
     if (p->lane_cap < 0) return fail(SFE_EINVAL, "lane_cap must be >= 0");
     if (p->lanes_per_sm < 0) return fail(SFE_EINVAL, "lanes_per_sm must be >= 0");
+    if (p->walk_chunk < 0) return fail(SFE_EINVAL, "walk_chunk must be >= 0");
+    if (p->walk_mode != SFE_WALK_PERSISTENT && p->walk_mode != SFE_WALK_TWO_LAUNCHES)
+        return fail(SFE_EINVAL, "walk_mode must be SFE_WALK_PERSISTENT or SFE_WALK_TWO_LAUNCHES");
+    if (p->walk_schedule != SFE_SCHED_NATURAL && p->walk_schedule != SFE_SCHED_LARGEST_FIRST)
+        return fail(SFE_EINVAL, "unknown walk_schedule");
     if (p->tile_hits < 0) return fail(SFE_EINVAL, "tile_hits must be >= 0");
     if (p->input_codes != 0 && p->input_codes != 1) return fail(SFE_EINVAL, "input_codes must be 0 or 1");
     for (int i = 0; i < 16; i++)
@@ -392,13 +403,52 @@ struct WalkSetup {
     unsigned long long hsp_cap;
 };
 
+// The lane and warp tiers over hits sorted by (diagonal word, t), in one
+// persistent launch or as two launches (params->walk_mode).
+int walk_tiers(sfe_ctx *c, const uint64_t *hits, long long n, WalkParams &wp, uint4 *queue,
+               unsigned long long qcap, const sfe_params *p) {
+    wp.queue = queue;
+    wp.queue_cap = qcap;
+    wp.queue_len = &c->small->queue_len;
+    CK(cudaMemsetAsync(&c->small->queue_len, 0, 4, c->st));
+    if (p->walk_mode == SFE_WALK_TWO_LAUNCHES) {
+        {
+            Span sp(c, SFE_STAGE_WALK_LANES);
+            CK(launch_walk_lanes(hits, n, wp, p->lanes_per_sm, c->st));
+        }
+        Span sp(c, SFE_STAGE_WALK_WARPS);
+        CK(launch_walk_warps(hits, n, wp, 0, c->st));
+        return SFE_OK;
+    }
+    if (++c->epoch == 0) c->epoch = 1;
+    wp.epoch = c->epoch;
+    wp.work_next = &c->small->work_next;
+    wp.warps_done = &c->small->warps_done;
+    wp.queue_take = &c->small->queue_take;
+    wp.chunk = p->walk_chunk > 0 ? (uint32_t)p->walk_chunk : 32u;
+    wp.order = nullptr;
+    if (p->walk_schedule != SFE_SCHED_NATURAL) {
+        Span sp(c, SFE_STAGE_SCHEDULE);
+        void *tmp = nullptr;
+        TRY(ensure(c, SL_SCHED, walk_schedule_temp_bytes(n, wp.chunk), &tmp));
+        uint32_t *order = nullptr;
+        CK(launch_walk_schedule(hits, n, wp.chunk, p->walk_schedule, tmp, &order,
+                                &c->small->status, c->st));
+        wp.order = order;
+    }
+    Span sp(c, SFE_STAGE_WALK_LANES);
+    CK(cudaMemsetAsync(&c->small->work_next, 0, 12, c->st));
+    CK(cudaMemsetAsync(queue, 0, (size_t)qcap * sizeof(uint4), c->st));
+    CK(launch_walk_persistent(hits, n, wp, c->st));
+    return SFE_OK;
+}
+
 // Lane and warp walks of hits sorted by (diagonal, t).
 int walk_sorted(sfe_ctx *c, const uint64_t *hits, long long n, const WalkSetup &ws) {
     if (n <= 0) return SFE_OK;
     uint4 *queue = nullptr;
     const unsigned long long qcap = std::min<unsigned long long>((unsigned long long)n, kQueueMax);
     TRY(ensure_t(c, SL_QUEUE, (size_t)qcap, &queue));
-    CK(cudaMemsetAsync(&c->small->queue_len, 0, 4, c->st));
     WalkParams wp{};
     wp.T = ws.T;
     wp.Q = ws.Qs;
@@ -416,18 +466,7 @@ int walk_sorted(sfe_ctx *c, const uint64_t *hits, long long n, const WalkSetup &
     wp.hsps = ws.hsps;
     wp.hsp_cap = ws.hsp_cap;
     wp.ctr = &c->small->ctr;
-    wp.queue = queue;
-    wp.queue_cap = qcap;
-    wp.queue_len = &c->small->queue_len;
-    {
-        Span sp(c, SFE_STAGE_WALK_LANES);
-        CK(launch_walk_lanes(hits, n, wp, ws.p->lanes_per_sm, c->st));
-    }
-    {
-        Span sp(c, SFE_STAGE_WALK_WARPS);
-        CK(launch_walk_warps(hits, n, wp, 0, c->st));
-    }
-    return SFE_OK;
+    return walk_tiers(c, hits, n, wp, queue, qcap, ws.p);
 }
 
 // Sort the HSPs found and copy them out; sets *nhsps (SFE_EOVERFLOW if > cap).
@@ -917,10 +956,28 @@ int sfe_run_batch(sfe_ctx *c, const uint8_t *targets, const int64_t *toff, const
         x.pad = 0;
         nbuckets += 1LL << x.bbits;
     }
-    PairInfo *dpairs = nullptr;
-    TRY(ensure_t(c, SL_PAIRS, (size_t)npairs, &dpairs));
+    // work items: chunks of one pair's target / query positions, pair by pair
+    const int item = batch_item_size();
+    std::vector<long long> pref(2 * (size_t)(npairs + 1));
+    long long *tpref = pref.data(), *qpref = pref.data() + npairs + 1;
+    tpref[0] = qpref[0] = 0;
+    for (int p = 0; p < npairs; p++) {
+        const long long nt = std::max(0LL, (long long)P[p].tlen - pat.span + 1);
+        const long long nq = std::max(0LL, (long long)P[p].qlen - pat.span + 1);
+        tpref[p + 1] = tpref[p] + (nt + item - 1) / item;
+        qpref[p + 1] = qpref[p] + 2 * ((nq + item - 1) / item);
+    }
+    const long long titems = tpref[npairs], qitems = qpref[npairs];
+    if (titems >= (1LL << 31) || qitems >= (1LL << 31)) return fail(SFE_EINVAL, "batch too large");
+    const size_t pbytes = ((size_t)npairs * sizeof(PairInfo) + 255) & ~(size_t)255;
+    unsigned char *dmeta = nullptr;
+    TRY(ensure_t(c, SL_PAIRS, pbytes + pref.size() * 8, &dmeta));
+    PairInfo *dpairs = reinterpret_cast<PairInfo *>(dmeta);
+    long long *dtpref = reinterpret_cast<long long *>(dmeta + pbytes);
+    long long *dqpref = dtpref + npairs + 1;
     CK(cudaMemcpyAsync(dpairs, P.data(), (size_t)npairs * sizeof(PairInfo), cudaMemcpyHostToDevice,
                        c->st));
+    CK(cudaMemcpyAsync(dtpref, pref.data(), pref.size() * 8, cudaMemcpyHostToDevice, c->st));
 
     uint32_t *Tp = nullptr, *Qp = nullptr, *Qm = nullptr;
     {
@@ -943,35 +1000,38 @@ int sfe_run_batch(sfe_ctx *c, const uint8_t *targets, const int64_t *toff, const
         TRY(ensure_t(c, SL_OFFS, (size_t)nbuckets + 1, &boffs));
         TRY(ensure_t(c, SL_BENTRIES, (size_t)std::max(1LL, ttot), &entries));
         TRY(ensure(c, SL_TMP, std::max(scan_temp_bytes(nbuckets), scan_temp_bytes(2 * qtot)), &tmp));
-        CK(launch_batch_index(Tp, dpairs, npairs, pat, bcnt, nbuckets, boffs, entries, tmp, c->st));
+        CK(launch_batch_index(Tp, dpairs, dtpref, titems, npairs, pat, bcnt, nbuckets, boffs,
+                              entries, tmp, c->st));
     }
-    uint32_t *counts = nullptr;
-    unsigned long long *starts = nullptr, total = 0;
-    {
-        Span sp(c, SFE_STAGE_COUNT);
-        TRY(ensure_t(c, SL_COUNTS, (size_t)std::max(1LL, 2 * qtot), &counts));
-        TRY(ensure_t(c, SL_STARTS, (size_t)(2 * qtot + 1), &starts));
-        CK(launch_batch_hit_count(Qp, Qm, dpairs, npairs, params->strands, pat, params->transition,
-                                  dbits, qtot, boffs, entries, counts, c->st));
-        CK(scan_u32_to_u64(counts, starts, 2 * qtot, tmp, c->st));
-        CK(cudaMemcpyAsync(&total, starts + 2 * qtot, 8, cudaMemcpyDeviceToHost, c->st));
+    // hits in one pass: the room for them is the previous batch's count (grown
+    // and the pass repeated when it was too small), and a sort by the whole
+    // hit word restores a fixed order
+    unsigned long long total = 0;
+    uint64_t *ha = nullptr, *hb = nullptr;
+    unsigned long long hitcap = std::max<unsigned long long>(c->batch_hits_hint, 1ull << 20);
+    for (int attempt = 0; attempt < 2; attempt++) {
+        TRY(ensure_t(c, SL_HITS_A, (size_t)hitcap, &ha));
+        Span sp(c, SFE_STAGE_WRITE);
+        CK(launch_batch_hit_emit(Qp, Qm, dpairs, dqpref, qitems, npairs, params->strands, pat,
+                                 params->transition, dbits, boffs, entries, &c->small->split,
+                                 hitcap, ha, c->st));
+        CK(cudaMemcpyAsync(&total, &c->small->split, 8, cudaMemcpyDeviceToHost, c->st));
         CK(cudaStreamSynchronize(c->st));
+        if (total <= hitcap) break;
+        hitcap = total + total / 8;
     }
+    c->batch_hits_hint = total + total / 16;
     if (total >= (1ull << 32)) return fail(SFE_EINVAL, "a batch may hold at most 2^32 - 1 hits");
     const long long nh = (long long)total;
-    uint64_t *ha = nullptr, *hb = nullptr;
-    TRY(ensure_t(c, SL_HITS_A, (size_t)std::max(1LL, nh), &ha));
     TRY(ensure_t(c, SL_HITS_B, (size_t)std::max(1LL, nh), &hb));
     TRY(ensure(c, SL_TMP, radix_sort_temp_bytes(nh), &tmp));
-    {
-        Span sp(c, SFE_STAGE_WRITE);
-        CK(launch_batch_hit_write(Qp, Qm, dpairs, npairs, params->strands, pat,
-                                  params->transition, dbits, qtot, boffs, entries, starts, ha,
-                                  c->st));
-    }
     bool in_b = false;
     {
         Span sp(c, SFE_STAGE_SORT);
+        // local t, then (pair, strand, diagonal): two stable passes, least significant first
+        CK(radix_sort(ha, hb, nullptr, nullptr, nh, 0, bits_for(maxlen), tmp, &in_b,
+                      &c->small->status, c->st));
+        if (in_b) std::swap(ha, hb);
         CK(radix_sort(ha, hb, nullptr, nullptr, nh, 32, 32 + pbits + 1 + dbits, tmp, &in_b,
                       &c->small->status, c->st));
     }
@@ -986,7 +1046,6 @@ int sfe_run_batch(sfe_ctx *c, const uint8_t *targets, const int64_t *toff, const
         const unsigned long long qcap =
             std::min<unsigned long long>((unsigned long long)std::max(1LL, nh), kQueueMax);
         TRY(ensure_t(c, SL_QUEUE, (size_t)qcap, &queue));
-        CK(cudaMemsetAsync(&c->small->queue_len, 0, 4, c->st));
         WalkParams wp{};
         wp.T = Tp;
         wp.Q = Qp;
@@ -1002,17 +1061,7 @@ int sfe_run_batch(sfe_ctx *c, const uint8_t *targets, const int64_t *toff, const
         wp.bhsps = hd;
         wp.hsp_cap = hcap;
         wp.ctr = &c->small->ctr;
-        wp.queue = queue;
-        wp.queue_cap = qcap;
-        wp.queue_len = &c->small->queue_len;
-        {
-            Span sp(c, SFE_STAGE_WALK_LANES);
-            CK(launch_walk_lanes(sorted, nh, wp, params->lanes_per_sm, c->st));
-        }
-        {
-            Span sp(c, SFE_STAGE_WALK_WARPS);
-            CK(launch_walk_warps(sorted, nh, wp, 0, c->st));
-        }
+        TRY(walk_tiers(c, sorted, nh, wp, queue, qcap, params));
         TRY(sync_small(c));
         if (c->host_small->ctr.hsps <= hcap) break;
         hcap = c->host_small->ctr.hsps;

@@ -163,6 +163,14 @@ struct WalkParams {
     const uint32_t *Qrc;  // packed reverse complements of the queries
     int dbits;
     BatchHsp *bhsps;
+    // persistent walk: lanes take chunks of `chunk` hits from a work counter
+    // (in `order` when given), and warps out of lane work consume the hand-off
+    // queue in the same launch; queue entries of this call carry `epoch`
+    unsigned int *work_next;
+    unsigned int *warps_done;
+    unsigned int *queue_take;
+    const uint32_t *order;
+    uint32_t nchunks, chunk, epoch;
 };
 // Walks of hits sorted by (diagonal word, t): lanes own contiguous hit ranges
 // (lanes_per_sm sizes the ranges; 0 = default); warps finish the diagonals
@@ -171,6 +179,15 @@ cudaError_t launch_walk_lanes(const uint64_t *hits, long long n, WalkParams wp, 
                               cudaStream_t st);
 cudaError_t launch_walk_warps(const uint64_t *hits, long long n, WalkParams wp, int grid_warps,
                               cudaStream_t st);
+// Chunk order of the persistent walk for a schedule (SFE_SCHED_*): *order is
+// left null for the natural order. tmp: walk_schedule_temp_bytes(n, chunk).
+size_t walk_schedule_temp_bytes(long long n, uint32_t chunk);
+cudaError_t launch_walk_schedule(const uint64_t *hits, long long n, uint32_t chunk, int schedule,
+                                 void *tmp, uint32_t **order, uint32_t *status, cudaStream_t st);
+// Both tiers in one persistent launch fed by the work counter and the queue
+// (wp.work_next, warps_done, queue_take, queue_len zeroed by the caller).
+cudaError_t launch_walk_persistent(const uint64_t *hits, long long n, WalkParams wp,
+                                   cudaStream_t st);
 
 // Sort HSPs in place by (strand, tpos, qpos, len, score); tpos < 2^tbits,
 // qpos < 2^qbits, tbits + qbits <= 62. tmp: hsp_sort_temp_bytes(n).
@@ -182,18 +199,32 @@ cudaError_t hsp_sort(Hsp *hsps, long long n, int tbits, int qbits, void *tmp, ui
 // nbuckets + 1 entries, entries one per target seed position), per-pair hit
 // count and write over (strand, query position), and the HSP order (pair,
 // strand, tpos, qpos, len, score) with pairs < 2^pbits, positions < 2^lbits.
-cudaError_t launch_batch_index(const uint32_t *T, const PairInfo *pairs, int npairs,
-                               SeedPattern pat, uint32_t *cnt, long long nbuckets, uint32_t *off,
-                               uint64_t *entries, void *tmp, cudaStream_t st);
+// Work items are chunks of batch_item_size() positions of one pair, numbered
+// pair by pair: tprefix / qprefix (npairs + 1 entries, device) give each pair's
+// first item; query items hold both strands of a chunk next to each other.
+int batch_item_size();
+cudaError_t launch_batch_index(const uint32_t *T, const PairInfo *pairs, const long long *tprefix,
+                               long long titems, int npairs, SeedPattern pat, uint32_t *cnt,
+                               long long nbuckets, uint32_t *off, uint64_t *entries, void *tmp,
+                               cudaStream_t st);
 cudaError_t launch_batch_hit_count(const uint32_t *Q, const uint32_t *Qrc, const PairInfo *pairs,
-                                   int npairs, int strands_mask, SeedPattern pat, int transition,
-                                   int dbits, long long qtotal, const uint32_t *off,
-                                   const uint64_t *entries, uint32_t *counts, cudaStream_t st);
+                                   const long long *qprefix, long long qitems, int npairs,
+                                   int strands_mask, SeedPattern pat, int transition, int dbits,
+                                   long long qtotal, const uint32_t *off, const uint64_t *entries,
+                                   uint32_t *counts, cudaStream_t st);
 cudaError_t launch_batch_hit_write(const uint32_t *Q, const uint32_t *Qrc, const PairInfo *pairs,
-                                   int npairs, int strands_mask, SeedPattern pat, int transition,
-                                   int dbits, long long qtotal, const uint32_t *off,
-                                   const uint64_t *entries, const unsigned long long *starts,
-                                   uint64_t *hits, cudaStream_t st);
+                                   const long long *qprefix, long long qitems, int npairs,
+                                   int strands_mask, SeedPattern pat, int transition, int dbits,
+                                   long long qtotal, const uint32_t *off, const uint64_t *entries,
+                                   const unsigned long long *starts, uint64_t *hits,
+                                   cudaStream_t st);
+// One pass: hits in no particular order, at most cap written, *total = all.
+cudaError_t launch_batch_hit_emit(const uint32_t *Q, const uint32_t *Qrc, const PairInfo *pairs,
+                                  const long long *qprefix, long long qitems, int npairs,
+                                  int strands_mask, SeedPattern pat, int transition, int dbits,
+                                  const uint32_t *off, const uint64_t *entries,
+                                  unsigned long long *total, unsigned long long cap,
+                                  uint64_t *hits, cudaStream_t st);
 size_t batch_hsp_sort_temp_bytes(long long n);
 cudaError_t batch_hsp_sort(BatchHsp *h, long long n, int pbits, int lbits, void *tmp,
                            uint32_t *status, cudaStream_t st);

@@ -31,6 +31,7 @@ namespace {
 
 constexpr int W_BLOCK = 256;
 constexpr int SCORE_LIMIT = 1 << 30;  // a best score above this flags overflow
+constexpr long long QUEUE_SPIN_LIMIT = 1LL << 26;  // polls of an empty hand-off queue before giving up
 
 struct Side {
     int best;    // maximum of the running sum (0 for the empty extension)
@@ -235,6 +236,12 @@ __device__ __forceinline__ void lane_window(const uint32_t *__restrict__ T,
     sd.done = a == 0 || sd.n >= avail;
 }
 
+template <bool BATCH>
+__device__ void warp_walk_diagonal(const uint64_t *__restrict__ hits, uint32_t nhits, uint32_t i,
+                                   int E, const WalkParams &wp, const int *lut, int lane,
+                                   unsigned long long &ext, unsigned long long &cells,
+                                   uint32_t &status);
+
 // Lane tier. Lane k owns the diagonals that start in hit range
 // [k*chunk, (k+1)*chunk) and streams through its hits in order, with the next
 // hit prefetched. The lanes of a warp advance in lock step, one iteration at
@@ -246,7 +253,7 @@ __device__ __forceinline__ void lane_window(const uint32_t *__restrict__ T,
 // hits finish in one iteration, so the warp stays converged while its lanes
 // work on different hits and diagonals. A side that passes `lane_cap` bases
 // hands the rest of its diagonal to the warp tier.
-template <bool PACKED, bool BATCH>
+template <bool PACKED, bool BATCH, bool PERSIST>
 __global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__restrict__ hits,
                                                              uint32_t n, uint32_t chunk,
                                                              WalkParams wp) {
@@ -261,15 +268,15 @@ __global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__r
     __syncthreads();
     const int span = wp.span, X = wp.xdrop;
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long lo64 = tid * (long long)chunk;
-    const uint32_t range_end = (uint32_t)min((long long)n, lo64 + chunk);
+    const long long lo64 = PERSIST ? 0 : tid * (long long)chunk;
+    uint32_t range_end = PERSIST ? 0u : (uint32_t)min((long long)n, lo64 + chunk);
 
     uint32_t i = (uint32_t)min((long long)n, lo64);
     // a diagonal that started before this range belongs to the previous lane
-    if (i > 0 && i < range_end && diag_of(hits[i]) == diag_of(hits[i - 1]))
+    if (!PERSIST && i > 0 && i < range_end && diag_of(hits[i]) == diag_of(hits[i - 1]))
         i = segment_end(hits, i, n, diag_of(hits[i]));
-    uint64_t cur = i < n ? hits[i] : ~0ull, nxt = ~0ull;
-    bool in_seg = false, handed = false, busy = false, done = i >= range_end;
+    uint64_t cur = (!PERSIST && i < n) ? hits[i] : ~0ull, nxt = ~0ull;
+    bool in_seg = false, handed = false, busy = false, done = !PERSIST && i >= range_end;
     uint32_t D = 0;
     SegCtx c;
     seg_ctx<BATCH>(wp, 0u, c);
@@ -284,8 +291,23 @@ __global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__r
         while (!busy && !done) {
             if (!in_seg) {
                 if (i >= range_end) {
-                    done = true;
-                    break;
+                    if (!PERSIST) {
+                        done = true;
+                        break;
+                    }
+                    // take the next chunk of hits from the work counter
+                    const uint32_t w = atomicAdd(wp.work_next, 1u);
+                    if (w >= wp.nchunks) {
+                        done = true;
+                        break;
+                    }
+                    const uint32_t ck = wp.order ? wp.order[w] : w;
+                    i = ck * wp.chunk;
+                    range_end = (uint32_t)min((long long)n, (long long)i + wp.chunk);
+                    if (i > 0 && i < range_end && diag_of(hits[i]) == diag_of(hits[i - 1]))
+                        i = segment_end(hits, i, n, diag_of(hits[i]));
+                    cur = i < n ? hits[i] : ~0ull;
+                    continue;
                 }
                 D = diag_of(cur);
                 if (BATCH) seg_ctx<BATCH>(wp, D, c);
@@ -341,7 +363,15 @@ __global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__r
             // a long extension: the rest of this diagonal goes to a warp
             unsigned int slot = atomicAdd(wp.queue_len, 1u);
             if (slot < wp.queue_cap) {
-                wp.queue[slot] = make_uint4(i, (uint32_t)E, 0u, 0u);
+                if (PERSIST) {
+                    // entry first, then its epoch tag: a consumer that sees the tag sees the entry
+                    wp.queue[slot].x = i;
+                    wp.queue[slot].y = (uint32_t)E;
+                    __threadfence();
+                    atomicExch(&wp.queue[slot].z, wp.epoch);
+                } else {
+                    wp.queue[slot] = make_uint4(i, (uint32_t)E, 0u, 0u);
+                }
                 handed = true;
                 i = segment_end(hits, i, n, D);
                 cur = i < n ? hits[i] : ~0ull;
@@ -359,12 +389,62 @@ __global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__r
         tasks += __shfl_down_sync(0xffffffffu, tasks, o);
         status |= __shfl_down_sync(0xffffffffu, status, o);
     }
-    if ((threadIdx.x & 31) == 0) {
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) {
         if (ext) atomicAdd(&wp.ctr->extended, ext);
         if (cells) atomicAdd(&wp.ctr->cells, cells);
         if (tasks) atomicAdd(&wp.ctr->lane_tasks, tasks);
-        if (status) atomicOr(&wp.ctr->status, status);
     }
+    if (PERSIST) {
+        // this warp's lanes are out of work: consume the hand-off queue
+        __threadfence();
+        if (lane == 0) atomicAdd(wp.warps_done, 1u);
+        const unsigned total_warps = gridDim.x * (W_BLOCK / 32);
+        unsigned long long wext = 0, wcells = 0, wtasks = 0;
+        while (true) {
+            unsigned e = 0;
+            if (lane == 0) e = atomicAdd(wp.queue_take, 1u);
+            e = __shfl_sync(0xffffffffu, e, 0);
+            if (e >= wp.queue_cap) break;
+            int state = 0;  // 1: entry ready, 2: no entry will come
+            long long spins = 0;
+            while (state == 0) {
+                if (lane == 0) {
+                    volatile uint4 *qe = wp.queue + e;
+                    if (qe->z == wp.epoch) {
+                        state = 1;
+                    } else {
+                        const unsigned wd = *(volatile unsigned *)wp.warps_done;
+                        const unsigned ql = *(volatile unsigned *)wp.queue_len;
+                        if (wd >= total_warps && e >= min(ql, (unsigned)wp.queue_cap)) state = 2;
+                        else if (++spins > QUEUE_SPIN_LIMIT) {
+                            status |= ST_TIMEOUT;
+                            state = 2;
+                        }
+                    }
+                }
+                state = __shfl_sync(0xffffffffu, state, 0);
+            }
+            if (state == 2) break;
+            __threadfence();
+            volatile uint4 *qe = wp.queue + e;
+            const uint32_t hi_idx = qe->x;
+            const int hi_E = (int)qe->y;
+            wtasks++;
+            warp_walk_diagonal<BATCH>(hits, n, hi_idx, hi_E, wp, lut, lane, wext, wcells, status);
+        }
+        if (lane == 0) {
+            if (wext) atomicAdd(&wp.ctr->extended, wext);
+            if (wcells) {
+                atomicAdd(&wp.ctr->cells, wcells);
+                atomicAdd(&wp.ctr->warp_cells, wcells);
+            }
+            if (wtasks) atomicAdd(&wp.ctr->warp_tasks, wtasks);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) status |= __shfl_down_sync(0xffffffffu, status, o);
+    }
+    if (lane == 0 && status) atomicOr(&wp.ctr->status, status);
 }
 
 // ------------------------------------------------------------------ warps
@@ -424,6 +504,51 @@ __device__ __forceinline__ Side warp_side(const uint32_t *__restrict__ T,
     return {best, blen, scored};
 }
 
+// The warp tier on one handed-off diagonal: from hit i with skip state E to
+// the end of the diagonal, every extension in 32-base chunks.
+template <bool BATCH>
+__device__ void warp_walk_diagonal(const uint64_t *__restrict__ hits, uint32_t nhits, uint32_t i,
+                                   int E, const WalkParams &wp, const int *lut, int lane,
+                                   unsigned long long &ext, unsigned long long &cells,
+                                   uint32_t &status) {
+    const uint32_t dword = diag_of(hits[i]);
+    SegCtx c;
+    seg_ctx<BATCH>(wp, dword, c);
+    const long long D = c.D;
+    while (i < nhits) {
+        const uint64_t h = hits[i];
+        if (diag_of(h) != dword) break;
+        const long long t = (long long)(uint32_t)h;
+        if (t < E) {
+            i++;
+            continue;
+        }
+        const long long q = t - D + c.qoff;
+        // seed span: lanes 0..span-1
+        int s = 0;
+        if (lane < wp.span)
+            s = lut[base_at(wp.T, c.tb + t + lane) * 4u + base_at(c.Q, c.qb + q + lane)];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const long long pt = t + wp.span, pq = q + wp.span;
+        const int ravail = (int)min(c.tlen - pt, c.qlen - pq);
+        const int lavail = (int)min(t, q);
+        const Side r = warp_side(wp.T, c.Q, c.tb + pt, c.qb + pq, +1, ravail, wp.xdrop, lut, lane,
+                                 status);
+        const Side l = warp_side(wp.T, c.Q, c.tb + t - 1, c.qb + q - 1, -1, lavail, wp.xdrop,
+                                 lut, lane, status);
+        const long long score = (long long)s + r.best + l.best;
+        if (score > INT_MAX) status |= ST_SCORE_OVERFLOW;
+        ext++;
+        cells += (unsigned long long)(wp.span + r.scored + l.scored);
+        const bool pass = score >= wp.thresh;
+        if (pass && lane == 0) emit<BATCH>(wp, c, t, q, l.blen, r.blen, score, status);
+        if (pass || !(wp.flags & SFE_SKIP_PASSING_ONLY)) E = (int)(t + wp.span + r.blen);
+        i++;
+    }
+    if (wp.Ecarry && lane == 0) wp.Ecarry[D] = E;
+}
+
 template <bool BATCH>
 __global__ void __launch_bounds__(W_BLOCK) walk_warps_kernel(const uint64_t *__restrict__ hits,
                                                              uint32_t nhits, WalkParams wp) {
@@ -439,44 +564,7 @@ __global__ void __launch_bounds__(W_BLOCK) walk_warps_kernel(const uint64_t *__r
     for (long long e = warp; e < (long long)nq; e += nwarps) {
         const uint4 it = wp.queue[e];
         tasks++;
-        uint32_t i = it.x;
-        int E = (int)it.y;
-        const uint32_t dword = diag_of(hits[i]);
-        SegCtx c;
-        seg_ctx<BATCH>(wp, dword, c);
-        const long long D = c.D;
-        while (i < nhits) {
-            const uint64_t h = hits[i];
-            if (diag_of(h) != dword) break;
-            const long long t = (long long)(uint32_t)h;
-            if (t < E) {
-                i++;
-                continue;
-            }
-            const long long q = t - D + c.qoff;
-            // seed span: lanes 0..span-1
-            int s = 0;
-            if (lane < wp.span)
-                s = lut[base_at(wp.T, c.tb + t + lane) * 4u + base_at(c.Q, c.qb + q + lane)];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            const long long pt = t + wp.span, pq = q + wp.span;
-            const int ravail = (int)min(c.tlen - pt, c.qlen - pq);
-            const int lavail = (int)min(t, q);
-            const Side r = warp_side(wp.T, c.Q, c.tb + pt, c.qb + pq, +1, ravail, wp.xdrop, lut,
-                                     lane, status);
-            const Side l = warp_side(wp.T, c.Q, c.tb + t - 1, c.qb + q - 1, -1, lavail, wp.xdrop,
-                                     lut, lane, status);
-            const long long score = (long long)s + r.best + l.best;
-            if (score > INT_MAX) status |= ST_SCORE_OVERFLOW;
-            ext++;
-            cells += (unsigned long long)(wp.span + r.scored + l.scored);
-            const bool pass = score >= wp.thresh;
-            if (pass && lane == 0) emit<BATCH>(wp, c, t, q, l.blen, r.blen, score, status);
-            if (pass || !(wp.flags & SFE_SKIP_PASSING_ONLY)) E = (int)(t + wp.span + r.blen);
-            i++;
-        }
-        if (wp.Ecarry && lane == 0) wp.Ecarry[D] = E;
+        warp_walk_diagonal<BATCH>(hits, nhits, it.x, (int)it.y, wp, lut, lane, ext, cells, status);
     }
     if (lane == 0) {
         if (ext) atomicAdd(&wp.ctr->extended, ext);
@@ -520,13 +608,13 @@ cudaError_t launch_walk_lanes(const uint64_t *hits, long long n, WalkParams wp, 
     const unsigned grid = grid_for(nthreads, W_BLOCK);
     const bool packed = wp.xdrop < PACKED_X_LIMIT, batch = wp.pairs != nullptr;
     if (packed && !batch)
-        walk_lanes_kernel<true, false><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, (uint32_t)chunk, wp);
+        walk_lanes_kernel<true, false, false><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, (uint32_t)chunk, wp);
     else if (!packed && !batch)
-        walk_lanes_kernel<false, false><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, (uint32_t)chunk, wp);
+        walk_lanes_kernel<false, false, false><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, (uint32_t)chunk, wp);
     else if (packed)
-        walk_lanes_kernel<true, true><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, (uint32_t)chunk, wp);
+        walk_lanes_kernel<true, true, false><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, (uint32_t)chunk, wp);
     else
-        walk_lanes_kernel<false, true><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, (uint32_t)chunk, wp);
+        walk_lanes_kernel<false, true, false><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, (uint32_t)chunk, wp);
     return cudaGetLastError();
 }
 
@@ -540,6 +628,85 @@ cudaError_t launch_walk_warps(const uint64_t *hits, long long n, WalkParams wp, 
         walk_warps_kernel<true><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, wp);
     else
         walk_warps_kernel<false><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, wp);
+    return cudaGetLastError();
+}
+
+// Sort key of each work chunk for the largest-first schedule: the number of
+// hits of the diagonal its first hit lies on (descending), then chunk index.
+__global__ void chunk_keys_kernel(const uint64_t *__restrict__ hits, uint32_t n, uint32_t chunk,
+                                  uint32_t nchunks, uint64_t *__restrict__ keys) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nchunks) return;
+    const uint32_t i = k * chunk;
+    const uint32_t d = diag_of(hits[i]);
+    uint32_t lo = 0, hi = i;  // first index of this diagonal
+    while (lo < hi) {
+        const uint32_t mid = lo + (hi - lo) / 2;
+        if (diag_of(hits[mid]) < d)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    const uint32_t len = segment_end(hits, i, n, d) - lo;
+    keys[k] = ((uint64_t)(0xFFFFFFFFu - len) << 32) | k;
+}
+
+__global__ void chunk_order_kernel(const uint64_t *__restrict__ keys, uint32_t nchunks,
+                                   uint32_t *__restrict__ order) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nchunks) order[k] = (uint32_t)keys[k];
+}
+
+template <bool PACKED, bool BATCH>
+cudaError_t launch_persistent_t(const uint64_t *hits, long long n, const WalkParams &wp,
+                                cudaStream_t st) {
+    // every CTA resident at once: consumers wait on producers of other CTAs
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, walk_lanes_kernel<PACKED, BATCH, true>, W_BLOCK, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    g_launches++;
+    walk_lanes_kernel<PACKED, BATCH, true><<<per_sm * sms(), W_BLOCK, 0, st>>>(hits, (uint32_t)n,
+                                                                              wp.chunk, wp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_walk_persistent(const uint64_t *hits, long long n, WalkParams wp,
+                                   cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (wp.chunk == 0) wp.chunk = 32;
+    wp.nchunks = (uint32_t)((n + wp.chunk - 1) / wp.chunk);
+    const bool packed = wp.xdrop < PACKED_X_LIMIT, batch = wp.pairs != nullptr;
+    if (packed && !batch) return launch_persistent_t<true, false>(hits, n, wp, st);
+    if (!packed && !batch) return launch_persistent_t<false, false>(hits, n, wp, st);
+    if (packed) return launch_persistent_t<true, true>(hits, n, wp, st);
+    return launch_persistent_t<false, true>(hits, n, wp, st);
+}
+
+size_t walk_schedule_temp_bytes(long long n, uint32_t chunk) {
+    const long long nchunks = (n + chunk - 1) / chunk;
+    return (size_t)nchunks * 20 + radix_sort_temp_bytes(nchunks) + 1024;
+}
+
+cudaError_t launch_walk_schedule(const uint64_t *hits, long long n, uint32_t chunk, int schedule,
+                                 void *tmp, uint32_t **order, uint32_t *status, cudaStream_t st) {
+    *order = nullptr;
+    if (schedule != SFE_SCHED_LARGEST_FIRST || n <= 0) return cudaSuccess;
+    const uint32_t nchunks = (uint32_t)((n + chunk - 1) / chunk);
+    char *p = reinterpret_cast<char *>(tmp);
+    uint64_t *ka = reinterpret_cast<uint64_t *>(p);
+    uint64_t *kb = ka + ((nchunks + 31) & ~31u);
+    uint32_t *ord = reinterpret_cast<uint32_t *>(kb + ((nchunks + 31) & ~31u));
+    void *rt = ord + ((nchunks + 63) & ~63u);
+    g_launches++;
+    chunk_keys_kernel<<<grid_for(nchunks), BLOCK, 0, st>>>(hits, (uint32_t)n, chunk, nchunks, ka);
+    bool in_b = false;
+    cudaError_t e = radix_sort(ka, kb, nullptr, nullptr, nchunks, 32, 64, rt, &in_b, status, st);
+    if (e != cudaSuccess) return e;
+    g_launches++;
+    chunk_order_kernel<<<grid_for(nchunks), BLOCK, 0, st>>>(in_b ? kb : ka, nchunks, ord);
+    *order = ord;
     return cudaGetLastError();
 }
 

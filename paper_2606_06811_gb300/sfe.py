@@ -19,7 +19,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsfe.so")
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW = 0, -1, -2, -3, -4, -5
 SKIP_PASSING_ONLY = 1
 TIME_STAGES = 2
-STAGES = ("pack", "index", "count", "write", "sort", "segments", "walk_lanes", "walk_warps",
+WALK_PERSISTENT, WALK_TWO_LAUNCHES = 0, 1
+SCHED_NATURAL, SCHED_LARGEST_FIRST = 0, 1
+STAGES = ("pack", "index", "count", "write", "sort", "schedule", "walk_lanes", "walk_warps",
           "output")
 
 HIT_DTYPE = np.dtype([("strand", "<i4"), ("tpos", "<i4"), ("qpos", "<i4")])
@@ -39,7 +41,9 @@ class Params(C.Structure):
     _fields_ = [("seed_pattern", C.c_char_p), ("transition", C.c_int32),
                 ("strands", C.c_int32), ("scores", C.c_int32 * 16), ("xdrop", C.c_int32),
                 ("hsp_thresh", C.c_int32), ("flags", C.c_int32), ("input_codes", C.c_int32),
-                ("lane_cap", C.c_int32), ("lanes_per_sm", C.c_int32), ("tile_hits", C.c_int64)]
+                ("lane_cap", C.c_int32), ("lanes_per_sm", C.c_int32), ("tile_hits", C.c_int64),
+                ("walk_chunk", C.c_int32), ("walk_mode", C.c_int32), ("walk_schedule", C.c_int32),
+                ("reserved2", C.c_int32)]
 
 
 class Stats(C.Structure):

@@ -44,7 +44,8 @@ def gpu_batch(P, pairs, **kw):
 
 def check(P, pairs, **kw):
     okw = {("thresh" if k == "hsp_thresh" else k): v for k, v in kw.items()
-           if k not in ("lane_cap", "lanes_per_sm", "tile_hits")}
+           if k not in ("lane_cap", "lanes_per_sm", "tile_hits", "walk_mode", "walk_chunk",
+                        "walk_schedule")}
     H, hits, ext, cells = oracle_batch(pairs, **okw)
     G, st = gpu_batch(P, pairs, **kw)
     assert G.shape == H.shape and np.array_equal(G, H)
@@ -73,3 +74,9 @@ def test_batch_single_strand_and_lane_cap(pkg):
     pairs = synth.batch_pairs(seed=4, n_pairs=40, len_lo=2000, len_hi=30_000)
     check(pkg, pairs, strands=2, lane_cap=16)
     check(pkg, pairs, strands=1)
+
+
+@pytest.mark.parametrize("mode,sched,chunk", [(1, 0, 0), (0, 1, 16), (0, 0, 3)])
+def test_batch_walk_modes(pkg, mode, sched, chunk):
+    pairs = synth.batch_pairs(seed=6, n_pairs=64, len_lo=1000, len_hi=30_000)
+    check(pkg, pairs, walk_mode=mode, walk_schedule=sched, walk_chunk=chunk, lane_cap=32)
