@@ -94,6 +94,12 @@ typedef struct {
     int32_t pair, strand, tpos, qpos, len, score;
 } sfe_batch_hsp;
 
+/* One logged extension (see sfe_params.ext_log): the seed hit and the bases
+ * its X-drop scored on each side. Its work in cells is span + right + left. */
+typedef struct {
+    int32_t pair, strand, t, q, right, left;
+} sfe_ext_record;
+
 typedef struct {
     const char *seed_pattern; /* '1' care, '0' don't care; span <= 32, weight <= 14; NULL = 12of19 */
     int32_t transition;       /* 1: at most one care position may be a transition (A<->G, C<->T) */
@@ -109,13 +115,19 @@ typedef struct {
     int32_t walk_chunk;       /* hits a lane takes per grab from the work counter; 0 = default (32) */
     int32_t walk_mode;        /* SFE_WALK_PERSISTENT (default) or SFE_WALK_TWO_LAUNCHES */
     int32_t walk_schedule;    /* order in which the persistent walk hands out chunks (SFE_SCHED_*) */
-    int32_t reserved2;
+    int32_t ext_log_every;    /* log about 1 in ext_log_every extensions (0: no log) */
+    sfe_ext_record *ext_log;  /* device buffer for the log; the choice of logged hits is a hash of
+                                 (pair, strand, t, q), so it does not depend on the schedule */
+    int64_t ext_log_cap;      /* records the buffer holds (further ones are counted, not written) */
+    const void *model;        /* device weights of the work predictor (SFE_SCHED_PREDICTED) */
 } sfe_params;
 
 /* sfe_params.walk_schedule: the order of work never changes the output, only
  * how evenly it spreads over the warps */
 #define SFE_SCHED_NATURAL 0       /* chunks in hit order */
 #define SFE_SCHED_LARGEST_FIRST 1 /* chunks starting in larger diagonals (more hits) first */
+#define SFE_SCHED_PREDICTED 2     /* chunks with more predicted work first (model in params) */
+#define SFE_SCHED_RANDOM 3        /* chunks in a fixed pseudo-random order (a control) */
 
 /* sfe_params.walk_mode */
 #define SFE_WALK_PERSISTENT 0   /* one launch: lanes pull chunks from a device counter, then
@@ -134,6 +146,7 @@ typedef struct {
     int64_t warp_cells; /* cells scored by the warp tier (the rest by lanes) */
     int64_t tiles;      /* query tiles processed */
     int64_t launches;   /* kernels this call launched */
+    int64_t ext_logged; /* extensions selected for the log (may exceed ext_log_cap) */
     double stage_ms[SFE_NSTAGES];        /* device time per stage (with SFE_TIME_STAGES) */
     int64_t stage_launches[SFE_NSTAGES]; /* kernels launched per stage (with SFE_TIME_STAGES) */
 } sfe_stats;
@@ -213,6 +226,83 @@ int sfe_run_batch(sfe_ctx *ctx, const uint8_t *targets, const int64_t *toff,
                   const uint8_t *queries, const int64_t *qoff, int32_t npairs,
                   const sfe_params *params, sfe_batch_hsp *hsps, int64_t cap, int64_t *nhsps,
                   sfe_stats *stats);
+
+/*
+ * Work predictor of the learned schedule (SFE_SCHED_PREDICTED).
+ *
+ * The paper names the load imbalance of X-drop extensions (Section 8: some
+ * extensions run far longer than the median, and a warp waits for its
+ * slowest lane) but learns nothing; this predictor is an addition that only
+ * reorders independent work, so the HSP output never depends on it.
+ *
+ * Network: for a seed hit at (t, q) with seed span s, the 32 diagonal columns
+ * left of the seed (T[t - 32 + i] against Q[q - 32 + i]) and the 32 right of
+ * it (T[t + s + i] against Q[q + s + i]), i = 0..31, each one-hot over its
+ * substitution class T xor Q of the 2-bit codes (0 match, 2 transition, 1 and
+ * 3 transversions): input (column * 4 + class), columns 0..31 left and 32..63
+ * right; a column outside either sequence is all zero. 256 inputs, two ReLU
+ * layers of 64 and one linear output, the prediction of log(1 + right + left)
+ * of the hit's extension (sfe_ext_record). Parameters:
+ * sfe_mlp_param_count() FP32 values, in the order W1[256][64], b1[64],
+ * W2[64][64], b2[64], W3[64], b3 (row = input unit). Training runs on the
+ * device in FP32 with the library's own forward and backward kernels and
+ * Adam; inference reads a model blob of sfe_mlp_model_bytes() bytes made by
+ * sfe_mlp_pack (FP16 weights, FP32 biases, FP32 accumulation).
+ */
+typedef struct sfe_mlp_data sfe_mlp_data;
+
+int32_t sfe_mlp_param_count(void);
+int64_t sfe_mlp_model_bytes(void);
+
+/* Random initial parameters (uniform, scaled by fan-in; b3 = 3) from `seed`
+ * into the device buffer params. */
+int sfe_mlp_init(sfe_ctx *ctx, float *params, uint64_t seed);
+
+/* FP16 inference blob of the FP32 parameters; both device buffers. */
+int sfe_mlp_pack(sfe_ctx *ctx, const float *params, void *model);
+
+/*
+ * Training samples: the extension records `recs` (n of them, host or device,
+ * as logged by sfe_run with pair = 0 or by sfe_run_batch) and the sequences
+ * they refer to, given as in sfe_run_batch (npairs = 1 with toff = {0, tlen},
+ * qoff = {0, qlen} for sfe_run's records); span is the seed span of the run
+ * that logged them (19 for the default pattern). The sequences are packed and
+ * the records copied once; the handle owns its device memory. SFE_EINVAL when
+ * a record's pair or strand is out of range (positions need no check: columns
+ * outside a sequence are zero inputs).
+ */
+int sfe_mlp_data_create(sfe_ctx *ctx, const uint8_t *targets, const int64_t *toff,
+                        const uint8_t *queries, const int64_t *qoff, int32_t npairs,
+                        int32_t input_codes, int32_t span, const sfe_ext_record *recs, int64_t n,
+                        sfe_mlp_data **out);
+void sfe_mlp_data_free(sfe_mlp_data *data);
+
+/*
+ * Loss and gradient of the FP32 network over all samples: *loss (host)
+ * receives the mean squared error of the prediction against
+ * log(1 + right + left); grad (device, param_count floats, may be NULL)
+ * receives the gradient of that mean; preds (device, n floats, may be NULL)
+ * the predictions in record order.
+ */
+int sfe_mlp_loss_grad(sfe_ctx *ctx, const sfe_mlp_data *data, const float *params, float *grad,
+                      float *preds, double *loss);
+
+/*
+ * Predictions of the FP16 inference model (sfe_mlp_pack) for every sample,
+ * into preds (device, n floats) in record order.
+ */
+int sfe_mlp_predict(sfe_ctx *ctx, const sfe_mlp_data *data, const void *model, float *preds);
+
+/*
+ * Adam on minibatches: `epochs` passes, each over a fresh permutation of the
+ * samples drawn from (seed, epoch), in minibatches of `batch` samples (the
+ * last one smaller), learning rate lr, beta1 0.9, beta2 0.999, eps 1e-8.
+ * params (device) is updated in place; the optimiser state starts at zero.
+ * epoch_loss (host, `epochs` entries, may be NULL) receives each epoch's mean
+ * squared error over its samples, each taken before its minibatch's update.
+ */
+int sfe_mlp_train(sfe_ctx *ctx, const sfe_mlp_data *data, float *params, int32_t epochs,
+                  int32_t batch, float lr, uint64_t seed, double *epoch_loss);
 
 /*
  * Allocation-free variant of sfe_ungapped_xdrop (the paper has no counterpart:

@@ -212,8 +212,13 @@ int check_params(const sfe_params *p) {
     if (p->walk_chunk < 0) return fail(SFE_EINVAL, "walk_chunk must be >= 0");
     if (p->walk_mode != SFE_WALK_PERSISTENT && p->walk_mode != SFE_WALK_TWO_LAUNCHES)
         return fail(SFE_EINVAL, "walk_mode must be SFE_WALK_PERSISTENT or SFE_WALK_TWO_LAUNCHES");
-    if (p->walk_schedule != SFE_SCHED_NATURAL && p->walk_schedule != SFE_SCHED_LARGEST_FIRST)
+    if (p->walk_schedule < SFE_SCHED_NATURAL || p->walk_schedule > SFE_SCHED_RANDOM)
         return fail(SFE_EINVAL, "unknown walk_schedule");
+    if (p->walk_schedule == SFE_SCHED_PREDICTED && (!p->model || !is_device_ptr(p->model)))
+        return fail(SFE_EINVAL, "SFE_SCHED_PREDICTED needs params.model in device memory");
+    if (p->ext_log_every < 0 || p->ext_log_cap < 0) return fail(SFE_EINVAL, "bad ext_log settings");
+    if (p->ext_log && p->ext_log_every > 0 && !is_device_ptr(p->ext_log))
+        return fail(SFE_EINVAL, "ext_log must be device memory");
     if (p->tile_hits < 0) return fail(SFE_EINVAL, "tile_hits must be >= 0");
     if (p->input_codes != 0 && p->input_codes != 1) return fail(SFE_EINVAL, "input_codes must be 0 or 1");
     for (int i = 0; i < 16; i++)
@@ -407,6 +412,11 @@ struct WalkSetup {
 // persistent launch or as two launches (params->walk_mode).
 int walk_tiers(sfe_ctx *c, const uint64_t *hits, long long n, WalkParams &wp, uint4 *queue,
                unsigned long long qcap, const sfe_params *p) {
+    if (p->ext_log && p->ext_log_every > 0) {
+        wp.elog = p->ext_log;
+        wp.elog_cap = (unsigned long long)std::max<int64_t>(0, p->ext_log_cap);
+        wp.elog_every = (uint32_t)p->ext_log_every;
+    }
     wp.queue = queue;
     wp.queue_cap = qcap;
     wp.queue_len = &c->small->queue_len;
@@ -432,7 +442,7 @@ int walk_tiers(sfe_ctx *c, const uint64_t *hits, long long n, WalkParams &wp, ui
         void *tmp = nullptr;
         TRY(ensure(c, SL_SCHED, walk_schedule_temp_bytes(n, wp.chunk), &tmp));
         uint32_t *order = nullptr;
-        CK(launch_walk_schedule(hits, n, wp.chunk, p->walk_schedule, tmp, &order,
+        CK(launch_walk_schedule(hits, n, wp, p->walk_schedule, p->model, tmp, &order,
                                 &c->small->status, c->st));
         wp.order = order;
     }
@@ -495,6 +505,7 @@ void fill_stats(const Small &s, sfe_stats *st, long long hits, long long tiles) 
     st->lane_tasks = (int64_t)s.ctr.lane_tasks;
     st->warp_tasks = (int64_t)s.ctr.warp_tasks;
     st->warp_cells = (int64_t)s.ctr.warp_cells;
+    st->ext_logged = (int64_t)s.ctr.ext_logged;
     st->tiles = tiles;
 }
 
@@ -1086,6 +1097,264 @@ int sfe_run_batch(sfe_ctx *c, const uint8_t *targets, const int64_t *toff, const
     CK(cudaStreamSynchronize(c->st));
     add_timings(c, stats);
     return r;
+}
+
+// ---------------------------------------------------------------------------
+// Work predictor: training data, loss/gradient, Adam, FP16 inference.
+
+int32_t sfe_mlp_param_count(void) { return mlp_param_count(); }
+int64_t sfe_mlp_model_bytes(void) { return (int64_t)mlp_model_bytes(); }
+
+int sfe_mlp_init(sfe_ctx *c, float *params, uint64_t seed) {
+    TRY(begin(c));
+    if (!is_device_ptr(params)) return fail(SFE_EINVAL, "params must be device memory");
+    CK(launch_mlp_init(params, (unsigned long long)seed, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return SFE_OK;
+}
+
+int sfe_mlp_pack(sfe_ctx *c, const float *params, void *model) {
+    TRY(begin(c));
+    if (!is_device_ptr(params) || !is_device_ptr(model))
+        return fail(SFE_EINVAL, "params and model must be device memory");
+    CK(launch_mlp_pack(params, model, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return SFE_OK;
+}
+
+}  // extern "C"
+
+struct sfe_mlp_data {
+    int device = 0;
+    long long n = 0;
+    int npairs = 0;
+    int span = 19;  // seed span of the run that logged the records
+    long long ttot = 0, qtot = 0;
+    uint32_t *tp = nullptr, *qp = nullptr, *qm = nullptr;  // packed, with padding
+    PairInfo *pairs = nullptr;
+    sfe_ext_record *recs = nullptr;
+    // training scratch
+    uint64_t *ka = nullptr, *kb = nullptr;
+    uint32_t *perm = nullptr;
+    void *tmp = nullptr;
+    float *grad = nullptr, *m = nullptr, *v = nullptr;
+    double *loss = nullptr;  // one per epoch (grown on demand)
+    int loss_cap = 0;
+    uint32_t *status = nullptr;
+    std::vector<void *> owned;
+};
+
+namespace {
+
+int data_alloc(sfe_mlp_data *d, size_t bytes, void **out) {
+    void *p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(bytes, 256)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SFE_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    d->owned.push_back(p);
+    *out = p;
+    return SFE_OK;
+}
+
+template <typename T>
+int data_alloc_t(sfe_mlp_data *d, size_t count, T **out) {
+    void *p = nullptr;
+    TRY(data_alloc(d, count * sizeof(T), &p));
+    *out = reinterpret_cast<T *>(p);
+    return SFE_OK;
+}
+
+void data_release(sfe_mlp_data *d) {
+    if (!d) return;
+    cudaSetDevice(d->device);
+    for (void *p : d->owned) cudaFree(p);
+    delete d;
+}
+
+// Pack (host or device) bases into a new padded buffer owned by d.
+int data_pack(sfe_ctx *c, sfe_mlp_data *d, const uint8_t *src, long long n, int codes,
+              uint32_t **base0) {
+    uint32_t *a = nullptr;
+    TRY(data_alloc_t(d, packed_words(n), &a));
+    CK(cudaMemsetAsync(a, 0, packed_words(n) * 4, c->st));
+    *base0 = a + SEQ_PAD;
+    if (n == 0) return SFE_OK;
+    const uint8_t *dev = src;
+    if (!is_device_ptr(src)) {
+        uint8_t *stg = nullptr;
+        TRY(data_alloc_t(d, (size_t)n, &stg));
+        CK(cudaMemcpyAsync(stg, src, (size_t)n, cudaMemcpyHostToDevice, c->st));
+        dev = stg;
+    }
+    CK(launch_pack(dev, n, codes, *base0, d->status, c->st));
+    return SFE_OK;
+}
+
+int data_status(sfe_ctx *c, sfe_mlp_data *d) {
+    uint32_t st = 0;
+    CK(cudaMemcpyAsync(&st, d->status, 4, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (st & ST_BAD_HIT) return fail(SFE_EINVAL, "a record's pair or strand is out of range");
+    return check_status(st);
+}
+
+int data_check(sfe_ctx *c, const sfe_mlp_data *d) {
+    if (!d) return fail(SFE_EINVAL, "data is NULL");
+    if (d->device != c->device) return fail(SFE_EINVAL, "data belongs to another device");
+    return SFE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sfe_mlp_data_create(sfe_ctx *c, const uint8_t *targets, const int64_t *toff,
+                        const uint8_t *queries, const int64_t *qoff, int32_t npairs,
+                        int32_t input_codes, int32_t span, const sfe_ext_record *recs, int64_t n,
+                        sfe_mlp_data **out) {
+    if (!out || !toff || !qoff) return fail(SFE_EINVAL, "out, toff or qoff is NULL");
+    *out = nullptr;
+    if (npairs < 1 || npairs > (1 << 16)) return fail(SFE_EINVAL, "npairs must be 1..65536");
+    if (n < 0 || n >= (1LL << 32)) return fail(SFE_EINVAL, "record count must be in [0, 2^32)");
+    if (n > 0 && !recs) return fail(SFE_EINVAL, "recs is NULL");
+    if (input_codes != 0 && input_codes != 1) return fail(SFE_EINVAL, "input_codes must be 0 or 1");
+    if (span < 1 || span > MAX_SPAN) return fail(SFE_EINVAL, "span must be in [1, 32]");
+    if (toff[0] != 0 || qoff[0] != 0) return fail(SFE_EINVAL, "offsets must start at 0");
+    for (int p = 0; p < npairs; p++)
+        if (toff[p + 1] < toff[p] || qoff[p + 1] < qoff[p])
+            return fail(SFE_EINVAL, "offsets must not decrease");
+    TRY(check_len(toff[npairs], "concatenated target"));
+    TRY(check_len(qoff[npairs], "concatenated query"));
+    TRY(begin(c));
+    sfe_mlp_data *d = new sfe_mlp_data;
+    d->device = c->device;
+    d->n = n;
+    d->npairs = npairs;
+    d->span = span;
+    d->ttot = toff[npairs];
+    d->qtot = qoff[npairs];
+    auto bail = [&](int r) {
+        cudaStreamSynchronize(c->st);
+        data_release(d);
+        return r;
+    };
+    int r = SFE_OK;
+    if ((r = data_alloc_t(d, 1, &d->status)) != SFE_OK) return bail(r);
+    if (cudaMemsetAsync(d->status, 0, 4, c->st) != cudaSuccess) return bail(fail(SFE_ECUDA, "memset"));
+    std::vector<PairInfo> P(npairs);
+    for (int p = 0; p < npairs; p++) {
+        P[p] = PairInfo{};
+        P[p].toff = toff[p];
+        P[p].qoff = qoff[p];
+        P[p].qoff_rc = d->qtot - qoff[p + 1];
+        P[p].tlen = (int)(toff[p + 1] - toff[p]);
+        P[p].qlen = (int)(qoff[p + 1] - qoff[p]);
+    }
+    if ((r = data_alloc_t(d, (size_t)npairs, &d->pairs)) != SFE_OK) return bail(r);
+    if (cudaMemcpyAsync(d->pairs, P.data(), (size_t)npairs * sizeof(PairInfo),
+                        cudaMemcpyHostToDevice, c->st) != cudaSuccess)
+        return bail(fail(SFE_ECUDA, "copy of the pair table failed"));
+    if ((r = data_pack(c, d, targets, d->ttot, input_codes, &d->tp)) != SFE_OK) return bail(r);
+    if ((r = data_pack(c, d, queries, d->qtot, input_codes, &d->qp)) != SFE_OK) return bail(r);
+    uint32_t *qm_alloc = nullptr;
+    if ((r = data_alloc_t(d, packed_words(d->qtot), &qm_alloc)) != SFE_OK) return bail(r);
+    d->qm = qm_alloc + SEQ_PAD;
+    if (launch_revcomp(d->qp, d->qtot, d->qm, c->st) != cudaSuccess)
+        return bail(fail(SFE_ECUDA, "reverse complement failed"));
+    if ((r = data_alloc_t(d, (size_t)std::max<int64_t>(n, 1), &d->recs)) != SFE_OK) return bail(r);
+    if (n > 0 &&
+        cudaMemcpyAsync(d->recs, recs, (size_t)n * sizeof(sfe_ext_record),
+                        is_device_ptr(recs) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        c->st) != cudaSuccess)
+        return bail(fail(SFE_ECUDA, "copy of the records failed"));
+    if (launch_validate_records(d->recs, n, npairs, d->status, c->st) != cudaSuccess)
+        return bail(fail(SFE_ECUDA, "record check failed"));
+    if ((r = data_status(c, d)) != SFE_OK) return bail(r);
+    *out = d;
+    return SFE_OK;
+}
+
+void sfe_mlp_data_free(sfe_mlp_data *d) { data_release(d); }
+
+int sfe_mlp_loss_grad(sfe_ctx *c, const sfe_mlp_data *d, const float *params, float *grad,
+                      float *preds, double *loss) {
+    TRY(begin(c));
+    TRY(data_check(c, d));
+    if (!loss) return fail(SFE_EINVAL, "loss is NULL");
+    if (!is_device_ptr(params) || (grad && !is_device_ptr(grad)) ||
+        (preds && !is_device_ptr(preds)))
+        return fail(SFE_EINVAL, "params, grad and preds must be device memory");
+    double *dl = nullptr;
+    TRY(ensure_t(c, SL_TMP, 1, &dl));
+    CK(cudaMemsetAsync(dl, 0, 8, c->st));
+    if (grad) CK(cudaMemsetAsync(grad, 0, (size_t)mlp_param_count() * 4, c->st));
+    CK(launch_mlp_fwd_bwd(d->tp, d->ttot, d->qp, d->qm, d->qtot, d->pairs, d->span, d->recs, nullptr,
+                          d->n, params, grad, preds, dl, c->st));
+    double h = 0.0;
+    CK(cudaMemcpyAsync(&h, dl, 8, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    *loss = d->n > 0 ? h / (double)d->n : 0.0;
+    return SFE_OK;
+}
+
+int sfe_mlp_predict(sfe_ctx *c, const sfe_mlp_data *d, const void *model, float *preds) {
+    TRY(begin(c));
+    TRY(data_check(c, d));
+    if (!is_device_ptr(model) || (d->n > 0 && !is_device_ptr(preds)))
+        return fail(SFE_EINVAL, "model and preds must be device memory");
+    CK(launch_mlp_predict16(d->tp, d->ttot, d->qp, d->qm, d->qtot, d->pairs, d->span, d->recs,
+                            d->n, model, preds, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return SFE_OK;
+}
+
+int sfe_mlp_train(sfe_ctx *c, const sfe_mlp_data *dc, float *params, int32_t epochs,
+                  int32_t batch, float lr, uint64_t seed, double *epoch_loss) {
+    TRY(begin(c));
+    TRY(data_check(c, dc));
+    sfe_mlp_data *d = const_cast<sfe_mlp_data *>(dc);  // training scratch lives in the handle
+    if (!is_device_ptr(params)) return fail(SFE_EINVAL, "params must be device memory");
+    if (epochs < 0 || batch < 1 || !(lr > 0.f)) return fail(SFE_EINVAL, "bad epochs, batch or lr");
+    const long long n = d->n;
+    if (n == 0 || epochs == 0) return SFE_OK;
+    const int np = mlp_param_count();
+    if (!d->grad) {
+        TRY(data_alloc_t(d, (size_t)np, &d->grad));
+        TRY(data_alloc_t(d, (size_t)np, &d->m));
+        TRY(data_alloc_t(d, (size_t)np, &d->v));
+        TRY(data_alloc_t(d, (size_t)n, &d->ka));
+        TRY(data_alloc_t(d, (size_t)n, &d->kb));
+        TRY(data_alloc_t(d, (size_t)n, &d->perm));
+        TRY(data_alloc(d, radix_sort_temp_bytes(n), &d->tmp));
+    }
+    if (d->loss_cap < epochs) {
+        TRY(data_alloc_t(d, (size_t)epochs, &d->loss));
+        d->loss_cap = epochs;
+    }
+    CK(cudaMemsetAsync(d->m, 0, (size_t)np * 4, c->st));
+    CK(cudaMemsetAsync(d->v, 0, (size_t)np * 4, c->st));
+    CK(cudaMemsetAsync(d->loss, 0, (size_t)epochs * 8, c->st));
+    CK(cudaMemsetAsync(d->status, 0, 4, c->st));
+    int step = 0;
+    for (int e = 0; e < epochs; e++) {
+        CK(launch_perm(n, (unsigned long long)seed, e, d->ka, d->kb, d->tmp, d->perm, d->status,
+                       c->st));
+        for (long long b0 = 0; b0 < n; b0 += batch) {
+            const long long nb = std::min<long long>(batch, n - b0);
+            CK(cudaMemsetAsync(d->grad, 0, (size_t)np * 4, c->st));
+            CK(launch_mlp_fwd_bwd(d->tp, d->ttot, d->qp, d->qm, d->qtot, d->pairs, d->span,
+                                  d->recs, d->perm + b0, nb, params, d->grad, nullptr,
+                                  d->loss + e, c->st));
+            CK(launch_adam(params, d->grad, d->m, d->v, lr, ++step, c->st));
+        }
+    }
+    std::vector<double> h((size_t)epochs);
+    CK(cudaMemcpyAsync(h.data(), d->loss, (size_t)epochs * 8, cudaMemcpyDeviceToHost, c->st));
+    TRY(data_status(c, d));
+    if (epoch_loss)
+        for (int e = 0; e < epochs; e++) epoch_loss[e] = h[(size_t)e] / (double)n;
+    return SFE_OK;
 }
 
 }  // extern "C"

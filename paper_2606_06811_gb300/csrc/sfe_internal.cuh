@@ -42,6 +42,7 @@ struct DevCounters {
     unsigned long long lane_tasks;
     unsigned long long warp_tasks; // queue entries
     unsigned long long warp_cells; // cells scored by the warp tier
+    unsigned long long ext_logged; // extensions selected for the extension log
     unsigned int status;
     unsigned int pad;
 };
@@ -171,7 +172,25 @@ struct WalkParams {
     unsigned int *queue_take;
     const uint32_t *order;
     uint32_t nchunks, chunk, epoch;
+    // sampled log of extensions (elog == nullptr: none)
+    sfe_ext_record *elog;
+    unsigned long long elog_cap;
+    uint32_t elog_every;
 };
+
+// Whether the extension of hit (pair, strand, t, q) goes to the log: a hash of
+// the hit, so the sample does not depend on the order of the walk.
+__device__ __forceinline__ bool ext_sampled(uint32_t every, int pair, int strand, long long t,
+                                            long long q) {
+    uint32_t h = (uint32_t)t * 0x9E3779B1u ^ (uint32_t)q * 0x85EBCA77u ^
+                 (uint32_t)pair * 0xC2B2AE3Du ^ (uint32_t)strand * 0x27D4EB2Fu;
+    h ^= h >> 16;
+    h *= 0x7FEB352Du;
+    h ^= h >> 15;
+    h *= 0x846CA68Bu;
+    h ^= h >> 16;
+    return h % every == 0;
+}
 // Walks of hits sorted by (diagonal word, t): lanes own contiguous hit ranges
 // (lanes_per_sm sizes the ranges; 0 = default); warps finish the diagonals
 // the lanes handed off.
@@ -181,9 +200,39 @@ cudaError_t launch_walk_warps(const uint64_t *hits, long long n, WalkParams wp, 
                               cudaStream_t st);
 // Chunk order of the persistent walk for a schedule (SFE_SCHED_*): *order is
 // left null for the natural order. tmp: walk_schedule_temp_bytes(n, chunk).
+// SFE_SCHED_PREDICTED ranks chunks with the work predictor `model`.
 size_t walk_schedule_temp_bytes(long long n, uint32_t chunk);
-cudaError_t launch_walk_schedule(const uint64_t *hits, long long n, uint32_t chunk, int schedule,
-                                 void *tmp, uint32_t **order, uint32_t *status, cudaStream_t st);
+cudaError_t launch_walk_schedule(const uint64_t *hits, long long n, const WalkParams &wp,
+                                 int schedule, const void *model, void *tmp, uint32_t **order,
+                                 uint32_t *status, cudaStream_t st);
+
+// Work predictor (MLP, see mlp.cu): parameter count, inference blob size,
+// initialisation, FP16 packing, loss/gradient/prediction over extension
+// records, Adam, and the per-chunk predicted work used by the schedule.
+int mlp_param_count();
+size_t mlp_model_bytes();
+cudaError_t launch_mlp_init(float *P, unsigned long long seed, cudaStream_t st);
+cudaError_t launch_mlp_pack(const float *P, void *model, cudaStream_t st);
+cudaError_t launch_mlp_fwd_bwd(const uint32_t *T, long long tlen, const uint32_t *Q,
+                               const uint32_t *Qrc, long long qlen, const PairInfo *pairs,
+                               int span, const sfe_ext_record *recs, const uint32_t *perm,
+                               long long n, const float *P, float *grad, float *preds,
+                               double *loss, cudaStream_t st);
+cudaError_t launch_adam(float *P, const float *g, float *m, float *v, float lr, int step,
+                        cudaStream_t st);
+cudaError_t launch_mlp_predict16(const uint32_t *T, long long tlen, const uint32_t *Q,
+                                 const uint32_t *Qrc, long long qlen, const PairInfo *pairs,
+                                 int span, const sfe_ext_record *recs, long long n,
+                                 const void *model, float *preds, cudaStream_t st);
+cudaError_t launch_validate_records(const sfe_ext_record *recs, long long n, int npairs,
+                                    uint32_t *status, cudaStream_t st);
+// A permutation of 0..n-1 from (seed, epoch): random keys sorted on the device.
+cudaError_t launch_perm(long long n, unsigned long long seed, int epoch, uint64_t *ka,
+                        uint64_t *kb, void *tmp, uint32_t *perm, uint32_t *status,
+                        cudaStream_t st);
+cudaError_t launch_chunk_predict(const uint64_t *hits, long long n, uint32_t chunk,
+                                 uint32_t nchunks, const WalkParams &wp, const void *model,
+                                 uint64_t *keys, cudaStream_t st);
 // Both tiers in one persistent launch fed by the work counter and the queue
 // (wp.work_next, warps_done, queue_take, queue_len zeroed by the caller).
 cudaError_t launch_walk_persistent(const uint64_t *hits, long long n, WalkParams wp,

@@ -74,6 +74,22 @@ __device__ __forceinline__ void seg_ctx(const WalkParams &wp, uint32_t word, Seg
     c.qoff = c.qlen - wp.span;
 }
 
+__device__ __forceinline__ void log_ext(const WalkParams &wp, const SegCtx &c, long long t,
+                                        long long q, int right, int left) {
+    if (!wp.elog || !ext_sampled(wp.elog_every, c.pair, c.strand, t, q)) return;
+    const unsigned long long idx = atomicAdd(&wp.ctr->ext_logged, 1ull);
+    if (idx < wp.elog_cap) {
+        sfe_ext_record r;
+        r.pair = c.pair;
+        r.strand = c.strand;
+        r.t = (int32_t)t;
+        r.q = (int32_t)q;
+        r.right = right;
+        r.left = left;
+        wp.elog[idx] = r;
+    }
+}
+
 template <bool BATCH>
 __device__ __forceinline__ void emit(const WalkParams &wp, const SegCtx &c, long long t,
                                      long long q, int lblen, int rblen, long long score,
@@ -353,6 +369,7 @@ __global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__r
             if (score > INT_MAX) status |= ST_SCORE_OVERFLOW;
             ext++;
             cells += (unsigned long long)(span + R.n + L.n);
+            log_ext(wp, c, t, q, R.n, L.n);
             const bool pass = score >= wp.thresh;
             if (pass) emit<BATCH>(wp, c, t, q, L.blen, R.blen, score, status);
             if (pass || !(wp.flags & SFE_SKIP_PASSING_ONLY)) E = (int)(t + span + R.blen);
@@ -541,6 +558,7 @@ __device__ void warp_walk_diagonal(const uint64_t *__restrict__ hits, uint32_t n
         if (score > INT_MAX) status |= ST_SCORE_OVERFLOW;
         ext++;
         cells += (unsigned long long)(wp.span + r.scored + l.scored);
+        if (lane == 0) log_ext(wp, c, t, q, r.scored, l.scored);
         const bool pass = score >= wp.thresh;
         if (pass && lane == 0) emit<BATCH>(wp, c, t, q, l.blen, r.blen, score, status);
         if (pass || !(wp.flags & SFE_SKIP_PASSING_ONLY)) E = (int)(t + wp.span + r.blen);
@@ -634,9 +652,17 @@ cudaError_t launch_walk_warps(const uint64_t *hits, long long n, WalkParams wp, 
 // Sort key of each work chunk for the largest-first schedule: the number of
 // hits of the diagonal its first hit lies on (descending), then chunk index.
 __global__ void chunk_keys_kernel(const uint64_t *__restrict__ hits, uint32_t n, uint32_t chunk,
-                                  uint32_t nchunks, uint64_t *__restrict__ keys) {
+                                  uint32_t nchunks, int random, uint64_t *__restrict__ keys) {
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nchunks) return;
+    if (random) {  // a fixed pseudo-random order (splitmix64 finaliser of k)
+        unsigned long long z = 0x9E3779B97F4A7C15ull * (unsigned long long)(k + 1);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        keys[k] = (z & 0xFFFFFFFF00000000ull) | k;
+        return;
+    }
     const uint32_t i = k * chunk;
     const uint32_t d = diag_of(hits[i]);
     uint32_t lo = 0, hi = i;  // first index of this diagonal
@@ -689,18 +715,26 @@ size_t walk_schedule_temp_bytes(long long n, uint32_t chunk) {
     return (size_t)nchunks * 20 + radix_sort_temp_bytes(nchunks) + 1024;
 }
 
-cudaError_t launch_walk_schedule(const uint64_t *hits, long long n, uint32_t chunk, int schedule,
-                                 void *tmp, uint32_t **order, uint32_t *status, cudaStream_t st) {
+cudaError_t launch_walk_schedule(const uint64_t *hits, long long n, const WalkParams &wp,
+                                 int schedule, const void *model, void *tmp, uint32_t **order,
+                                 uint32_t *status, cudaStream_t st) {
     *order = nullptr;
-    if (schedule != SFE_SCHED_LARGEST_FIRST || n <= 0) return cudaSuccess;
+    const uint32_t chunk = wp.chunk;
+    if (schedule == SFE_SCHED_NATURAL || n <= 0) return cudaSuccess;
     const uint32_t nchunks = (uint32_t)((n + chunk - 1) / chunk);
     char *p = reinterpret_cast<char *>(tmp);
     uint64_t *ka = reinterpret_cast<uint64_t *>(p);
     uint64_t *kb = ka + ((nchunks + 31) & ~31u);
     uint32_t *ord = reinterpret_cast<uint32_t *>(kb + ((nchunks + 31) & ~31u));
     void *rt = ord + ((nchunks + 63) & ~63u);
-    g_launches++;
-    chunk_keys_kernel<<<grid_for(nchunks), BLOCK, 0, st>>>(hits, (uint32_t)n, chunk, nchunks, ka);
+    if (schedule == SFE_SCHED_PREDICTED) {
+        cudaError_t e0 = launch_chunk_predict(hits, n, chunk, nchunks, wp, model, ka, st);
+        if (e0 != cudaSuccess) return e0;
+    } else {
+        g_launches++;
+        chunk_keys_kernel<<<grid_for(nchunks), BLOCK, 0, st>>>(
+            hits, (uint32_t)n, chunk, nchunks, schedule == SFE_SCHED_RANDOM ? 1 : 0, ka);
+    }
     bool in_b = false;
     cudaError_t e = radix_sort(ka, kb, nullptr, nullptr, nchunks, 32, 64, rt, &in_b, status, st);
     if (e != cudaSuccess) return e;

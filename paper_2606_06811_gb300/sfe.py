@@ -20,7 +20,9 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW = 0, -1, -2, -3, -4, -5
 SKIP_PASSING_ONLY = 1
 TIME_STAGES = 2
 WALK_PERSISTENT, WALK_TWO_LAUNCHES = 0, 1
-SCHED_NATURAL, SCHED_LARGEST_FIRST = 0, 1
+SCHED_NATURAL, SCHED_LARGEST_FIRST, SCHED_PREDICTED, SCHED_RANDOM = 0, 1, 2, 3
+EXT_DTYPE = np.dtype([("pair", "<i4"), ("strand", "<i4"), ("t", "<i4"), ("q", "<i4"),
+                      ("right", "<i4"), ("left", "<i4")])
 STAGES = ("pack", "index", "count", "write", "sort", "schedule", "walk_lanes", "walk_warps",
           "output")
 
@@ -43,18 +45,20 @@ class Params(C.Structure):
                 ("hsp_thresh", C.c_int32), ("flags", C.c_int32), ("input_codes", C.c_int32),
                 ("lane_cap", C.c_int32), ("lanes_per_sm", C.c_int32), ("tile_hits", C.c_int64),
                 ("walk_chunk", C.c_int32), ("walk_mode", C.c_int32), ("walk_schedule", C.c_int32),
-                ("reserved2", C.c_int32)]
+                ("ext_log_every", C.c_int32), ("ext_log", C.c_void_p), ("ext_log_cap", C.c_int64),
+                ("model", C.c_void_p)]
 
 
 class Stats(C.Structure):
     _fields_ = [("hits", C.c_int64), ("extended", C.c_int64), ("cells", C.c_int64),
                 ("hsps", C.c_int64), ("lane_tasks", C.c_int64), ("warp_tasks", C.c_int64),
                 ("warp_cells", C.c_int64), ("tiles", C.c_int64), ("launches", C.c_int64),
+                ("ext_logged", C.c_int64),
                 ("stage_ms", C.c_double * len(STAGES)),
                 ("stage_launches", C.c_int64 * len(STAGES))]
 
     def as_dict(self) -> dict:
-        d = {k: int(getattr(self, k)) for k, _ in self._fields_[:9]}
+        d = {k: int(getattr(self, k)) for k, _ in self._fields_[:10]}
         d["stage_ms"] = {n: float(self.stage_ms[i]) for i, n in enumerate(STAGES)}
         d["stage_launches"] = {n: int(self.stage_launches[i]) for i, n in enumerate(STAGES)}
         return d
@@ -91,8 +95,24 @@ def lib() -> C.CDLL:
                               C.POINTER(Stats)]
         L.sfe_run_batch.argtypes = [vp, vp, vp, vp, vp, i32, C.POINTER(Params), vp, i64,
                                     C.POINTER(i64), C.POINTER(Stats)]
+        L.sfe_mlp_param_count.argtypes = []
+        L.sfe_mlp_param_count.restype = i32
+        L.sfe_mlp_model_bytes.argtypes = []
+        L.sfe_mlp_model_bytes.restype = i64
+        L.sfe_mlp_init.argtypes = [vp, vp, C.c_uint64]
+        L.sfe_mlp_pack.argtypes = [vp, vp, vp]
+        L.sfe_mlp_data_create.argtypes = [vp, vp, vp, vp, vp, i32, i32, i32, vp, i64,
+                                          C.POINTER(vp)]
+        L.sfe_mlp_data_free.argtypes = [vp]
+        L.sfe_mlp_data_free.restype = None
+        L.sfe_mlp_loss_grad.argtypes = [vp, vp, vp, vp, vp, C.POINTER(C.c_double)]
+        L.sfe_mlp_predict.argtypes = [vp, vp, vp, vp]
+        L.sfe_mlp_train.argtypes = [vp, vp, vp, i32, i32, C.c_float, C.c_uint64,
+                                    C.POINTER(C.c_double)]
         for f in ("sfe_params_default", "sfe_ctx_create", "sfe_ctx_set_stream", "sfe_index_build",
-                  "sfe_seed_hits", "sfe_ungapped_xdrop", "sfe_run", "sfe_run_batch"):
+                  "sfe_seed_hits", "sfe_ungapped_xdrop", "sfe_run", "sfe_run_batch",
+                  "sfe_mlp_init", "sfe_mlp_pack", "sfe_mlp_data_create", "sfe_mlp_loss_grad",
+                  "sfe_mlp_predict", "sfe_mlp_train"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -269,6 +289,62 @@ class Context:
             _check(code)
             return buf[: nout.value], st.as_dict()
 
+    # ------------------------------------------------ work predictor (MLP)
+
+    def mlp_init(self, params, seed: int) -> None:
+        """Random initial FP32 parameters into the device tensor `params`."""
+        ptr, n, keep = _buf(params)
+        if n < 4 * mlp_param_count():
+            raise ValueError("params holds fewer than sfe_mlp_param_count() floats")
+        _check(lib().sfe_mlp_init(self.h, ptr, int(seed)))
+
+    def mlp_pack(self, params, model) -> None:
+        """FP16 inference blob (device tensor of sfe_mlp_model_bytes() bytes) of `params`."""
+        pptr, pn, pk = _buf(params)
+        mptr, mn, mk = _buf(model)
+        if pn < 4 * mlp_param_count() or mn < mlp_model_bytes():
+            raise ValueError("params or model buffer too small")
+        _check(lib().sfe_mlp_pack(self.h, pptr, mptr))
+
+    def mlp_data(self, targets, toff, queries, qoff, recs, input_codes: int = 0,
+                 span: int = 19) -> "MlpData":
+        """Training samples: extension records (EXT_DTYPE, host or device) and their pairs'
+        sequences back to back with int64 offsets, as for run_batch; span is the seed span
+        of the run that logged them."""
+        tptr, _, tkeep = _buf(targets)
+        qptr, _, qkeep = _buf(queries)
+        to = np.ascontiguousarray(toff, dtype=np.int64)
+        qo = np.ascontiguousarray(qoff, dtype=np.int64)
+        rptr, rn, rkeep = _buf(recs)
+        n = rn // EXT_DTYPE.itemsize
+        h = C.c_void_p()
+        _check(lib().sfe_mlp_data_create(self.h, tptr, to.ctypes.data, qptr, qo.ctypes.data,
+                                         int(to.size - 1), int(input_codes), int(span), rptr,
+                                         n, C.byref(h)))
+        return MlpData(h, n)
+
+    def mlp_loss_grad(self, data: "MlpData", params, grad=None, preds=None) -> float:
+        """Mean squared error of the FP32 network; fills the device tensors grad / preds."""
+        pptr, _, pk = _buf(params)
+        gptr = _buf(grad)[0] if grad is not None else None
+        optr = _buf(preds)[0] if preds is not None else None
+        loss = C.c_double(0.0)
+        _check(lib().sfe_mlp_loss_grad(self.h, data.h, pptr, gptr, optr, C.byref(loss)))
+        return float(loss.value)
+
+    def mlp_predict(self, data: "MlpData", model, preds) -> None:
+        """Predictions of the FP16 model into the device tensor preds (one per record)."""
+        _check(lib().sfe_mlp_predict(self.h, data.h, _buf(model)[0], _buf(preds)[0]))
+
+    def mlp_train(self, data: "MlpData", params, epochs: int, batch: int = 4096,
+                  lr: float = 1e-3, seed: int = 0) -> list[float]:
+        """Adam on minibatches, in place on `params`; returns each epoch's loss."""
+        pptr, _, pk = _buf(params)
+        out = (C.c_double * max(int(epochs), 1))()
+        _check(lib().sfe_mlp_train(self.h, data.h, pptr, int(epochs), int(batch), float(lr),
+                                   int(seed), out))
+        return [float(out[i]) for i in range(int(epochs))]
+
     def _retry(self, cap, call):
         cap = 1 << 16 if cap is None else int(cap)
         nout = C.c_int64(0)
@@ -300,6 +376,33 @@ class Index:
             self.close()
         except Exception:
             pass
+
+
+class MlpData:
+    """Training samples of the work predictor (owned device memory)."""
+
+    def __init__(self, h, n: int):
+        self.h = h
+        self.n = n
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            lib().sfe_mlp_data_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mlp_param_count() -> int:
+    return int(lib().sfe_mlp_param_count())
+
+
+def mlp_model_bytes() -> int:
+    return int(lib().sfe_mlp_model_bytes())
 
 
 def exported_symbols() -> list[str]:
