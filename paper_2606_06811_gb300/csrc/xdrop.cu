@@ -263,9 +263,11 @@ __device__ void warp_walk_diagonal(const uint64_t *__restrict__ hits, uint32_t n
 // hit prefetched. The lanes of a warp advance in lock step, one iteration at
 // a time: (1) lanes without a hit in progress fetch their next extendable hit
 // (skipping hits with t < E, closing a diagonal when the diagonal word
-// changes) and score its seed span from a pair-sum table; (2) every lane whose
+// changes); (2) every lane whose
 // right side is still open scores its next 16 bases; (3) the same for the left
-// sides; (4) lanes whose two sides are closed emit the HSP and advance E. Most
+// sides; (4) lanes whose two sides are closed advance E and, when the two
+// extensions could reach the threshold with any seed span, score the span
+// from a pair-sum table and emit the HSP if it passes. Most
 // hits finish in one iteration, so the warp stays converged while its lanes
 // work on different hits and diagonals. A side that passes `lane_cap` bases
 // hands the rest of its diagonal to the warp tier.
@@ -283,6 +285,12 @@ __global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__r
     }
     __syncthreads();
     const int span = wp.span, X = wp.xdrop;
+    // upper bound of a seed span's score: the span is scored only for hits
+    // whose extensions could lift the HSP to the threshold
+    int maxsc = lut[0];
+#pragma unroll
+    for (int k = 1; k < 16; k++) maxsc = max(maxsc, lut[k]);
+    const long long s0_bound = (long long)span * maxsc;
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long lo64 = PERSIST ? 0 : tid * (long long)chunk;
     uint32_t range_end = PERSIST ? 0u : (uint32_t)min((long long)n, lo64 + chunk);
@@ -297,7 +305,7 @@ __global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__r
     SegCtx c;
     seg_ctx<BATCH>(wp, 0u, c);
     long long t = 0, q = 0;
-    int E = INT_MIN, cap = wp.lane_cap, s0 = 0, ravail = 0, lavail = 0;
+    int E = INT_MIN, cap = wp.lane_cap, ravail = 0, lavail = 0;
     LaneSide R{0, 0, 0, 0, true}, L{0, 0, 0, 0, true};
     unsigned long long ext = 0, cells = 0, tasks = 0;
     uint32_t status = 0;
@@ -346,7 +354,6 @@ __global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__r
                 continue;
             }
             q = t - (BATCH ? c.D : (long long)(D & 0x7FFFFFFFu)) + c.qoff;
-            s0 = span_score(wp.T, c.Q, c.tb + t, c.qb + q, span, psum, lut);
             ravail = (int)min(c.tlen - t - span, c.qlen - q - span);
             lavail = (int)min(t, q);
             R = LaneSide{0, 0, 0, 0, ravail == 0};
@@ -365,12 +372,17 @@ __global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__r
         if (busy && (R.best > SCORE_LIMIT || L.best > SCORE_LIMIT)) status |= ST_SCORE_OVERFLOW;
         // (4) finish or hand off
         if (busy && R.done && L.done) {
-            const long long score = (long long)s0 + R.best + L.best;
-            if (score > INT_MAX) status |= ST_SCORE_OVERFLOW;
+            const long long rl = (long long)R.best + L.best;
+            long long score = 0;
+            bool pass = false;
+            if (rl + s0_bound >= wp.thresh) {  // rare for random hits
+                score = rl + span_score(wp.T, c.Q, c.tb + t, c.qb + q, span, psum, lut);
+                if (score > INT_MAX) status |= ST_SCORE_OVERFLOW;
+                pass = score >= wp.thresh;
+            }
             ext++;
             cells += (unsigned long long)(span + R.n + L.n);
             log_ext(wp, c, t, q, R.n, L.n);
-            const bool pass = score >= wp.thresh;
             if (pass) emit<BATCH>(wp, c, t, q, L.blen, R.blen, score, status);
             if (pass || !(wp.flags & SFE_SKIP_PASSING_ONLY)) E = (int)(t + span + R.blen);
             i++;
