@@ -171,26 +171,28 @@ struct LaneSide {
     bool done;
 };
 
-// Largest X for which the packed-key window below cannot overflow int32.
-constexpr int PACKED_X_LIMIT = 1 << 26;
+// Largest X for which the packed-key window below cannot overflow int32
+// (scores are limited to |M| <= 2^20).
+constexpr int PACKED_X_LIMIT = 1 << 23;
 
 // Scores the next 16 bases of a side whose next base is (pt, pq) going `dir`
 // (+1 forward, -1 backward; a backward window is read bit-reversed).
 //
 // The window works on sums relative to the current maximum, so its values stay
-// within X + 16 max|score| whatever the side's length. With PACKED, cell j
-// keeps the maximum and its earliest position in one key, 16 * sum + (15 - j):
-// a larger key is a larger sum, or the same sum reached earlier, so one max
-// tracks both, and ties keep the older maximum. The stop test becomes
-// key_max - 16 * sum >= 16 * (X + 1). The running sum, the keys and the test
-// are multiply-adds (the FMA pipe), which leaves the integer ALU pipe (the
-// walk's limit) with the table index, the max and the compare. A stopped
-// side multiplies its scores by zero, which leaves its state unchanged.
+// within X + 16 max|score| whatever the side's length. With PACKED, the table
+// lut64 holds 64 * M - 1, and one accumulator carries both the running sum and
+// the count of scored cells: acc = 64 * sum - cells. Since cells <= 16 < 64, a
+// larger acc is a larger sum, or the same sum reached after fewer cells, so
+// max(acc) tracks the maximum and its earliest position at once (the previous
+// maximum is key 0 and wins ties). best - sum > X exactly when
+// max(acc) - acc >= 64 * (X + 1). A stopped side multiplies its scores by
+// zero, which freezes acc. Per cell: one table load, a multiply-add, a max,
+// a compare and a select.
 template <bool PACKED>
 __device__ __forceinline__ void lane_window(const uint32_t *__restrict__ T,
                                             const uint32_t *__restrict__ Q, long long pt,
                                             long long pq, int dir, int avail, int X,
-                                            const int *lut, LaneSide &sd) {
+                                            const int *lut, const int *lut64, LaneSide &sd) {
     const long long wt = dir > 0 ? pt + sd.n : pt - sd.n - 16;
     const long long wq = dir > 0 ? pq + sd.n : pq - sd.n - 16;
     uint32_t tw = win16(T, wt), qw = win16(Q, wq);
@@ -199,36 +201,37 @@ __device__ __forceinline__ void lane_window(const uint32_t *__restrict__ T,
         qw = rev2(qw);
     }
     const int lim = avail - sd.n;
-    int sum = -sd.d;  // relative to the current maximum
-    int cnt = 0, a = 1, bj = -1, gain = 0;
+    int cnt = 0, a = 1, bj = -1, gain = 0, sum = 0;
     if (PACKED) {
-        const int thr = 16 * (X + 1);
-        int bk = 15;  // key of the current maximum (relative sum 0, oldest position)
+        const int thr = 64 * (X + 1);
+        int acc = -64 * sd.d;
+        int bk = 0;  // key of the current maximum
         if (lim >= 16) {
 #pragma unroll
             for (int j = 0; j < 16; j++) {
-                const int sc = lut[((tw >> (2 * j)) & 3u) * 4u + ((qw >> (2 * j)) & 3u)];
-                sum = sc * a + sum;
-                cnt += a;
-                bk = max(bk, sum * 16 + (15 - j));
-                a = (bk - sum * 16 < thr) ? a : 0;
+                const int sc = lut64[((tw >> (2 * j)) & 3u) * 4u + ((qw >> (2 * j)) & 3u)];
+                acc = sc * a + acc;
+                bk = max(bk, acc);
+                a = (bk - acc < thr) ? a : 0;
             }
         } else {
 #pragma unroll
             for (int j = 0; j < 16; j++) {
-                const int sc = lut[((tw >> (2 * j)) & 3u) * 4u + ((qw >> (2 * j)) & 3u)];
+                const int sc = lut64[((tw >> (2 * j)) & 3u) * 4u + ((qw >> (2 * j)) & 3u)];
                 a = j < lim ? a : 0;
-                sum = sc * a + sum;
-                cnt += a;
-                bk = max(bk, sum * 16 + (15 - j));
-                a = (bk - sum * 16 < thr) ? a : 0;
+                acc = sc * a + acc;
+                bk = max(bk, acc);
+                a = (bk - acc < thr) ? a : 0;
             }
         }
-        if (bk != 15) {
-            gain = bk >> 4;
-            bj = 15 - (bk & 15);
+        cnt = (-acc) & 63;
+        sum = (acc + cnt) >> 6;
+        if (bk > 0) {
+            gain = (bk + 63) >> 6;
+            bj = 64 * gain - bk - 1;
         }
     } else {
+        sum = -sd.d;
         int lbest = 0;
 #pragma unroll
         for (int j = 0; j < 16; j++) {
@@ -276,8 +279,12 @@ __global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__r
                                                              uint32_t n, uint32_t chunk,
                                                              WalkParams wp) {
     __shared__ int lut[16];
+    __shared__ int lut64[16];
     __shared__ int psum[256];
-    if (threadIdx.x < 16) lut[threadIdx.x] = wp.scores[threadIdx.x];
+    if (threadIdx.x < 16) {
+        lut[threadIdx.x] = wp.scores[threadIdx.x];
+        lut64[threadIdx.x] = 64 * wp.scores[threadIdx.x] - 1;
+    }
     {
         const int e = threadIdx.x;  // W_BLOCK == 256 entries
         psum[e] = wp.scores[(e & 3) * 4 + ((e >> 4) & 3)] +
@@ -364,11 +371,12 @@ __global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__r
         // (2) right sides
         const bool needR = busy && !R.done;
         if (__any_sync(0xffffffffu, needR) && needR)
-            lane_window<PACKED>(wp.T, c.Q, c.tb + t + span, c.qb + q + span, 1, ravail, X, lut, R);
+            lane_window<PACKED>(wp.T, c.Q, c.tb + t + span, c.qb + q + span, 1, ravail, X, lut,
+                                lut64, R);
         // (3) left sides
         const bool needL = busy && !L.done;
         if (__any_sync(0xffffffffu, needL) && needL)
-            lane_window<PACKED>(wp.T, c.Q, c.tb + t, c.qb + q, -1, lavail, X, lut, L);
+            lane_window<PACKED>(wp.T, c.Q, c.tb + t, c.qb + q, -1, lavail, X, lut, lut64, L);
         if (busy && (R.best > SCORE_LIMIT || L.best > SCORE_LIMIT)) status |= ST_SCORE_OVERFLOW;
         // (4) finish or hand off
         if (busy && R.done && L.done) {

@@ -99,11 +99,16 @@ def _asym(seed):
     dict(pattern="111010010100110111"), dict(X=0), dict(X=50), dict(X=5000),
     dict(thresh=0), dict(thresh=-100000), dict(flags=1, thresh=1000), dict(strands=1),
     dict(strands=2), dict(scores="asym", X=300, thresh=500),
+    # the packed window's limits: X just below and at 2^23, scores near 2^19
+    dict(X=(1 << 23) - 1), dict(X=1 << 23), dict(scores="x4096", X=910 * 4096, thresh=3000 * 4096),
+    dict(scores="x4096", X=1 << 23, thresh=3000 * 4096),
 ], ids=lambda c: ",".join(f"{k}={v}" for k, v in c.items()) or "default")
 def test_parameters(pkg, ctx, case):
     case = dict(case)
     if case.get("scores") == "asym":
         case["scores"] = _asym(5)
+    elif case.get("scores") == "x4096":
+        case["scores"] = oracle.HOXD70.astype(np.int64) * 4096
     T, Q = _pair(11, 9_001, 7_333)
     got, st, ref = run_both(pkg, ctx, T, Q, **case)
     assert_same(got, st, ref)
