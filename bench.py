@@ -9,10 +9,14 @@ write, diagonal grouping, lane and warp walks, HSP sort. Inputs (ASCII bytes)
 are resident in HBM when the timed region starts; each step is timed with CUDA
 events on the library's stream, with a 256 MiB write between steps to flush L2.
 
-Prints one JSON line (rank 0). `value` is GCUPS: the oracle-defined cells
-(seed span plus bases scored on both sides of every extended hit) per second.
-`--impl reference` times the CPU oracle instead on a bounded sample of the
-same workload.
+Prints one JSON line (rank 0). `value` is GCUPS of the plain path (the
+library's defaults): the oracle-defined cells (seed span plus bases scored on
+both sides of every extended hit) per second. `learned_binned` times the same
+steps with the persistent walk taking its chunks of hits in the order of the
+work predictor (trained first, on the extension log of a plain run of the
+same generator at another seed) and checks that its HSP list is byte-identical
+to the plain path's. `--impl reference` times the CPU oracle instead on a
+bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -32,7 +36,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "ungapped X-drop GCUPS (oracle-defined cells/s), HSPs/s and hits/s"
+METRIC = ("ungapped X-drop GCUPS (oracle-defined cells/s), HSPs/s and hits/s; "
+          "learned-binned vs plain, bit-exact")
 WORKLOAD = "plain_pair_10mb"
 OPS_PER_CELL = 4  # score lookup, add, running max, X-drop compare
 L2_FLUSH_BYTES = 256 << 20
@@ -52,6 +57,13 @@ def args_parse():
                     help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-binned arm (predictor training and its timed steps)")
+    ap.add_argument("--train-seed", type=int, default=100,
+                    help="generator seed of the predictor's training pair")
+    ap.add_argument("--log-every", type=int, default=20,
+                    help="extension log sampling of the training run (1 in N)")
+    ap.add_argument("--learned-chunk", type=int, default=128)
     return ap.parse_args()
 
 
@@ -213,6 +225,45 @@ def run_reference(a, rank, world):
     return 0
 
 
+def train_predictor(a, pkg, ctx, dev):
+    """Train the work predictor on a plain run of the same generator at another
+    seed; returns (predictor, info)."""
+    import torch
+    from paper_2606_06811_gb300 import predictor
+    t0 = time.perf_counter()
+    tr = make_workload(a.train_seed, a.scale)[0]
+    recs, _ = predictor.collect(ctx, tr.T, tr.Q, a.log_every, cap=1 << 24,
+                                params=pkg.default_params(input_codes=1))
+    data = predictor.training_data(ctx, [(tr.T, tr.Q, recs)])
+    t1 = time.perf_counter()
+    pred = predictor.train(ctx, data, epochs=2, batch=8192, lr=2e-3, seed=3)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    info = {"train_workload": f"{WORKLOAD} seed {a.train_seed}", "samples": int(data.n),
+            "log_every": a.log_every, "epochs": 2, "batch": 8192, "lr": 2e-3,
+            "train_loss": [round(x, 5) for x in pred.history],
+            "collect_s": round(t1 - t0, 3), "train_s": round(t2 - t1, 3)}
+    data.close()
+    return pred, info
+
+
+def predictor_r2(a, pkg, ctx, pred, pair) -> dict:
+    """Accuracy of the FP16 predictor on the benchmark pair's own extensions."""
+    import torch
+    from paper_2606_06811_gb300 import predictor
+    recs, _ = predictor.collect(ctx, pair.T, pair.Q, a.log_every, cap=1 << 24,
+                                params=pkg.default_params(input_codes=1))
+    data = predictor.training_data(ctx, [(pair.T, pair.Q, recs)])
+    out = torch.zeros(data.n, dtype=torch.float32, device=recs.device)
+    ctx.mlp_predict(data, pred.model, out)
+    y = torch.log1p((recs[:, 4] + recs[:, 5]).double())
+    mse = float(((out.double() - y) ** 2).mean())
+    var = float(y.var(unbiased=False))
+    data.close()
+    return {"eval_samples": int(y.numel()), "mse": round(mse, 5), "target_var": round(var, 5),
+            "r2": round(1 - mse / var, 4)}
+
+
 def run_sfe(a, rank, world, local):
     import torch
     import paper_2606_06811_gb300 as pkg
@@ -238,13 +289,13 @@ def run_sfe(a, rank, world, local):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
 
-    def step():
+    def step(prm=params):
         with torch.cuda.stream(stream):
             flush.fill_(1)  # evicts L2 between steps, outside the events
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        hs, st = ctx.run(T, Q, params, out=out)
+        hs, st = ctx.run(T, Q, prm, out=out)
         e1.record(stream)
         return e0, e1, st, int(hs.shape[0])
 
@@ -324,6 +375,48 @@ def run_sfe(a, rank, world, local):
         "clocks": clk,
         "wall_s": wall,
     }
+
+    if not a.no_learned:
+        # learned-binned arm: persistent walk, chunks ordered by predicted work
+        plain_out = out[: recs[0][3]].clone()
+        pred, info = train_predictor(a, pkg, ctx, dev)
+        lp = pkg.default_params(flags=pkg.TIME_STAGES, lane_cap=a.lane_cap,
+                                tile_hits=a.tile_hits, walk_mode=pkg.WALK_PERSISTENT,
+                                walk_schedule=pkg.SCHED_PREDICTED, walk_chunk=a.learned_chunk,
+                                model=pred.model.data_ptr())
+        for _ in range(a.warmup):
+            step(lp)
+        torch.cuda.synchronize()
+        lrecs = [step(lp) for _ in range(a.steps)]
+        torch.cuda.synchronize()
+        l_ms = [e0.elapsed_time(e1) for e0, e1, _, _ in lrecs]
+        lst = [st for _, _, st, _ in lrecs]
+        l_cells = sum(x["cells"] for x in lst)
+        same = (lrecs[-1][3] == plain_out.shape[0] and
+                torch.equal(out[: lrecs[-1][3]], plain_out))
+        # the same persistent walk in hit order: what the predicted order changes
+        np_ = pkg.default_params(flags=pkg.TIME_STAGES, lane_cap=a.lane_cap,
+                                 tile_hits=a.tile_hits, walk_mode=pkg.WALK_PERSISTENT,
+                                 walk_chunk=a.learned_chunk)
+        for _ in range(a.warmup):
+            step(np_)
+        torch.cuda.synchronize()
+        nrecs = [step(np_) for _ in range(a.steps)]
+        torch.cuda.synchronize()
+        n_ms = [e0.elapsed_time(e1) for e0, e1, _, _ in nrecs]
+        n_cells = sum(st["cells"] for _, _, st, _ in nrecs)
+        line["learned_binned"] = {
+            "value": l_cells / (sum(l_ms) / 1e3) / 1e9, "unit": "GCUPS",
+            "ms_per_step": sum(l_ms) / a.steps,
+            "bit_exact_vs_plain": bool(same),
+            "hsps_per_s": sum(n for *_, n in lrecs) / (sum(l_ms) / 1e3),
+            "walk": f"persistent, chunks of {a.learned_chunk} hits ordered by predicted work",
+            "stage_ms": {k: round(sum(x["stage_ms"][k] for x in lst) / a.steps, 4)
+                         for k in pkg.STAGES},
+            "persistent_hit_order": {"value": n_cells / (sum(n_ms) / 1e3) / 1e9,
+                                     "ms_per_step": sum(n_ms) / a.steps},
+            "predictor": dict(info, **predictor_r2(a, pkg, ctx, pred, pair)),
+        }
 
     if not a.no_e2e:
         Th = torch.from_numpy(Ta.copy()).pin_memory()

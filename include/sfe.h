@@ -113,8 +113,9 @@ typedef struct {
     int32_t lanes_per_sm;     /* lane-tier threads per SM sharing a tile's hits (sizes their hit ranges); 0 = default */
     int64_t tile_hits;        /* hits per query tile (bounds scratch memory); 0 = default */
     int32_t walk_chunk;       /* hits a lane takes per grab from the work counter; 0 = default (32) */
-    int32_t walk_mode;        /* SFE_WALK_PERSISTENT (default) or SFE_WALK_TWO_LAUNCHES */
-    int32_t walk_schedule;    /* order in which the persistent walk hands out chunks (SFE_SCHED_*) */
+    int32_t walk_mode;        /* SFE_WALK_TWO_LAUNCHES (default) or SFE_WALK_PERSISTENT */
+    int32_t walk_schedule;    /* order in which the persistent walk hands out chunks (SFE_SCHED_*);
+                                 anything but SFE_SCHED_NATURAL needs SFE_WALK_PERSISTENT */
     int32_t ext_log_every;    /* log about 1 in ext_log_every extensions (0: no log) */
     sfe_ext_record *ext_log;  /* device buffer for the log; the choice of logged hits is a hash of
                                  (pair, strand, t, q), so it does not depend on the schedule */
@@ -130,9 +131,9 @@ typedef struct {
 #define SFE_SCHED_RANDOM 3        /* chunks in a fixed pseudo-random order (a control) */
 
 /* sfe_params.walk_mode */
-#define SFE_WALK_PERSISTENT 0   /* one launch: lanes pull chunks from a device counter, then
+#define SFE_WALK_TWO_LAUNCHES 0 /* lanes own fixed hit ranges; a second launch drains the queue */
+#define SFE_WALK_PERSISTENT 1   /* one launch: lanes pull chunks from a device counter, then
                                    the same warps drain the hand-off queue */
-#define SFE_WALK_TWO_LAUNCHES 1 /* lanes own fixed hit ranges; a second launch drains the queue */
 
 /* Statistics of one call. cells is the work measure of the method: seed span
  * plus the bases scored on both sides, summed over hits that were extended. */

@@ -42,7 +42,7 @@ const int32_t kHoxd70[16] = {91,   -114, -31, -123, -114, 100,  -125, -31,
                              -31,  -125, 100, -114, -123, -31,  -114, 91};
 const char *kDefaultPattern = "1110100110010101111";
 
-constexpr int kDefaultLaneCap = 96;
+constexpr int kDefaultLaneCap = 256;
 constexpr long long kDefaultTileHits = 1LL << 28;
 constexpr unsigned long long kQueueMax = 1ull << 20;
 
@@ -214,6 +214,8 @@ int check_params(const sfe_params *p) {
         return fail(SFE_EINVAL, "walk_mode must be SFE_WALK_PERSISTENT or SFE_WALK_TWO_LAUNCHES");
     if (p->walk_schedule < SFE_SCHED_NATURAL || p->walk_schedule > SFE_SCHED_RANDOM)
         return fail(SFE_EINVAL, "unknown walk_schedule");
+    if (p->walk_schedule != SFE_SCHED_NATURAL && p->walk_mode != SFE_WALK_PERSISTENT)
+        return fail(SFE_EINVAL, "a walk_schedule other than natural needs SFE_WALK_PERSISTENT");
     if (p->walk_schedule == SFE_SCHED_PREDICTED && (!p->model || !is_device_ptr(p->model)))
         return fail(SFE_EINVAL, "SFE_SCHED_PREDICTED needs params.model in device memory");
     if (p->ext_log_every < 0 || p->ext_log_cap < 0) return fail(SFE_EINVAL, "bad ext_log settings");

@@ -242,10 +242,10 @@ __global__ void pack_kernel16(const float *__restrict__ P, __half *__restrict__ 
 }
 
 // Predicted work of each chunk of hits for the learned schedule: the mean of
-// exp(prediction) over up to 4 hits of the chunk (its first hit and three
-// evenly spaced ones), times the chunk's hit count. One warp per chunk; FP16
-// weights, FP32 accumulation. Key: (~cost, chunk) so an ascending sort puts
-// the most work first.
+// exp(prediction) over two hits of the chunk (its first and its middle hit),
+// times the chunk's hit count. One warp per chunk; FP16 weights, FP32
+// accumulation. Key: (~cost, chunk) so an ascending sort puts the most work
+// first.
 __global__ void __launch_bounds__(MLP_BLOCK) chunk_predict_kernel(
     const uint64_t *__restrict__ hits, uint32_t n, uint32_t chunk, uint32_t nchunks,
     WalkParams wp, const __half *__restrict__ w16, const float *__restrict__ b32,
@@ -257,8 +257,8 @@ __global__ void __launch_bounds__(MLP_BLOCK) chunk_predict_kernel(
     const uint32_t len = min(chunk, n - i0);
     float cost = 0.f;
     int used = 0;
-    for (int j = 0; j < 4; j++) {
-        const uint32_t i = i0 + (uint32_t)((len * (uint32_t)j) / 4u);
+    for (int j = 0; j < 2; j++) {
+        const uint32_t i = i0 + (uint32_t)((len * (uint32_t)j) / 2u);
         if (j > 0 && i == i0) continue;
         const uint64_t h = hits[i];
         const uint32_t word = (uint32_t)(h >> 32);

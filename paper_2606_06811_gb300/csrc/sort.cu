@@ -19,7 +19,8 @@ constexpr int RS_BLOCK = 256;
 constexpr int RS_WARPS = RS_BLOCK / 32;
 constexpr int RS_ITEMS = 16;
 constexpr int RS_TILE = RS_BLOCK * RS_ITEMS;  // 4096
-constexpr int RS_R = 256;                     // buckets per pass (+1 for padding lanes)
+constexpr int RS_MAXBITS = 9;                 // widest digit
+constexpr int RS_R = 1 << RS_MAXBITS;         // buckets per pass (+1 for padding lanes)
 
 int g_num_sms = 0;
 
@@ -197,7 +198,7 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_scatter(
             tcount[d] = s;
         }
         __syncthreads();
-        // exclusive scan of tcount[0..R] by warp 0 (9 values per lane)
+        // exclusive scan of tcount[0..R] by warp 0 (17 values per lane)
         if (w == 0) {
             constexpr int PER = (RS_R + 1 + 31) / 32;
             unsigned loc[PER], s = 0;
@@ -390,8 +391,12 @@ cudaError_t radix_sort(uint64_t *keys_a, uint64_t *keys_b, uint32_t *vals_a, uin
     uint64_t *kin = keys_a, *kout = keys_b;
     uint32_t *vin = vals_a, *vout = vals_b;
     bool in_b = false;
-    for (int shift = lo; shift < hi; shift += 8) {
-        int bits = min(8, hi - shift);
+    // as few passes as the widest digit allows, with the bits spread evenly
+    // over them (a 25-bit key takes 9 + 8 + 8, not 8 + 8 + 8 + 1)
+    const int npass = (hi - lo + RS_MAXBITS - 1) / RS_MAXBITS;
+    const int per = (hi - lo + npass - 1) / npass;
+    for (int shift = lo; shift < hi; shift += per) {
+        int bits = min(per, hi - shift);
         unsigned mask = (1u << bits) - 1u;
         cudaMemsetAsync(totals, 0, RS_R * 4, st);
         g_launches += 3;

@@ -171,6 +171,13 @@ struct LaneSide {
     bool done;
 };
 
+// The 2-bit codes in bits 0..15 of x, one per nibble (code k -> bits 4k, 4k + 1).
+__device__ __forceinline__ uint32_t spread8(uint32_t x, uint32_t sel) {
+    x = __byte_perm(x, 0u, sel);  // two bytes of x into the low bytes of the halfwords
+    x = (x | (x << 4)) & 0x0F0F0F0Fu;
+    return (x | (x << 2)) & 0x33333333u;
+}
+
 // Largest X for which the packed-key window below cannot overflow int32
 // (scores are limited to |M| <= 2^20).
 constexpr int PACKED_X_LIMIT = 1 << 23;
@@ -206,10 +213,13 @@ __device__ __forceinline__ void lane_window(const uint32_t *__restrict__ T,
         const int thr = 64 * (X + 1);
         int acc = -64 * sd.d;
         int bk = 0;  // key of the current maximum
+        // table index of cell j (4 * t + q) in nibble j of z[j / 8]
+        const uint32_t z[2] = {spread8(tw, 0x4140u) * 4u + spread8(qw, 0x4140u),
+                               spread8(tw, 0x4342u) * 4u + spread8(qw, 0x4342u)};
         if (lim >= 16) {
 #pragma unroll
             for (int j = 0; j < 16; j++) {
-                const int sc = lut64[((tw >> (2 * j)) & 3u) * 4u + ((qw >> (2 * j)) & 3u)];
+                const int sc = lut64[(z[j >> 3] >> (4 * (j & 7))) & 15u];
                 acc = sc * a + acc;
                 bk = max(bk, acc);
                 a = (bk - acc < thr) ? a : 0;
@@ -217,7 +227,7 @@ __device__ __forceinline__ void lane_window(const uint32_t *__restrict__ T,
         } else {
 #pragma unroll
             for (int j = 0; j < 16; j++) {
-                const int sc = lut64[((tw >> (2 * j)) & 3u) * 4u + ((qw >> (2 * j)) & 3u)];
+                const int sc = lut64[(z[j >> 3] >> (4 * (j & 7))) & 15u];
                 a = j < lim ? a : 0;
                 acc = sc * a + acc;
                 bk = max(bk, acc);

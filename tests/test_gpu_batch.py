@@ -76,7 +76,7 @@ def test_batch_single_strand_and_lane_cap(pkg):
     check(pkg, pairs, strands=1)
 
 
-@pytest.mark.parametrize("mode,sched,chunk", [(1, 0, 0), (0, 1, 16), (0, 0, 3)])
+@pytest.mark.parametrize("mode,sched,chunk", [(0, 0, 0), (1, 1, 16), (1, 0, 3), (1, 3, 8)])
 def test_batch_walk_modes(pkg, mode, sched, chunk):
     pairs = synth.batch_pairs(seed=6, n_pairs=64, len_lo=1000, len_hi=30_000)
     check(pkg, pairs, walk_mode=mode, walk_schedule=sched, walk_chunk=chunk, lane_cap=32)

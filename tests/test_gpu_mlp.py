@@ -57,8 +57,9 @@ def test_extension_log_is_every_extension_of_the_oracle(pkg, ctx, tiny):
     p, ref = tiny
     want = {(int(e["strand"]), int(e["t"]), int(e["q"]), int(e["rscored"]), int(e["lscored"]))
             for e in ref.ext}
-    for kw in ({}, {"lane_cap": 1}, {"walk_mode": pkg.WALK_TWO_LAUNCHES},
-               {"walk_schedule": pkg.SCHED_RANDOM, "walk_chunk": 4}):
+    for kw in ({}, {"lane_cap": 1}, {"walk_mode": pkg.WALK_PERSISTENT},
+               {"walk_mode": pkg.WALK_PERSISTENT, "walk_schedule": pkg.SCHED_RANDOM,
+                "walk_chunk": 4}):
         recs, st = ext_records(pkg, ctx, p.T, p.Q, 1, **kw)
         r = recs.cpu().numpy()
         assert st["ext_logged"] == ref.extended == r.shape[0], kw
@@ -69,9 +70,9 @@ def test_extension_log_is_every_extension_of_the_oracle(pkg, ctx, tiny):
 def test_sampled_log_does_not_depend_on_the_schedule(pkg, ctx, tiny):
     p, ref = tiny
     base = None
-    for kw in ({}, {"walk_mode": pkg.WALK_TWO_LAUNCHES, "lane_cap": 8},
-               {"walk_schedule": pkg.SCHED_LARGEST_FIRST},
-               {"walk_schedule": pkg.SCHED_RANDOM}):
+    P_ = pkg.WALK_PERSISTENT
+    for kw in ({}, {"lane_cap": 8}, {"walk_mode": P_, "walk_schedule": pkg.SCHED_LARGEST_FIRST},
+               {"walk_mode": P_, "walk_schedule": pkg.SCHED_RANDOM}):
         recs, st = ext_records(pkg, ctx, p.T, p.Q, 7, **kw)
         s = rec_set(recs.cpu().numpy())
         assert len(s) == recs.shape[0]
@@ -183,7 +184,10 @@ def test_bad_records_and_missing_model_are_rejected(pkg, ctx, torch, tiny):
     with pytest.raises(pkg.SfeError):
         ctx.mlp_data(p.T, [0, p.tlen], p.Q, [0, p.qlen], bad, input_codes=1)
     with pytest.raises(pkg.SfeError):
-        ctx.run(p.T, p.Q, pkg.default_params(input_codes=1, walk_schedule=pkg.SCHED_PREDICTED))
+        ctx.run(p.T, p.Q, pkg.default_params(input_codes=1, walk_mode=pkg.WALK_PERSISTENT,
+                                             walk_schedule=pkg.SCHED_PREDICTED))
+    with pytest.raises(pkg.SfeError):  # a schedule orders the persistent walk only
+        ctx.run(p.T, p.Q, pkg.default_params(input_codes=1, walk_schedule=pkg.SCHED_RANDOM))
 
 
 @pytest.fixture(scope="module")
@@ -220,7 +224,8 @@ def test_predicted_schedule_keeps_the_oracle_output(pkg, ctx, trained):
     for seed, kw in ((1, {}), (2, {"walk_chunk": 4, "lane_cap": 16}), (3, {"walk_chunk": 200})):
         p = synth.tiny_pair(seed, length=80_000, n_blocks=20)
         ref = oracle.run(p.T, p.Q)
-        prm = pkg.default_params(input_codes=1, walk_schedule=pkg.SCHED_PREDICTED,
+        prm = pkg.default_params(input_codes=1, walk_mode=pkg.WALK_PERSISTENT,
+                                 walk_schedule=pkg.SCHED_PREDICTED,
                                  model=trained.model.data_ptr(), **kw)
         got, st = ctx.run(p.T, p.Q, prm)
         a = np.ascontiguousarray(got).view(np.int32).reshape(-1, 5)
@@ -232,8 +237,9 @@ def test_predicted_schedule_keeps_the_oracle_output(pkg, ctx, trained):
 def test_predicted_schedule_on_a_batch(pkg, ctx, trained):
     pairs = synth.batch_pairs(seed=9, n_pairs=16, len_lo=2000, len_hi=40_000)
     T, toff, Q, qoff = concat_batch(pairs)
-    prm = pkg.default_params(input_codes=1, walk_schedule=pkg.SCHED_PREDICTED,
-                             model=trained.model.data_ptr(), walk_chunk=8)
+    prm = pkg.default_params(input_codes=1, walk_mode=pkg.WALK_PERSISTENT,
+                             walk_schedule=pkg.SCHED_PREDICTED, model=trained.model.data_ptr(),
+                             walk_chunk=8)
     got, st = ctx.run_batch(T, toff, Q, qoff, prm)
     H = np.ascontiguousarray(got).view(np.int32).reshape(-1, 6)
     for i, pr in enumerate(pairs):

@@ -211,8 +211,8 @@ def test_ungapped_xdrop_api_on_shuffled_oracle_hits(pkg, ctx):
 
 
 @pytest.mark.parametrize("mode,chunk,sched,cap", [
-    (1, 0, 0, 96), (0, 1, 0, 16), (0, 7, 1, 16), (0, 32, 1, 96), (0, 500, 0, 16),
-    (0, 32, 0, 1 << 30), (0, 64, 1, 1),
+    (0, 0, 0, 96), (1, 1, 0, 16), (1, 7, 1, 16), (1, 32, 1, 96), (1, 500, 0, 16),
+    (1, 32, 0, 1 << 30), (1, 64, 1, 1), (1, 16, 3, 16), (0, 0, 0, 0),
 ])
 def test_walk_modes_chunks_and_schedules(pkg, ctx, mode, chunk, sched, cap):
     """Persistent or two-launch walks, any chunk size and chunk order: same output."""
@@ -225,6 +225,7 @@ def test_walk_modes_chunks_and_schedules(pkg, ctx, mode, chunk, sched, cap):
 def test_persistent_walk_on_identical_sequences(pkg, ctx):
     st = synth.Stream(32, "ident2")
     T = synth.iid_bases(st, 30_000, 0.5)
-    got, stt, ref = run_both(pkg, ctx, T, T.copy(), walk_chunk=8, walk_schedule=1, lane_cap=16)
+    got, stt, ref = run_both(pkg, ctx, T, T.copy(), walk_mode=pkg.WALK_PERSISTENT, walk_chunk=8,
+                             walk_schedule=1, lane_cap=16)
     assert_same(got, stt, ref)
     assert stt["warp_tasks"] > 0
