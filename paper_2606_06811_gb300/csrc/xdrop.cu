@@ -274,9 +274,9 @@ __device__ void warp_walk_diagonal(const uint64_t *__restrict__ hits, uint32_t n
 // Lane tier. Lane k owns the diagonals that start in hit range
 // [k*chunk, (k+1)*chunk) and streams through its hits in order, with the next
 // hit prefetched. The lanes of a warp advance in lock step, one iteration at
-// a time: (1) lanes without a hit in progress fetch their next extendable hit
-// (skipping hits with t < E, closing a diagonal when the diagonal word
-// changes); (2) every lane whose
+// a time: (1) each lane without a hit in progress looks at its next hit
+// (closing its diagonal and opening the next when the diagonal word changes)
+// and skips it if t < E, or starts extending it; (2) every lane whose
 // right side is still open scores its next 16 bases; (3) the same for the left
 // sides; (4) lanes whose two sides are closed advance E and, when the two
 // extensions could reach the threshold with any seed span, score the span
@@ -328,54 +328,56 @@ __global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__r
     uint32_t status = 0;
 
     while (true) {
-        // (1) fetch
-        while (!busy && !done) {
-            if (!in_seg) {
-                if (i >= range_end) {
-                    if (!PERSIST) {
-                        done = true;
-                        break;
-                    }
-                    // take the next chunk of hits from the work counter
-                    const uint32_t w = atomicAdd(wp.work_next, 1u);
-                    if (w >= wp.nchunks) {
-                        done = true;
-                        break;
-                    }
-                    const uint32_t ck = wp.order ? wp.order[w] : w;
-                    i = ck * wp.chunk;
-                    range_end = (uint32_t)min((long long)n, (long long)i + wp.chunk);
-                    if (i > 0 && i < range_end && diag_of(hits[i]) == diag_of(hits[i - 1]))
-                        i = segment_end(hits, i, n, diag_of(hits[i]));
-                    cur = i < n ? hits[i] : ~0ull;
-                    continue;
-                }
-                D = diag_of(cur);
-                if (BATCH) seg_ctx<BATCH>(wp, D, c);
-                E = wp.Ecarry ? wp.Ecarry[D & 0x7FFFFFFFu] : INT_MIN;
-                in_seg = true;
-                handed = false;
-                cap = wp.lane_cap;
-                tasks++;
-            }
-            if (i >= n || diag_of(cur) != D) {
-                if (!handed && wp.Ecarry) wp.Ecarry[D & 0x7FFFFFFFu] = E;
+        // (1) fetch: a lane without a hit in progress looks at one hit per
+        // iteration (straight-line, so the lanes stay converged)
+        if (!busy && !done) {
+            if (!in_seg || i >= n || diag_of(cur) != D) {
+                // diagonal boundary: close the current one, open the next
+                if (in_seg && !handed && wp.Ecarry) wp.Ecarry[D & 0x7FFFFFFFu] = E;
                 in_seg = false;
-                continue;
+                if (i >= range_end) {
+                    if (PERSIST) {
+                        // take the next chunk of hits from the work counter
+                        const uint32_t w = atomicAdd(wp.work_next, 1u);
+                        if (w >= wp.nchunks) {
+                            done = true;
+                        } else {
+                            const uint32_t ck = wp.order ? wp.order[w] : w;
+                            i = ck * wp.chunk;
+                            range_end = (uint32_t)min((long long)n, (long long)i + wp.chunk);
+                            if (i > 0 && i < range_end && diag_of(hits[i]) == diag_of(hits[i - 1]))
+                                i = segment_end(hits, i, n, diag_of(hits[i]));
+                            cur = i < n ? hits[i] : ~0ull;
+                        }
+                    } else {
+                        done = true;
+                    }
+                }
+                if (!done && i < range_end) {
+                    D = diag_of(cur);
+                    if (BATCH) seg_ctx<BATCH>(wp, D, c);
+                    E = wp.Ecarry ? wp.Ecarry[D & 0x7FFFFFFFu] : INT_MIN;
+                    in_seg = true;
+                    handed = false;
+                    cap = wp.lane_cap;
+                    tasks++;
+                }
             }
-            t = (long long)(uint32_t)cur;
-            nxt = (i + 1 < n) ? hits[i + 1] : ~0ull;  // consumed when this hit is done
-            if (t < E) {
-                i++;
-                cur = nxt;
-                continue;
+            if (in_seg) {
+                t = (long long)(uint32_t)cur;
+                nxt = (i + 1 < n) ? hits[i + 1] : ~0ull;  // consumed when this hit is done
+                if (t < E) {  // inside the last HSP of its diagonal: skipped
+                    i++;
+                    cur = nxt;
+                } else {
+                    q = t - (BATCH ? c.D : (long long)(D & 0x7FFFFFFFu)) + c.qoff;
+                    ravail = (int)min(c.tlen - t - span, c.qlen - q - span);
+                    lavail = (int)min(t, q);
+                    R = LaneSide{0, 0, 0, 0, ravail == 0};
+                    L = LaneSide{0, 0, 0, 0, lavail == 0};
+                    busy = true;
+                }
             }
-            q = t - (BATCH ? c.D : (long long)(D & 0x7FFFFFFFu)) + c.qoff;
-            ravail = (int)min(c.tlen - t - span, c.qlen - q - span);
-            lavail = (int)min(t, q);
-            R = LaneSide{0, 0, 0, 0, ravail == 0};
-            L = LaneSide{0, 0, 0, 0, lavail == 0};
-            busy = true;
         }
         if (__all_sync(0xffffffffu, done)) break;
         // (2) right sides
