@@ -46,7 +46,7 @@ L2_FLUSH_BYTES = 256 << 20
 def args_parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sfe", choices=["sfe", "reference"])
     ap.add_argument("--seed", type=int, default=2)
