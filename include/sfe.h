@@ -229,6 +229,34 @@ int sfe_run_batch(sfe_ctx *ctx, const uint8_t *targets, const int64_t *toff,
                   sfe_stats *stats);
 
 /*
+ * A batch captured as a CUDA graph (the batch of sfe_run_batch, replayed).
+ *
+ * sfe_run_batch keeps every count of its pipeline in device memory (the hit
+ * sort, the walk and the HSP sort read them there), so its device work needs
+ * no host synchronisation between stages. A plan fixes the pairs' lengths
+ * (toff, qoff as in sfe_run_batch) and the parameters, allocates every buffer
+ * the pipeline touches, and captures pack, index, hit emission, sort, walk
+ * and HSP sort into one CUDA graph on the context's stream; each run copies
+ * new sequences of those lengths into the plan and replays the graph. hit_cap
+ * bounds the hits of one run (0: an estimate from the lengths); a run that
+ * finds more hits, or more HSPs than the plan holds, grows the plan, captures
+ * it again and replays once more, so the output never depends on the caps.
+ * The parameters are copied, but pointers in them (ext_log, model) are
+ * captured as they are and must stay valid while the plan is used;
+ * SFE_TIME_STAGES is rejected. A plan belongs to its context and its stream
+ * and is not thread-safe.
+ */
+typedef struct sfe_batch_plan sfe_batch_plan;
+
+int sfe_batch_plan_create(sfe_ctx *ctx, const int64_t *toff, const int64_t *qoff, int32_t npairs,
+                          const sfe_params *params, int64_t hit_cap, sfe_batch_plan **out);
+/* targets / queries: toff[npairs] / qoff[npairs] bases (host or device);
+ * hsps, cap, nhsps and stats as in sfe_run_batch. */
+int sfe_batch_plan_run(sfe_batch_plan *plan, const uint8_t *targets, const uint8_t *queries,
+                       sfe_batch_hsp *hsps, int64_t cap, int64_t *nhsps, sfe_stats *stats);
+void sfe_batch_plan_free(sfe_batch_plan *plan);
+
+/*
  * Work predictor of the learned schedule (SFE_SCHED_PREDICTED).
  *
  * The paper names the load imbalance of X-drop extensions (Section 8: some

@@ -412,8 +412,13 @@ struct WalkSetup {
 
 // The lane and warp tiers over hits sorted by (diagonal word, t), in one
 // persistent launch or as two launches (params->walk_mode).
+// `sm` is the counter block (the context's by default) and `sched_tmp` the
+// schedule's scratch (taken from the arena by default); both are given by a
+// batch plan, whose captured graph must own every buffer it touches.
 int walk_tiers(sfe_ctx *c, const uint64_t *hits, long long n, WalkParams &wp, uint4 *queue,
-               unsigned long long qcap, const sfe_params *p) {
+               unsigned long long qcap, const sfe_params *p, Small *sm = nullptr,
+               void *sched_tmp = nullptr) {
+    if (!sm) sm = c->small;
     if (p->ext_log && p->ext_log_every > 0) {
         wp.elog = p->ext_log;
         wp.elog_cap = (unsigned long long)std::max<int64_t>(0, p->ext_log_cap);
@@ -421,8 +426,8 @@ int walk_tiers(sfe_ctx *c, const uint64_t *hits, long long n, WalkParams &wp, ui
     }
     wp.queue = queue;
     wp.queue_cap = qcap;
-    wp.queue_len = &c->small->queue_len;
-    CK(cudaMemsetAsync(&c->small->queue_len, 0, 4, c->st));
+    wp.queue_len = &sm->queue_len;
+    CK(cudaMemsetAsync(&sm->queue_len, 0, 4, c->st));
     if (p->walk_mode == SFE_WALK_TWO_LAUNCHES) {
         {
             Span sp(c, SFE_STAGE_WALK_LANES);
@@ -434,22 +439,22 @@ int walk_tiers(sfe_ctx *c, const uint64_t *hits, long long n, WalkParams &wp, ui
     }
     if (++c->epoch == 0) c->epoch = 1;
     wp.epoch = c->epoch;
-    wp.work_next = &c->small->work_next;
-    wp.warps_done = &c->small->warps_done;
-    wp.queue_take = &c->small->queue_take;
+    wp.work_next = &sm->work_next;
+    wp.warps_done = &sm->warps_done;
+    wp.queue_take = &sm->queue_take;
     wp.chunk = p->walk_chunk > 0 ? (uint32_t)p->walk_chunk : 32u;
     wp.order = nullptr;
     if (p->walk_schedule != SFE_SCHED_NATURAL) {
         Span sp(c, SFE_STAGE_SCHEDULE);
-        void *tmp = nullptr;
-        TRY(ensure(c, SL_SCHED, walk_schedule_temp_bytes(n, wp.chunk), &tmp));
+        void *tmp = sched_tmp;
+        if (!tmp) TRY(ensure(c, SL_SCHED, walk_schedule_temp_bytes(n, wp.chunk), &tmp));
         uint32_t *order = nullptr;
         CK(launch_walk_schedule(hits, n, wp, p->walk_schedule, p->model, tmp, &order,
-                                &c->small->status, c->st));
+                                &sm->status, c->st));
         wp.order = order;
     }
     Span sp(c, SFE_STAGE_WALK_LANES);
-    CK(cudaMemsetAsync(&c->small->work_next, 0, 12, c->st));
+    CK(cudaMemsetAsync(&sm->work_next, 0, 12, c->st));
     CK(cudaMemsetAsync(queue, 0, (size_t)qcap * sizeof(uint4), c->st));
     CK(launch_walk_persistent(hits, n, wp, c->st));
     return SFE_OK;
@@ -926,178 +931,498 @@ int sfe_run(sfe_ctx *c, const uint8_t *target, int64_t tlen, const uint8_t *quer
     return r;
 }
 
-int sfe_run_batch(sfe_ctx *c, const uint8_t *targets, const int64_t *toff, const uint8_t *queries,
-                  const int64_t *qoff, int32_t npairs, const sfe_params *params,
-                  sfe_batch_hsp *hsps, int64_t cap, int64_t *nhsps, sfe_stats *stats) {
-    if (!nhsps || !toff || !qoff) return fail(SFE_EINVAL, "nhsps, toff or qoff is NULL");
+}  // extern "C"
+
+// A batch of pairs: the pair table, the work items and the index buckets,
+// fixed by the pairs' lengths and the seed.
+struct BatchGeom {
+    int npairs = 0;
+    SeedPattern pat{};
+    long long ttot = 0, qtot = 0, maxlen = 1, nbuckets = 0, titems = 0, qitems = 0;
+    int dbits = 0, pbits = 0;
+    std::vector<PairInfo> P;
+    std::vector<long long> pref;  // target item prefix (npairs + 1), then query's
+};
+
+// Device buffers of one batch pipeline, and where its results end up.
+struct BatchBufs {
+    const uint8_t *tin = nullptr, *qin = nullptr;  // input bytes on the device
+    unsigned char *meta = nullptr;                   // pair table + item prefixes
+    uint32_t *tp = nullptr, *qp = nullptr, *qm = nullptr;  // packed (padded allocations)
+    uint32_t *bcnt = nullptr, *boffs = nullptr;
+    uint64_t *entries = nullptr;
+    uint64_t *ha = nullptr, *hb = nullptr;
+    unsigned long long hitcap = 0;
+    BatchHsp *hsps = nullptr;
+    unsigned long long hcap = 0;
+    uint4 *queue = nullptr;
+    unsigned long long qcap = 0;
+    void *tmp = nullptr;        // scans, sorts
+    void *sched_tmp = nullptr;  // chunk schedule
+    Small *small = nullptr;     // counters (scores set once)
+    unsigned long long *nhits = nullptr;  // hit count the later stages use (0 on overflow)
+    BatchHsp *sorted = nullptr;           // set by the pipeline
+};
+
+namespace {
+
+int batch_geometry(const int64_t *toff, const int64_t *qoff, int npairs, const sfe_params *params,
+                   BatchGeom &g) {
+    if (!toff || !qoff) return fail(SFE_EINVAL, "toff or qoff is NULL");
     if (npairs < 1 || npairs > (1 << 16)) return fail(SFE_EINVAL, "npairs must be 1..65536");
     TRY(check_params(params));
-    SeedPattern pat;
-    TRY(parse_pattern(params->seed_pattern, &pat));
+    TRY(parse_pattern(params->seed_pattern, &g.pat));
     if (toff[0] != 0 || qoff[0] != 0) return fail(SFE_EINVAL, "offsets must start at 0");
-    long long maxsum = 1, maxlen = 1;
+    long long maxsum = 1;
+    g.maxlen = 1;
     for (int p = 0; p < npairs; p++) {
         const long long tl = toff[p + 1] - toff[p], ql = qoff[p + 1] - qoff[p];
         if (tl < 0 || ql < 0) return fail(SFE_EINVAL, "offsets must not decrease");
         if (tl >= (1LL << 20) || ql >= (1LL << 20))
             return fail(SFE_EINVAL, "batch sequences must be shorter than 2^20 bases");
         maxsum = std::max(maxsum, tl + ql);
-        maxlen = std::max(maxlen, std::max(tl, ql));
+        g.maxlen = std::max(g.maxlen, std::max(tl, ql));
     }
-    const long long ttot = toff[npairs], qtot = qoff[npairs];
-    TRY(check_len(ttot, "concatenated target"));
-    TRY(check_len(qtot, "concatenated query"));
-    const int dbits = bits_for(maxsum), pbits = bits_for(npairs - 1);
-    if (pbits + 1 + dbits > 32) return fail(SFE_EINVAL, "too many pairs for their lengths");
-    TRY(begin(c, params->flags));
-    TRY(upload_scores(c, params->scores));
-
-    // pairs and the layout of their index buckets
-    std::vector<PairInfo> P(npairs);
-    long long nbuckets = 0;
-    const int kbits = 2 * pat.weight;
+    g.npairs = npairs;
+    g.ttot = toff[npairs];
+    g.qtot = qoff[npairs];
+    TRY(check_len(g.ttot, "concatenated target"));
+    TRY(check_len(g.qtot, "concatenated query"));
+    g.dbits = bits_for(maxsum);
+    g.pbits = bits_for(npairs - 1);
+    if (g.pbits + 1 + g.dbits > 32) return fail(SFE_EINVAL, "too many pairs for their lengths");
+    g.P.assign(npairs, PairInfo{});
+    g.nbuckets = 0;
+    const int kbits = 2 * g.pat.weight;
     for (int p = 0; p < npairs; p++) {
-        PairInfo &x = P[p];
+        PairInfo &x = g.P[p];
         x.toff = toff[p];
         x.qoff = qoff[p];
-        x.qoff_rc = qtot - qoff[p + 1];
+        x.qoff_rc = g.qtot - qoff[p + 1];
         x.tlen = (int)(toff[p + 1] - toff[p]);
         x.qlen = (int)(qoff[p + 1] - qoff[p]);
-        const long long npos = std::max(1LL, (long long)x.tlen - pat.span + 1);
+        const long long npos = std::max(1LL, (long long)x.tlen - g.pat.span + 1);
         x.bbits = std::min(kbits, std::max(4, bits_for(npos - 1)));
-        x.boff = nbuckets;
+        x.boff = g.nbuckets;
         x.pad = 0;
-        nbuckets += 1LL << x.bbits;
+        g.nbuckets += 1LL << x.bbits;
     }
     // work items: chunks of one pair's target / query positions, pair by pair
     const int item = batch_item_size();
-    std::vector<long long> pref(2 * (size_t)(npairs + 1));
-    long long *tpref = pref.data(), *qpref = pref.data() + npairs + 1;
-    tpref[0] = qpref[0] = 0;
+    g.pref.assign(2 * (size_t)(npairs + 1), 0);
+    long long *tpref = g.pref.data(), *qpref = g.pref.data() + npairs + 1;
     for (int p = 0; p < npairs; p++) {
-        const long long nt = std::max(0LL, (long long)P[p].tlen - pat.span + 1);
-        const long long nq = std::max(0LL, (long long)P[p].qlen - pat.span + 1);
+        const long long nt = std::max(0LL, (long long)g.P[p].tlen - g.pat.span + 1);
+        const long long nq = std::max(0LL, (long long)g.P[p].qlen - g.pat.span + 1);
         tpref[p + 1] = tpref[p] + (nt + item - 1) / item;
         qpref[p + 1] = qpref[p] + 2 * ((nq + item - 1) / item);
     }
-    const long long titems = tpref[npairs], qitems = qpref[npairs];
-    if (titems >= (1LL << 31) || qitems >= (1LL << 31)) return fail(SFE_EINVAL, "batch too large");
-    const size_t pbytes = ((size_t)npairs * sizeof(PairInfo) + 255) & ~(size_t)255;
-    unsigned char *dmeta = nullptr;
-    TRY(ensure_t(c, SL_PAIRS, pbytes + pref.size() * 8, &dmeta));
-    PairInfo *dpairs = reinterpret_cast<PairInfo *>(dmeta);
-    long long *dtpref = reinterpret_cast<long long *>(dmeta + pbytes);
-    long long *dqpref = dtpref + npairs + 1;
-    CK(cudaMemcpyAsync(dpairs, P.data(), (size_t)npairs * sizeof(PairInfo), cudaMemcpyHostToDevice,
-                       c->st));
-    CK(cudaMemcpyAsync(dtpref, pref.data(), pref.size() * 8, cudaMemcpyHostToDevice, c->st));
+    g.titems = tpref[npairs];
+    g.qitems = qpref[npairs];
+    if (g.titems >= (1LL << 31) || g.qitems >= (1LL << 31))
+        return fail(SFE_EINVAL, "batch too large");
+    return SFE_OK;
+}
 
-    uint32_t *Tp = nullptr, *Qp = nullptr, *Qm = nullptr;
+size_t batch_meta_bytes(const BatchGeom &g) {
+    return (((size_t)g.npairs * sizeof(PairInfo) + 255) & ~(size_t)255) + g.pref.size() * 8;
+}
+
+// Scratch shared by the scans and the sorts of a batch.
+size_t batch_tmp_bytes(const BatchGeom &g, unsigned long long hitcap, unsigned long long hcap) {
+    size_t t = std::max(scan_temp_bytes(g.nbuckets), scan_temp_bytes(2 * g.qtot));
+    t = std::max(t, radix_sort_temp_bytes((long long)hitcap));
+    return std::max(t, batch_hsp_sort_temp_bytes((long long)hcap));
+}
+
+__global__ void guard_count_kernel(const unsigned long long *total, unsigned long long cap,
+                                   unsigned long long *n) {
+    *n = *total <= cap ? *total : 0ull;  // an overflowed hit list is not walked
+}
+
+// The whole batch on the device, without host synchronisation: pack, index,
+// one-pass hit emission, sort, walk, HSP sort. Counts stay on the device
+// (the sort, the walk and the HSP sort read them there), so the same calls
+// run eagerly or are captured once into a CUDA graph. The pair table and the
+// item prefixes must already be in b.meta and the scores in b.small.
+int batch_pipeline(sfe_ctx *c, const BatchGeom &g, const sfe_params *params, BatchBufs &b) {
+    cudaStream_t st = c->st;
+    Small *sm = b.small;
+    CK(cudaMemsetAsync(&sm->ctr, 0, sizeof(DevCounters), st));
+    CK(cudaMemsetAsync(&sm->status, 0, 4, st));
+    const size_t pbytes = ((size_t)g.npairs * sizeof(PairInfo) + 255) & ~(size_t)255;
+    const PairInfo *dpairs = reinterpret_cast<const PairInfo *>(b.meta);
+    const long long *dtpref = reinterpret_cast<const long long *>(b.meta + pbytes);
+    const long long *dqpref = dtpref + g.npairs + 1;
+    uint32_t *Tp = b.tp + SEQ_PAD, *Qp = b.qp + SEQ_PAD, *Qm = b.qm + SEQ_PAD;
     {
         Span sp(c, SFE_STAGE_PACK);
-        const void *tdev = nullptr, *qdev = nullptr;
-        TRY(stage(c, SL_TIN, targets, (size_t)ttot, &tdev));
-        TRY(stage(c, SL_QIN, queries, (size_t)qtot, &qdev));
-        TRY(pack_slot(c, SL_TP, reinterpret_cast<const uint8_t *>(tdev), ttot, params->input_codes,
-                      &Tp));
-        TRY(pack_slot(c, SL_QP, reinterpret_cast<const uint8_t *>(qdev), qtot, params->input_codes,
-                      &Qp));
-        TRY(rc_slot(c, SL_QM, Qp, qtot, &Qm));
+        CK(launch_pack(b.tin, g.ttot, params->input_codes, Tp, &sm->status, st));
+        CK(launch_pack(b.qin, g.qtot, params->input_codes, Qp, &sm->status, st));
+        CK(launch_revcomp(Qp, g.qtot, Qm, st));
     }
-    uint32_t *bcnt = nullptr, *boffs = nullptr;
-    uint64_t *entries = nullptr;
-    void *tmp = nullptr;
     {
         Span sp(c, SFE_STAGE_INDEX);
-        TRY(ensure_t(c, SL_BCOUNT, (size_t)nbuckets, &bcnt));
-        TRY(ensure_t(c, SL_OFFS, (size_t)nbuckets + 1, &boffs));
-        TRY(ensure_t(c, SL_BENTRIES, (size_t)std::max(1LL, ttot), &entries));
-        TRY(ensure(c, SL_TMP, std::max(scan_temp_bytes(nbuckets), scan_temp_bytes(2 * qtot)), &tmp));
-        CK(launch_batch_index(Tp, dpairs, dtpref, titems, npairs, pat, bcnt, nbuckets, boffs,
-                              entries, tmp, c->st));
+        CK(launch_batch_index(Tp, dpairs, dtpref, g.titems, g.npairs, g.pat, b.bcnt, g.nbuckets,
+                              b.boffs, b.entries, b.tmp, st));
     }
-    // hits in one pass: the room for them is the previous batch's count (grown
-    // and the pass repeated when it was too small), and a sort by the whole
-    // hit word restores a fixed order
-    unsigned long long total = 0;
-    uint64_t *ha = nullptr, *hb = nullptr;
-    unsigned long long hitcap = std::max<unsigned long long>(c->batch_hits_hint, 1ull << 20);
-    for (int attempt = 0; attempt < 2; attempt++) {
-        TRY(ensure_t(c, SL_HITS_A, (size_t)hitcap, &ha));
+    {
         Span sp(c, SFE_STAGE_WRITE);
-        CK(launch_batch_hit_emit(Qp, Qm, dpairs, dqpref, qitems, npairs, params->strands, pat,
-                                 params->transition, dbits, boffs, entries, &c->small->split,
-                                 hitcap, ha, c->st));
-        CK(cudaMemcpyAsync(&total, &c->small->split, 8, cudaMemcpyDeviceToHost, c->st));
-        CK(cudaStreamSynchronize(c->st));
-        if (total <= hitcap) break;
-        hitcap = total + total / 8;
+        CK(launch_batch_hit_emit(Qp, Qm, dpairs, dqpref, g.qitems, g.npairs, params->strands, g.pat,
+                                 params->transition, g.dbits, b.boffs, b.entries, &sm->split,
+                                 b.hitcap, b.ha, st));
+        g_launches++;
+        guard_count_kernel<<<1, 1, 0, st>>>(&sm->split, b.hitcap, b.nhits);
+        CK(cudaGetLastError());
     }
-    c->batch_hits_hint = total + total / 16;
-    if (total >= (1ull << 32)) return fail(SFE_EINVAL, "a batch may hold at most 2^32 - 1 hits");
-    const long long nh = (long long)total;
-    TRY(ensure_t(c, SL_HITS_B, (size_t)std::max(1LL, nh), &hb));
-    TRY(ensure(c, SL_TMP, radix_sort_temp_bytes(nh), &tmp));
+    const long long cap = (long long)b.hitcap;
+    uint64_t *ha = b.ha, *hb = b.hb;
     bool in_b = false;
     {
         Span sp(c, SFE_STAGE_SORT);
         // local t, then (pair, strand, diagonal): two stable passes, least significant first
-        CK(radix_sort(ha, hb, nullptr, nullptr, nh, 0, bits_for(maxlen), tmp, &in_b,
-                      &c->small->status, c->st));
+        CK(radix_sort_dev(ha, hb, nullptr, nullptr, cap, b.nhits, 0, bits_for(g.maxlen), b.tmp,
+                          &in_b, &sm->status, st));
         if (in_b) std::swap(ha, hb);
-        CK(radix_sort(ha, hb, nullptr, nullptr, nh, 32, 32 + pbits + 1 + dbits, tmp, &in_b,
-                      &c->small->status, c->st));
+        CK(radix_sort_dev(ha, hb, nullptr, nullptr, cap, b.nhits, 32,
+                          32 + g.pbits + 1 + g.dbits, b.tmp, &in_b, &sm->status, st));
     }
     const uint64_t *sorted = in_b ? hb : ha;
-    BatchHsp *hd = nullptr;
-    unsigned long long hcap = std::max<unsigned long long>(1ull << 16, (unsigned long long)cap);
-    if (c->cap[SL_HSPS] / sizeof(BatchHsp) > hcap) hcap = c->cap[SL_HSPS] / sizeof(BatchHsp);
-    for (int attempt = 0; attempt < 2; attempt++) {
-        TRY(ensure_t(c, SL_HSPS, (size_t)hcap, &hd));
-        CK(cudaMemsetAsync(&c->small->ctr, 0, sizeof(DevCounters), c->st));
-        uint4 *queue = nullptr;
-        const unsigned long long qcap =
-            std::min<unsigned long long>((unsigned long long)std::max(1LL, nh), kQueueMax);
-        TRY(ensure_t(c, SL_QUEUE, (size_t)qcap, &queue));
-        WalkParams wp{};
-        wp.T = Tp;
-        wp.Q = Qp;
-        wp.Qrc = Qm;
-        wp.pairs = dpairs;
-        wp.dbits = dbits;
-        wp.span = pat.span;
-        wp.xdrop = params->xdrop;
-        wp.thresh = params->hsp_thresh;
-        wp.flags = params->flags;
-        wp.lane_cap = params->lane_cap > 0 ? params->lane_cap : kDefaultLaneCap;
-        wp.scores = c->small->scores;
-        wp.bhsps = hd;
-        wp.hsp_cap = hcap;
-        wp.ctr = &c->small->ctr;
-        TRY(walk_tiers(c, sorted, nh, wp, queue, qcap, params));
-        TRY(sync_small(c));
-        if (c->host_small->ctr.hsps <= hcap) break;
-        hcap = c->host_small->ctr.hsps;
+    WalkParams wp{};
+    wp.T = Tp;
+    wp.Q = Qp;
+    wp.Qrc = Qm;
+    wp.pairs = dpairs;
+    wp.dbits = g.dbits;
+    wp.span = g.pat.span;
+    wp.xdrop = params->xdrop;
+    wp.thresh = params->hsp_thresh;
+    wp.flags = params->flags;
+    wp.lane_cap = params->lane_cap > 0 ? params->lane_cap : kDefaultLaneCap;
+    wp.scores = sm->scores;
+    wp.bhsps = b.hsps;
+    wp.hsp_cap = b.hcap;
+    wp.ctr = &sm->ctr;
+    wp.nd = b.nhits;
+    TRY(walk_tiers(c, sorted, cap, wp, b.queue, b.qcap, params, sm, b.sched_tmp));
+    {
+        Span sp(c, SFE_STAGE_OUTPUT);
+        CK(batch_hsp_sort(b.hsps, (long long)b.hcap, &sm->ctr.hsps, g.pbits, bits_for(g.maxlen),
+                          b.tmp, &b.sorted, &sm->status, st));
     }
-    Small sm = *c->host_small;
+    return SFE_OK;
+}
+
+// Upper bound on hits in the first pass: the previous batch's count, or the
+// chance count of the pairs' lengths (about 1.1e-6 per position pair and
+// strand at 41% GC) with room for planted homology.
+unsigned long long batch_hit_guess(const BatchGeom &g, unsigned long long hint) {
+    double chance = 0.0;
+    for (const PairInfo &x : g.P) chance += 2.2e-6 * (double)x.tlen * (double)x.qlen;
+    const unsigned long long est = (unsigned long long)(3.0 * chance) + (1ull << 20);
+    return std::max(hint, est);
+}
+
+// Report of a finished batch: status, stats, HSP count; copies the HSPs out.
+int batch_finish(sfe_ctx *c, const BatchGeom &g, const BatchBufs &b, const Small &sm,
+                 unsigned long long nhits, sfe_batch_hsp *hsps, int64_t cap, int64_t *nhsps,
+                 sfe_stats *stats) {
     TRY(check_status(sm.status | sm.ctr.status));
-    fill_stats(sm, stats, nh, 1);
+    fill_stats(sm, stats, (long long)nhits, 1);
     const unsigned long long found = sm.ctr.hsps;
     *nhsps = (int64_t)found;
-    int r = SFE_OK;
-    if ((long long)found > cap) {
-        r = fail(SFE_EOVERFLOW, "HSP buffer too small");
-    } else if (found > 0) {
-        Span sp(c, SFE_STAGE_OUTPUT);
-        TRY(ensure(c, SL_TMP, batch_hsp_sort_temp_bytes((long long)found), &tmp));
-        CK(batch_hsp_sort(hd, (long long)found, pbits, bits_for(maxlen), tmp, &c->small->status,
-                          c->st));
+    if ((long long)found > cap) return fail(SFE_EOVERFLOW, "HSP buffer too small");
+    if (found > 0) {
         const bool dev_out = is_device_ptr(hsps);
-        CK(cudaMemcpyAsync(hsps, hd, found * sizeof(BatchHsp),
+        CK(cudaMemcpyAsync(hsps, b.sorted, found * sizeof(BatchHsp),
                            dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st));
     }
+    (void)g;
+    return SFE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sfe_run_batch(sfe_ctx *c, const uint8_t *targets, const int64_t *toff, const uint8_t *queries,
+                  const int64_t *qoff, int32_t npairs, const sfe_params *params,
+                  sfe_batch_hsp *hsps, int64_t cap, int64_t *nhsps, sfe_stats *stats) {
+    if (!nhsps) return fail(SFE_EINVAL, "nhsps is NULL");
+    BatchGeom g;
+    TRY(batch_geometry(toff, qoff, npairs, params, g));
+    TRY(begin(c, params->flags));
+    TRY(upload_scores(c, params->scores));
+    BatchBufs b;
+    b.small = c->small;
+    TRY(ensure_t(c, SL_PAIRS, batch_meta_bytes(g), &b.meta));
+    const size_t pbytes = ((size_t)g.npairs * sizeof(PairInfo) + 255) & ~(size_t)255;
+    CK(cudaMemcpyAsync(b.meta, g.P.data(), (size_t)npairs * sizeof(PairInfo),
+                       cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(b.meta + pbytes, g.pref.data(), g.pref.size() * 8, cudaMemcpyHostToDevice,
+                       c->st));
+    {
+        Span sp(c, SFE_STAGE_PACK);
+        const void *tdev = nullptr, *qdev = nullptr;
+        TRY(stage(c, SL_TIN, targets, (size_t)g.ttot, &tdev));
+        TRY(stage(c, SL_QIN, queries, (size_t)g.qtot, &qdev));
+        b.tin = reinterpret_cast<const uint8_t *>(tdev);
+        b.qin = reinterpret_cast<const uint8_t *>(qdev);
+    }
+    TRY(ensure_t(c, SL_TP, packed_words(g.ttot), &b.tp));
+    TRY(ensure_t(c, SL_QP, packed_words(g.qtot), &b.qp));
+    TRY(ensure_t(c, SL_QM, packed_words(g.qtot), &b.qm));
+    TRY(ensure_t(c, SL_BCOUNT, (size_t)g.nbuckets, &b.bcnt));
+    TRY(ensure_t(c, SL_OFFS, (size_t)g.nbuckets + 1, &b.boffs));
+    TRY(ensure_t(c, SL_BENTRIES, (size_t)std::max(1LL, g.ttot), &b.entries));
+    TRY(ensure_t(c, SL_BOUNDS, 1, &b.nhits));
+    unsigned long long hitcap = batch_hit_guess(g, c->batch_hits_hint);
+    unsigned long long hcap = std::max<unsigned long long>(1ull << 16, (unsigned long long)cap);
+    if (c->cap[SL_HSPS] / sizeof(BatchHsp) > hcap) hcap = c->cap[SL_HSPS] / sizeof(BatchHsp);
+    unsigned long long total = 0;
+    for (int attempt = 0; attempt < 3; attempt++) {
+        b.hitcap = hitcap;
+        b.hcap = hcap;
+        b.qcap = std::min<unsigned long long>(hitcap, kQueueMax);
+        TRY(ensure_t(c, SL_HITS_A, (size_t)hitcap, &b.ha));
+        TRY(ensure_t(c, SL_HITS_B, (size_t)hitcap, &b.hb));
+        TRY(ensure_t(c, SL_HSPS, (size_t)hcap, &b.hsps));
+        TRY(ensure_t(c, SL_QUEUE, (size_t)b.qcap, &b.queue));
+        TRY(ensure(c, SL_TMP, batch_tmp_bytes(g, hitcap, hcap), &b.tmp));
+        const uint32_t chunk = params->walk_chunk > 0 ? (uint32_t)params->walk_chunk : 32u;
+        if (params->walk_schedule != SFE_SCHED_NATURAL)
+            TRY(ensure(c, SL_SCHED, walk_schedule_temp_bytes((long long)hitcap, chunk),
+                       &b.sched_tmp));
+        TRY(batch_pipeline(c, g, params, b));
+        TRY(sync_small(c));
+        total = c->host_small->split;
+        const unsigned long long found = c->host_small->ctr.hsps;
+        if (total <= hitcap && found <= hcap) break;
+        if (total > hitcap) hitcap = total + total / 8;
+        if (found > hcap) hcap = found;
+        if (attempt == 2) return fail(SFE_ECUDA, "batch buffers kept overflowing");
+    }
+    c->batch_hits_hint = total + total / 16;
+    if (total >= (1ull << 32)) return fail(SFE_EINVAL, "a batch may hold at most 2^32 - 1 hits");
+    const Small sm = *c->host_small;
+    const int r = batch_finish(c, g, b, sm, total, hsps, cap, nhsps, stats);
     CK(cudaStreamSynchronize(c->st));
     add_timings(c, stats);
+    return r;
+}
+
+}  // extern "C"
+
+// A batch captured once as a CUDA graph and replayed on new sequences of the
+// same lengths. Every buffer the graph touches belongs to the plan.
+struct sfe_batch_plan {
+    sfe_ctx *c = nullptr;
+    BatchGeom g;
+    sfe_params p{};
+    std::string pattern;
+    BatchBufs b;
+    uint8_t *tin = nullptr, *qin = nullptr;
+    std::vector<void *> fixed;  // allocations that do not depend on the capacities
+    std::vector<void *> sized;  // hits, HSPs, queue, scratch
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long launches = 0;  // kernels per replay
+    Small *host_small = nullptr;      // pinned
+};
+
+namespace {
+
+int plan_alloc(std::vector<void *> &list, size_t bytes, void **out) {
+    void *q = nullptr;
+    if (cudaMalloc(&q, std::max<size_t>(bytes, 256)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SFE_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    list.push_back(q);
+    *out = q;
+    return SFE_OK;
+}
+
+template <typename T>
+int plan_alloc_t(std::vector<void *> &list, size_t count, T **out) {
+    void *q = nullptr;
+    TRY(plan_alloc(list, count * sizeof(T), &q));
+    *out = reinterpret_cast<T *>(q);
+    return SFE_OK;
+}
+
+void plan_drop_graph(sfe_batch_plan *pl) {
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    pl->exec = nullptr;
+    pl->graph = nullptr;
+}
+
+void plan_drop_sized(sfe_batch_plan *pl) {
+    for (void *q : pl->sized) cudaFree(q);
+    pl->sized.clear();
+}
+
+// (Re)allocate the capacity-sized buffers and capture the pipeline.
+int plan_capture(sfe_batch_plan *pl, unsigned long long hitcap, unsigned long long hcap) {
+    sfe_ctx *c = pl->c;
+    CK(cudaStreamSynchronize(c->st));
+    plan_drop_graph(pl);
+    plan_drop_sized(pl);
+    BatchBufs &b = pl->b;
+    b.hitcap = hitcap;
+    b.hcap = hcap;
+    b.qcap = std::min<unsigned long long>(hitcap, kQueueMax);
+    TRY(plan_alloc_t(pl->sized, (size_t)hitcap, &b.ha));
+    TRY(plan_alloc_t(pl->sized, (size_t)hitcap, &b.hb));
+    TRY(plan_alloc_t(pl->sized, (size_t)hcap, &b.hsps));
+    TRY(plan_alloc_t(pl->sized, (size_t)b.qcap, &b.queue));
+    TRY(plan_alloc(pl->sized, batch_tmp_bytes(pl->g, hitcap, hcap), &b.tmp));
+    b.sched_tmp = nullptr;
+    if (pl->p.walk_schedule != SFE_SCHED_NATURAL) {
+        const uint32_t chunk = pl->p.walk_chunk > 0 ? (uint32_t)pl->p.walk_chunk : 32u;
+        TRY(plan_alloc(pl->sized, walk_schedule_temp_bytes((long long)hitcap, chunk),
+                       &b.sched_tmp));
+    }
+    c->tm.on = false;  // no event spans inside a graph
+    const unsigned long long l0 = g_launches;
+    CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeRelaxed));
+    const int r = batch_pipeline(c, pl->g, &pl->p, b);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->st, &graph);
+    pl->launches = g_launches - l0;
+    g_launches = l0;  // captured, not launched
+    if (r != SFE_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return r;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SFE_ECUDA, std::string("graph capture failed: ") + cudaGetErrorString(e));
+    }
+    pl->graph = graph;
+    CK(cudaGraphInstantiate(&pl->exec, graph, 0));
+    return SFE_OK;
+}
+
+void plan_release(sfe_batch_plan *pl) {
+    if (!pl) return;
+    if (pl->c) {
+        cudaSetDevice(pl->c->device);
+        cudaStreamSynchronize(pl->c->st);
+    }
+    plan_drop_graph(pl);
+    plan_drop_sized(pl);
+    for (void *q : pl->fixed) cudaFree(q);
+    if (pl->host_small) cudaFreeHost(pl->host_small);
+    delete pl;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sfe_batch_plan_create(sfe_ctx *c, const int64_t *toff, const int64_t *qoff, int32_t npairs,
+                          const sfe_params *params, int64_t hit_cap, sfe_batch_plan **out) {
+    if (!out) return fail(SFE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (hit_cap < 0) return fail(SFE_EINVAL, "hit_cap must be >= 0");
+    BatchGeom g;
+    TRY(batch_geometry(toff, qoff, npairs, params, g));
+    if (params->flags & SFE_TIME_STAGES)
+        return fail(SFE_EINVAL, "SFE_TIME_STAGES is not available in a captured batch");
+    TRY(begin(c));
+    sfe_batch_plan *pl = new sfe_batch_plan;
+    pl->c = c;
+    pl->g = std::move(g);
+    pl->p = *params;
+    pl->pattern = params->seed_pattern ? params->seed_pattern : kDefaultPattern;
+    pl->p.seed_pattern = pl->pattern.c_str();
+    auto bail = [&](int r) {
+        plan_release(pl);
+        return r;
+    };
+    BatchBufs &b = pl->b;
+    const BatchGeom &G = pl->g;
+    int r = SFE_OK;
+    if (cudaMallocHost(&pl->host_small, sizeof(Small)) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(SFE_ENOMEM, "pinned allocation failed"));
+    }
+    if ((r = plan_alloc_t(pl->fixed, 1, &b.small)) != SFE_OK) return bail(r);
+    if ((r = plan_alloc_t(pl->fixed, 1, &b.nhits)) != SFE_OK) return bail(r);
+    if ((r = plan_alloc_t(pl->fixed, batch_meta_bytes(G), &b.meta)) != SFE_OK) return bail(r);
+    if ((r = plan_alloc_t(pl->fixed, (size_t)std::max(1LL, G.ttot), &pl->tin)) != SFE_OK ||
+        (r = plan_alloc_t(pl->fixed, (size_t)std::max(1LL, G.qtot), &pl->qin)) != SFE_OK ||
+        (r = plan_alloc_t(pl->fixed, packed_words(G.ttot), &b.tp)) != SFE_OK ||
+        (r = plan_alloc_t(pl->fixed, packed_words(G.qtot), &b.qp)) != SFE_OK ||
+        (r = plan_alloc_t(pl->fixed, packed_words(G.qtot), &b.qm)) != SFE_OK ||
+        (r = plan_alloc_t(pl->fixed, (size_t)G.nbuckets, &b.bcnt)) != SFE_OK ||
+        (r = plan_alloc_t(pl->fixed, (size_t)G.nbuckets + 1, &b.boffs)) != SFE_OK ||
+        (r = plan_alloc_t(pl->fixed, (size_t)std::max(1LL, G.ttot), &b.entries)) != SFE_OK)
+        return bail(r);
+    b.tin = pl->tin;
+    b.qin = pl->qin;
+    const size_t pbytes = ((size_t)G.npairs * sizeof(PairInfo) + 255) & ~(size_t)255;
+    if (cudaMemsetAsync(b.small, 0, sizeof(Small), c->st) != cudaSuccess ||
+        cudaMemcpyAsync(b.small->scores, params->scores, 64, cudaMemcpyHostToDevice, c->st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(b.meta, G.P.data(), (size_t)G.npairs * sizeof(PairInfo),
+                        cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
+        cudaMemcpyAsync(b.meta + pbytes, G.pref.data(), G.pref.size() * 8, cudaMemcpyHostToDevice,
+                        c->st) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(SFE_ECUDA, "plan set-up copies failed"));
+    }
+    const unsigned long long hitcap =
+        hit_cap > 0 ? (unsigned long long)hit_cap : batch_hit_guess(G, c->batch_hits_hint);
+    if ((r = plan_capture(pl, hitcap, 1ull << 16)) != SFE_OK) return bail(r);
+    *out = pl;
+    return SFE_OK;
+}
+
+void sfe_batch_plan_free(sfe_batch_plan *pl) { plan_release(pl); }
+
+int sfe_batch_plan_run(sfe_batch_plan *pl, const uint8_t *targets, const uint8_t *queries,
+                       sfe_batch_hsp *hsps, int64_t cap, int64_t *nhsps, sfe_stats *stats) {
+    if (!pl || !nhsps) return fail(SFE_EINVAL, "plan or nhsps is NULL");
+    sfe_ctx *c = pl->c;
+    TRY(begin(c));
+    const BatchGeom &G = pl->g;
+    if ((G.ttot > 0 && !targets) || (G.qtot > 0 && !queries))
+        return fail(SFE_EINVAL, "input pointer is NULL");
+    if (G.ttot > 0)
+        CK(cudaMemcpyAsync(pl->tin, targets, (size_t)G.ttot,
+                           is_device_ptr(targets) ? cudaMemcpyDeviceToDevice
+                                                  : cudaMemcpyHostToDevice,
+                           c->st));
+    if (G.qtot > 0)
+        CK(cudaMemcpyAsync(pl->qin, queries, (size_t)G.qtot,
+                           is_device_ptr(queries) ? cudaMemcpyDeviceToDevice
+                                                  : cudaMemcpyHostToDevice,
+                           c->st));
+    unsigned long long total = 0, launches = 0;
+    for (int attempt = 0; attempt < 3; attempt++) {
+        CK(cudaGraphLaunch(pl->exec, c->st));
+        launches += pl->launches;
+        CK(cudaMemcpyAsync(pl->host_small, pl->b.small, sizeof(Small), cudaMemcpyDeviceToHost,
+                           c->st));
+        CK(cudaStreamSynchronize(c->st));
+        total = pl->host_small->split;
+        const unsigned long long found = pl->host_small->ctr.hsps;
+        if (total <= pl->b.hitcap && found <= pl->b.hcap) break;
+        if (attempt == 2) return fail(SFE_ECUDA, "batch buffers kept overflowing");
+        // grow and capture again (the inputs are still in the plan's buffers)
+        TRY(plan_capture(pl, std::max(pl->b.hitcap, total + total / 8),
+                         std::max(pl->b.hcap, found)));
+    }
+    c->batch_hits_hint = total + total / 16;
+    const Small sm = *pl->host_small;
+    const int r = batch_finish(c, G, pl->b, sm, total, hsps, cap, nhsps, stats);
+    CK(cudaStreamSynchronize(c->st));
+    if (stats) stats->launches = (int64_t)launches;
+    g_launches += launches;
     return r;
 }
 

@@ -239,10 +239,15 @@ __global__ void __launch_bounds__(BLOCK) bhits_emit(const uint32_t *__restrict__
 
 // ---------------------------------------------------------------- HSP order
 
-__global__ void bhsp_keys(const BatchHsp *__restrict__ h, long long n, int lbits,
-                          uint64_t *__restrict__ keys, unsigned *__restrict__ idx) {
+__device__ __forceinline__ long long count_of(long long n, const unsigned long long *nd) {
+    return nd ? min(n, (long long)*nd) : n;
+}
+
+__global__ void bhsp_keys(const BatchHsp *__restrict__ h, long long n,
+                          const unsigned long long *nd, int lbits, uint64_t *__restrict__ keys,
+                          unsigned *__restrict__ idx) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= count_of(n, nd)) return;
     const BatchHsp x = h[i];
     keys[i] = ((uint64_t)(uint32_t)x.pair << (2 * lbits + 1)) |
               ((uint64_t)(uint32_t)x.strand << (2 * lbits)) |
@@ -251,9 +256,10 @@ __global__ void bhsp_keys(const BatchHsp *__restrict__ h, long long n, int lbits
 }
 
 __global__ void bhsp_gather(const BatchHsp *__restrict__ h, const unsigned *__restrict__ idx,
-                            long long n, BatchHsp *__restrict__ out) {
+                            long long n, const unsigned long long *nd,
+                            BatchHsp *__restrict__ out) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= count_of(n, nd)) return;
     out[i] = h[idx[i]];
 }
 
@@ -264,8 +270,9 @@ __device__ __forceinline__ bool bhsp_less(const BatchHsp &a, const BatchHsp &b) 
 
 // Runs of equal (pair, strand, tpos, qpos) ordered by (len, score).
 __global__ void bhsp_fix_runs(BatchHsp *__restrict__ h, const uint64_t *__restrict__ keys,
-                              long long n) {
+                              long long n, const unsigned long long *nd) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    n = count_of(n, nd);
     if (i >= n) return;
     if (i > 0 && keys[i - 1] == keys[i]) return;
     long long j = i + 1;
@@ -360,9 +367,11 @@ size_t batch_hsp_sort_temp_bytes(long long n) {
     return (size_t)n * (8 + 8 + 4 + 4 + sizeof(BatchHsp)) + radix_sort_temp_bytes(n) + 1536;
 }
 
-cudaError_t batch_hsp_sort(BatchHsp *h, long long n, int pbits, int lbits, void *tmp,
-                           uint32_t *status, cudaStream_t st) {
-    if (n <= 1) return cudaSuccess;
+cudaError_t batch_hsp_sort(BatchHsp *h, long long n, const unsigned long long *nd, int pbits,
+                           int lbits, void *tmp, BatchHsp **out, uint32_t *status,
+                           cudaStream_t st) {
+    *out = h;
+    if (n <= 0 || (n <= 1 && !nd)) return cudaSuccess;
     char *p = reinterpret_cast<char *>(tmp);
     auto take = [&](size_t bytes) {
         char *r = p;
@@ -376,16 +385,17 @@ cudaError_t batch_hsp_sort(BatchHsp *h, long long n, int pbits, int lbits, void 
     BatchHsp *hb = reinterpret_cast<BatchHsp *>(take((size_t)n * sizeof(BatchHsp)));
     void *rt = take(radix_sort_temp_bytes(n));
     g_launches++;
-    bhsp_keys<<<grid_for(n), BLOCK, 0, st>>>(h, n, lbits, ka, va);
+    bhsp_keys<<<grid_for(n), BLOCK, 0, st>>>(h, n, nd, lbits, ka, va);
     bool in_b = false;
-    cudaError_t e = radix_sort(ka, kb, va, vb, n, 0, pbits + 1 + 2 * lbits, rt, &in_b, status, st);
+    cudaError_t e = radix_sort_dev(ka, kb, va, vb, n, nd, 0, pbits + 1 + 2 * lbits, rt, &in_b,
+                                   status, st);
     if (e != cudaSuccess) return e;
     uint64_t *kf = in_b ? kb : ka;
     unsigned *vf = in_b ? vb : va;
     g_launches += 2;
-    bhsp_gather<<<grid_for(n), BLOCK, 0, st>>>(h, vf, n, hb);
-    bhsp_fix_runs<<<grid_for(n), BLOCK, 0, st>>>(hb, kf, n);
-    cudaMemcpyAsync(h, hb, (size_t)n * sizeof(BatchHsp), cudaMemcpyDeviceToDevice, st);
+    bhsp_gather<<<grid_for(n), BLOCK, 0, st>>>(h, vf, n, nd, hb);
+    bhsp_fix_runs<<<grid_for(n), BLOCK, 0, st>>>(hb, kf, n, nd);
+    *out = hb;
     return cudaGetLastError();
 }
 

@@ -253,7 +253,12 @@ __global__ void __launch_bounds__(MLP_BLOCK) chunk_predict_kernel(
     const int lane = threadIdx.x & 31;
     const long long k = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     if (k >= nchunks) return;
+    if (wp.nd) n = (uint32_t)min((unsigned long long)n, *wp.nd);
     const uint32_t i0 = (uint32_t)k * chunk;
+    if ((unsigned long long)i0 >= n) {  // past a device-side hit count: last
+        if (lane == 0) keys[k] = (0xFFFFFFFFull << 32) | (uint32_t)k;
+        return;
+    }
     const uint32_t len = min(chunk, n - i0);
     float cost = 0.f;
     int used = 0;
@@ -292,7 +297,7 @@ __global__ void __launch_bounds__(MLP_BLOCK) chunk_predict_kernel(
     }
     if (lane == 0) {
         const float work = cost / (float)max(used, 1) * (float)len;
-        const uint32_t qk = (uint32_t)fminf(work * 16.f, 4.0e9f);
+        const uint32_t qk = (uint32_t)fmaxf(1.f, fminf(work * 16.f, 4.0e9f));
         keys[k] = ((uint64_t)(0xFFFFFFFFu - qk) << 32) | (uint32_t)k;
     }
 }

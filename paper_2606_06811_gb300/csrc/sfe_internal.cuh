@@ -117,6 +117,12 @@ size_t radix_sort_temp_bytes(long long n);
 cudaError_t radix_sort(uint64_t *keys_a, uint64_t *keys_b, uint32_t *vals_a, uint32_t *vals_b,
                        long long n, int lo, int hi, void *tmp, bool *result_in_b, uint32_t *status,
                        cudaStream_t st);
+// The same with the key count in device memory (*nd, at most n): the grid is
+// sized for n and each kernel reads the count, so no host synchronisation is
+// needed (the form a captured CUDA graph replays).
+cudaError_t radix_sort_dev(uint64_t *keys_a, uint64_t *keys_b, uint32_t *vals_a, uint32_t *vals_b,
+                           long long n, const unsigned long long *nd, int lo, int hi, void *tmp,
+                           bool *result_in_b, uint32_t *status, cudaStream_t st);
 
 // Exclusive scan of n uint32 into uint64 (out has n + 1 entries: out[n] = total).
 size_t scan_temp_bytes(long long n);
@@ -172,6 +178,9 @@ struct WalkParams {
     unsigned int *queue_take;
     const uint32_t *order;
     uint32_t nchunks, chunk, epoch;
+    // hit count in device memory (at most the launch's n), for launches that
+    // must not wait for the host (graph replay); null: the launch's n
+    const unsigned long long *nd;
     // sampled log of extensions (elog == nullptr: none)
     sfe_ext_record *elog;
     unsigned long long elog_cap;
@@ -274,9 +283,13 @@ cudaError_t launch_batch_hit_emit(const uint32_t *Q, const uint32_t *Qrc, const 
                                   const uint32_t *off, const uint64_t *entries,
                                   unsigned long long *total, unsigned long long cap,
                                   uint64_t *hits, cudaStream_t st);
+// Sort of a batch's HSPs by (pair, strand, tpos, qpos, len, score); n is the
+// count, or with `nd` the capacity and *nd the count. *out receives the
+// sorted array (in tmp, or h itself for n <= 1).
 size_t batch_hsp_sort_temp_bytes(long long n);
-cudaError_t batch_hsp_sort(BatchHsp *h, long long n, int pbits, int lbits, void *tmp,
-                           uint32_t *status, cudaStream_t st);
+cudaError_t batch_hsp_sort(BatchHsp *h, long long n, const unsigned long long *nd, int pbits,
+                           int lbits, void *tmp, BatchHsp **out, uint32_t *status,
+                           cudaStream_t st);
 
 // Conversions between the public hit record and the walk layout.
 cudaError_t launch_hits_to_public(const uint64_t *hits, long long n, int strand, long long qoff,

@@ -52,11 +52,23 @@ RsGeom rs_geom(long long n) {
     return g;
 }
 
+// With a device count `nd`, n is the capacity the grid was sized for and each
+// CTA derives the key count and its chunk from *nd.
+__device__ __forceinline__ void rs_device_count(const unsigned long long *nd, int G, long long &n,
+                                                long long &chunk) {
+    if (!nd) return;
+    n = min(n, (long long)*nd);
+    const long long tiles = (n + RS_TILE - 1) / RS_TILE;
+    chunk = max(1LL, (tiles + G - 1) / G) * RS_TILE;
+}
+
 __global__ void __launch_bounds__(RS_BLOCK) rs_hist(const uint64_t *__restrict__ keys,
-                                                    long long n, int shift, unsigned mask,
-                                                    long long chunk, unsigned *__restrict__ counts,
+                                                    long long n, const unsigned long long *nd,
+                                                    int shift, unsigned mask, long long chunk,
+                                                    unsigned *__restrict__ counts,
                                                     unsigned *__restrict__ totals, int G) {
     __shared__ unsigned h[RS_WARPS][RS_R];
+    rs_device_count(nd, G, n, chunk);
     for (int i = threadIdx.x; i < RS_WARPS * RS_R; i += RS_BLOCK) (&h[0][0])[i] = 0;
     __syncthreads();
     long long beg = (long long)blockIdx.x * chunk;
@@ -143,8 +155,10 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_offsets(unsigned *__restrict__ co
 template <bool VALS>
 __global__ void __launch_bounds__(RS_BLOCK) rs_scatter(
     const uint64_t *__restrict__ kin, uint64_t *__restrict__ kout,
-    const unsigned *__restrict__ vin, unsigned *__restrict__ vout, long long n, int shift,
-    unsigned mask, long long chunk, const unsigned *__restrict__ offsets, int G) {
+    const unsigned *__restrict__ vin, unsigned *__restrict__ vout, long long n,
+    const unsigned long long *nd, int shift, unsigned mask, long long chunk,
+    const unsigned *__restrict__ offsets, int G) {
+    rs_device_count(nd, G, n, chunk);
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *sk = reinterpret_cast<uint64_t *>(smem);                     // RS_TILE
     unsigned *sv = reinterpret_cast<unsigned *>(sk + RS_TILE);              // RS_TILE (VALS)
@@ -368,9 +382,16 @@ size_t radix_sort_temp_bytes(long long n) {
 cudaError_t radix_sort(uint64_t *keys_a, uint64_t *keys_b, uint32_t *vals_a, uint32_t *vals_b,
                        long long n, int lo, int hi, void *tmp, bool *result_in_b, uint32_t *status,
                        cudaStream_t st) {
+    return radix_sort_dev(keys_a, keys_b, vals_a, vals_b, n, nullptr, lo, hi, tmp, result_in_b,
+                          status, st);
+}
+
+cudaError_t radix_sort_dev(uint64_t *keys_a, uint64_t *keys_b, uint32_t *vals_a, uint32_t *vals_b,
+                           long long n, const unsigned long long *nd, int lo, int hi, void *tmp,
+                           bool *result_in_b, uint32_t *status, cudaStream_t st) {
     (void)status;  // no device-side waits in this sort
     *result_in_b = false;
-    if (n <= 1 || hi <= lo) return cudaSuccess;
+    if (hi <= lo || n <= 0 || (n <= 1 && !nd)) return cudaSuccess;
     if (n >= (1LL << 32)) return cudaErrorInvalidValue;
     RsGeom g = rs_geom(n);
     unsigned *counts = reinterpret_cast<unsigned *>(tmp);
@@ -398,16 +419,17 @@ cudaError_t radix_sort(uint64_t *keys_a, uint64_t *keys_b, uint32_t *vals_a, uin
     for (int shift = lo; shift < hi; shift += per) {
         int bits = min(per, hi - shift);
         unsigned mask = (1u << bits) - 1u;
-        cudaMemsetAsync(totals, 0, RS_R * 4, st);
+        cudaError_t me = cudaMemsetAsync(totals, 0, RS_R * 4, st);
+        if (me != cudaSuccess) return me;
         g_launches += 3;
-        rs_hist<<<g.G, RS_BLOCK, 0, st>>>(kin, n, shift, mask, g.chunk, counts, totals, g.G);
+        rs_hist<<<g.G, RS_BLOCK, 0, st>>>(kin, n, nd, shift, mask, g.chunk, counts, totals, g.G);
         rs_offsets<<<RS_R, RS_BLOCK, 0, st>>>(counts, totals, g.G);
         if (vals)
-            rs_scatter<true><<<g.G, RS_BLOCK, smem, st>>>(kin, kout, vin, vout, n, shift, mask,
-                                                          g.chunk, counts, g.G);
+            rs_scatter<true><<<g.G, RS_BLOCK, smem, st>>>(kin, kout, vin, vout, n, nd, shift,
+                                                          mask, g.chunk, counts, g.G);
         else
-            rs_scatter<false><<<g.G, RS_BLOCK, smem, st>>>(kin, kout, nullptr, nullptr, n, shift,
-                                                           mask, g.chunk, counts, g.G);
+            rs_scatter<false><<<g.G, RS_BLOCK, smem, st>>>(kin, kout, nullptr, nullptr, n, nd,
+                                                           shift, mask, g.chunk, counts, g.G);
         uint64_t *tk = kin;
         kin = kout;
         kout = tk;

@@ -302,6 +302,15 @@ __global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__r
     }
     __syncthreads();
     const int span = wp.span, X = wp.xdrop;
+    uint32_t nchunks = wp.nchunks;
+    if (wp.nd) {  // the hit count lives on the device: ranges and chunks follow it
+        n = (uint32_t)min((unsigned long long)n, *wp.nd);
+        if (PERSIST)
+            nchunks = (n + wp.chunk - 1) / wp.chunk;
+        else
+            chunk = max(16u, (uint32_t)((n + (unsigned long long)gridDim.x * blockDim.x - 1) /
+                                        ((unsigned long long)gridDim.x * blockDim.x)));
+    }
     // upper bound of a seed span's score: the span is scored only for hits
     // whose extensions could lift the HSP to the threshold
     int maxsc = lut[0];
@@ -339,7 +348,7 @@ __global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__r
                     if (PERSIST) {
                         // take the next chunk of hits from the work counter
                         const uint32_t w = atomicAdd(wp.work_next, 1u);
-                        if (w >= wp.nchunks) {
+                        if (w >= nchunks) {
                             done = true;
                         } else {
                             const uint32_t ck = wp.order ? wp.order[w] : w;
@@ -609,6 +618,7 @@ __global__ void __launch_bounds__(W_BLOCK) walk_warps_kernel(const uint64_t *__r
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const unsigned long long nq = min((unsigned long long)*wp.queue_len, wp.queue_cap);
+    if (wp.nd) nhits = (uint32_t)min((unsigned long long)nhits, *wp.nd);
     unsigned long long ext = 0, cells = 0, tasks = 0;
     uint32_t status = 0;
     for (long long e = warp; e < (long long)nq; e += nwarps) {
@@ -683,16 +693,25 @@ cudaError_t launch_walk_warps(const uint64_t *hits, long long n, WalkParams wp, 
 
 // Sort key of each work chunk for the largest-first schedule: the number of
 // hits of the diagonal its first hit lies on (descending), then chunk index.
-__global__ void chunk_keys_kernel(const uint64_t *__restrict__ hits, uint32_t n, uint32_t chunk,
-                                  uint32_t nchunks, int random, uint64_t *__restrict__ keys) {
+// Keys of the chunk schedules (sorted ascending by their high word). Chunks
+// past a device-side hit count (nd) get the largest key, so the ones that
+// exist come first.
+__global__ void chunk_keys_kernel(const uint64_t *__restrict__ hits, uint32_t n,
+                                  const unsigned long long *nd, uint32_t chunk, uint32_t nchunks,
+                                  int random, uint64_t *__restrict__ keys) {
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nchunks) return;
+    if (nd) n = (uint32_t)min((unsigned long long)n, *nd);
+    if ((unsigned long long)k * chunk >= n) {
+        keys[k] = (0xFFFFFFFFull << 32) | k;
+        return;
+    }
     if (random) {  // a fixed pseudo-random order (splitmix64 finaliser of k)
         unsigned long long z = 0x9E3779B97F4A7C15ull * (unsigned long long)(k + 1);
         z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
         z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
         z ^= z >> 31;
-        keys[k] = (z & 0xFFFFFFFF00000000ull) | k;
+        keys[k] = (z & 0x7FFFFFFF00000000ull) | k;
         return;
     }
     const uint32_t i = k * chunk;
@@ -765,7 +784,7 @@ cudaError_t launch_walk_schedule(const uint64_t *hits, long long n, const WalkPa
     } else {
         g_launches++;
         chunk_keys_kernel<<<grid_for(nchunks), BLOCK, 0, st>>>(
-            hits, (uint32_t)n, chunk, nchunks, schedule == SFE_SCHED_RANDOM ? 1 : 0, ka);
+            hits, (uint32_t)n, wp.nd, chunk, nchunks, schedule == SFE_SCHED_RANDOM ? 1 : 0, ka);
     }
     bool in_b = false;
     cudaError_t e = radix_sort(ka, kb, nullptr, nullptr, nchunks, 32, 64, rt, &in_b, status, st);

@@ -95,6 +95,11 @@ def lib() -> C.CDLL:
                               C.POINTER(Stats)]
         L.sfe_run_batch.argtypes = [vp, vp, vp, vp, vp, i32, C.POINTER(Params), vp, i64,
                                     C.POINTER(i64), C.POINTER(Stats)]
+        L.sfe_batch_plan_create.argtypes = [vp, vp, vp, i32, C.POINTER(Params), i64,
+                                            C.POINTER(vp)]
+        L.sfe_batch_plan_run.argtypes = [vp, vp, vp, vp, i64, C.POINTER(i64), C.POINTER(Stats)]
+        L.sfe_batch_plan_free.argtypes = [vp]
+        L.sfe_batch_plan_free.restype = None
         L.sfe_mlp_param_count.argtypes = []
         L.sfe_mlp_param_count.restype = i32
         L.sfe_mlp_model_bytes.argtypes = []
@@ -112,7 +117,8 @@ def lib() -> C.CDLL:
         for f in ("sfe_params_default", "sfe_ctx_create", "sfe_ctx_set_stream", "sfe_index_build",
                   "sfe_seed_hits", "sfe_ungapped_xdrop", "sfe_run", "sfe_run_batch",
                   "sfe_mlp_init", "sfe_mlp_pack", "sfe_mlp_data_create", "sfe_mlp_loss_grad",
-                  "sfe_mlp_predict", "sfe_mlp_train"):
+                  "sfe_mlp_predict", "sfe_mlp_train", "sfe_batch_plan_create",
+                  "sfe_batch_plan_run"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -289,6 +295,18 @@ class Context:
             _check(code)
             return buf[: nout.value], st.as_dict()
 
+    def batch_plan(self, toff, qoff, params: Params | None = None,
+                   hit_cap: int = 0) -> "BatchPlan":
+        """A batch of fixed pair lengths captured as a CUDA graph (sfe_batch_plan_create)."""
+        p = params or default_params()
+        to = np.ascontiguousarray(toff, dtype=np.int64)
+        qo = np.ascontiguousarray(qoff, dtype=np.int64)
+        h = C.c_void_p()
+        _check(lib().sfe_batch_plan_create(self.h, to.ctypes.data, qo.ctypes.data,
+                                           int(to.size - 1), C.byref(p), int(hit_cap),
+                                           C.byref(h)))
+        return BatchPlan(h, p)
+
     # ------------------------------------------------ work predictor (MLP)
 
     def mlp_init(self, params, seed: int) -> None:
@@ -369,6 +387,49 @@ class Index:
     def close(self) -> None:
         if getattr(self, "h", None):
             lib().sfe_index_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchPlan:
+    """A captured batch (owned device memory and CUDA graph); run() replays it."""
+
+    def __init__(self, h, params):
+        self.h = h
+        self._params = params  # pointers in it were captured
+
+    def run(self, targets, queries, cap: int | None = None, out=None):
+        """Replay on new sequences of the plan's lengths. Returns (HSPs as numpy
+        BATCH_HSP_DTYPE, stats), or the first rows of `out` (int32, shape (cap, 6))."""
+        tptr, _, tkeep = _buf(targets)
+        qptr, _, qkeep = _buf(queries)
+        nout = C.c_int64(0)
+        st = Stats()
+        if out is not None:
+            optr, on, _ = _buf(out)
+            _check(lib().sfe_batch_plan_run(self.h, tptr, qptr, optr,
+                                            on // BATCH_HSP_DTYPE.itemsize, C.byref(nout),
+                                            C.byref(st)))
+            return out[: nout.value], st.as_dict()
+        cap = 1 << 16 if cap is None else int(cap)
+        while True:
+            buf = np.zeros(max(cap, 1), dtype=BATCH_HSP_DTYPE)
+            code = lib().sfe_batch_plan_run(self.h, tptr, qptr, buf.ctypes.data, cap,
+                                            C.byref(nout), C.byref(st))
+            if code == EOVERFLOW and nout.value > cap:
+                cap = int(nout.value)
+                continue
+            _check(code)
+            return buf[: nout.value], st.as_dict()
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            lib().sfe_batch_plan_free(self.h)
             self.h = None
 
     def __del__(self):

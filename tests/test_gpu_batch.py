@@ -80,3 +80,50 @@ def test_batch_single_strand_and_lane_cap(pkg):
 def test_batch_walk_modes(pkg, mode, sched, chunk):
     pairs = synth.batch_pairs(seed=6, n_pairs=64, len_lo=1000, len_hi=30_000)
     check(pkg, pairs, walk_mode=mode, walk_schedule=sched, walk_chunk=chunk, lane_cap=32)
+
+
+def _variant(pairs):
+    """Pairs of the same lengths with other content: reverse-complemented
+    targets and reversed queries."""
+    out = []
+    for p in pairs:
+        T = (3 - p.T[::-1]).astype(np.uint8)
+        Q = np.ascontiguousarray(p.Q[::-1]).astype(np.uint8)
+        out.append(synth.Pair(T, Q, [], p.name + "'", p.gc))
+    return out
+
+
+@pytest.mark.parametrize("kw", [{}, {"walk_mode": 1, "walk_chunk": 8},
+                                {"walk_mode": 1, "walk_schedule": 3, "walk_chunk": 16}],
+                         ids=["two-launch", "persistent", "persistent-random"])
+def test_batch_plan_replays_a_captured_graph(pkg, kw):
+    pairs = synth.batch_pairs(seed=12, n_pairs=48, len_lo=1000, len_hi=30_000)
+    T, toff, Q, qoff = concat_batch(pairs)
+    H, hits, ext, cells = oracle_batch(pairs)
+    with pkg.Context(0) as ctx:
+        # a hit capacity far too small: the first run grows the plan and captures again
+        plan = ctx.batch_plan(toff, qoff, pkg.default_params(input_codes=1, **kw), hit_cap=1000)
+        for _ in range(2):
+            h, st = plan.run(T, Q)
+            G = np.ascontiguousarray(h).view(np.int32).reshape(-1, 6)
+            assert np.array_equal(G, H)
+            assert (st["hits"], st["extended"], st["cells"]) == (hits, ext, cells)
+            assert st["launches"] > 10
+        # new sequences of the same lengths, through the same graph
+        other = _variant(pairs)
+        T2, toff2, Q2, qoff2 = concat_batch(other)
+        assert np.array_equal(toff2, toff) and np.array_equal(qoff2, qoff)
+        H2, hits2, _, cells2 = oracle_batch(other)
+        h, st = plan.run(T2, Q2)
+        G2 = np.ascontiguousarray(h).view(np.int32).reshape(-1, 6)
+        assert np.array_equal(G2, H2)
+        assert (st["hits"], st["cells"]) == (hits2, cells2)
+        plan.close()
+
+
+def test_batch_plan_rejects_stage_timing_and_bad_offsets(pkg):
+    with pkg.Context(0) as ctx:
+        with pytest.raises(pkg.SfeError):
+            ctx.batch_plan([0, 100], [0, 100], pkg.default_params(flags=pkg.TIME_STAGES))
+        with pytest.raises(pkg.SfeError):
+            ctx.batch_plan([0, 100, 50], [0, 10, 20], pkg.default_params())
