@@ -64,6 +64,12 @@ def args_parse():
     ap.add_argument("--log-every", type=int, default=20,
                     help="extension log sampling of the training run (1 in N)")
     ap.add_argument("--learned-chunk", type=int, default=128)
+    ap.add_argument("--workload", default="plain_pair_10mb",
+                    choices=["plain_pair_10mb", "batch_pairs"],
+                    help="batch_pairs: 4096 uneven pairs, eager and as a replayed CUDA graph "
+                         "(a separate line, not the headline)")
+    ap.add_argument("--pairs", type=int, default=4096)
+    ap.add_argument("--no-tune", action="store_true", help="batch: skip the autotuner")
     return ap.parse_args()
 
 
@@ -452,11 +458,116 @@ def run_sfe(a, rank, world, local):
     return 0
 
 
+def run_batch_bench(a, rank, world, local):
+    """The batch of uneven pairs: autotuned walk parameters, then eager calls
+    (sfe_run_batch) and replays of the captured graph (sfe_batch_plan_run)."""
+    import torch
+    import synth
+    from synth.workloads import concat_batch
+    import paper_2606_06811_gb300 as pkg
+    from paper_2606_06811_gb300 import autotune
+    from paper_2606_06811_gb300 import build as cuda_build
+
+    cuda_build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    t0 = time.perf_counter()
+    pairs = synth.batch_pairs(seed=3, n_pairs=a.pairs)
+    Tc, toff, Qc, qoff = concat_batch(pairs)
+    gen_s = time.perf_counter() - t0
+    T = torch.from_numpy(np.frombuffer(synth.decode(Tc), np.uint8).copy()).to(dev)
+    Q = torch.from_numpy(np.frombuffer(synth.decode(Qc), np.uint8).copy()).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = pkg.Context(local, stream=stream)
+    cap = 1 << 22
+    out = torch.zeros((cap, 6), dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    base = pkg.default_params()
+    tuned, table = {}, []
+    if not a.no_tune:
+        def trial(c):
+            h, st = ctx.run_batch(T, toff, Q, qoff, pkg.default_params(**c), out=out)
+            return h.cpu().numpy().tobytes(), st
+        with torch.cuda.stream(stream):
+            tuned, table = autotune.tune(trial, autotune.batch_signature(toff, qoff, base),
+                                         stream=stream)
+    params = pkg.default_params(**tuned)
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h, st = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), st, h
+
+    eager = lambda: ctx.run_batch(T, toff, Q, qoff, params, out=out)  # noqa: E731
+    plan = ctx.batch_plan(toff, qoff, params)
+    pout = torch.zeros_like(out)
+    replay = lambda: plan.run(T, Q, out=pout)  # noqa: E731
+    for _ in range(a.warmup):
+        timed(eager)
+        timed(replay)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    res = {"eager": [], "graph": []}
+    last = {}
+    for _ in range(a.steps):
+        for name, fn in (("eager", eager), ("graph", replay)):
+            ms, st, h = timed(fn)
+            res[name].append((ms, st))
+            last[name] = h
+    clk = clocks.stop()
+    same = bool(torch.equal(last["eager"], last["graph"]))
+    st_t = ctx.run_batch(T, toff, Q, qoff, pkg.default_params(flags=pkg.TIME_STAGES, **tuned),
+                         out=out)[1]
+
+    def summary(rows):
+        ms = sum(r[0] for r in rows)
+        cells = sum(r[1]["cells"] for r in rows)
+        return {"value": cells / (ms / 1e3) / 1e9, "unit": "GCUPS",
+                "ms_per_step": ms / len(rows),
+                "hsps_per_s": rows[0][1]["hsps"] * len(rows) / (ms / 1e3),
+                "launches_per_step": rows[0][1]["launches"]}
+
+    g = summary(res["graph"])
+    s0 = res["graph"][0][1]
+    line = {
+        "metric": METRIC, "value": g["value"], "unit": "GCUPS", "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": g["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": "batch_pairs", "pairs": a.pairs, "seed": 3,
+                   "tbases": int(toff[-1]), "qbases": int(qoff[-1]),
+                   "path": "sfe_batch_plan_run (captured CUDA graph)", "walk": tuned or "defaults",
+                   "l2": "256 MiB write between steps, outside the per-step events"},
+        "per_step": {"cells": s0["cells"], "hits": s0["hits"], "extended": s0["extended"],
+                     "hsps": s0["hsps"]},
+        "eager": summary(res["eager"]),
+        "graph_equals_eager": same,
+        "stage_ms_eager": {k: round(v, 4) for k, v in st_t["stage_ms"].items()},
+        "autotune": [{"params": p, "ms": round(m, 3)} for p, m in table],
+        "gpu_launches": int(sum(r[1]["launches"] for r in res["graph"])),
+        "clocks": clk, "generate_s": round(gen_s, 2),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    ctx.close()
+    return 0
+
+
 def main():
     a = args_parse()
     rank, world, local = dist_env()
     if a.impl == "reference":
         return run_reference(a, rank, world)
+    if a.workload == "batch_pairs":
+        return run_batch_bench(a, rank, world, local)
     return run_sfe(a, rank, world, local)
 
 

@@ -45,11 +45,15 @@ const char *kDefaultPattern = "1110100110010101111";
 constexpr int kDefaultLaneCap = 256;
 constexpr long long kDefaultTileHits = 1LL << 28;
 constexpr unsigned long long kQueueMax = 1ull << 20;
+// A batch pair's split-key tables have about npos / 2 buckets each (1 to 2
+// entries per bucket: measured on 4096 pairs, 20.6 ms per batch against 21.2
+// with one bucket per position and 21.2 / 23.8 with 4 / 8 per bucket).
+constexpr int kBatchBucketShift = 1;
 
 enum Slot {
     SL_TIN, SL_QIN, SL_TP, SL_QP, SL_QM, SL_KEYS_A, SL_KEYS_B, SL_BCOUNT, SL_OFFS, SL_POS,
     SL_COUNTS, SL_STARTS, SL_HITS_A, SL_HITS_B, SL_QUEUE, SL_PAIRS, SL_BENTRIES, SL_SCHED,
-    SL_HSPS, SL_TMP, SL_ECARRY, SL_PUB, SL_BOUNDS, NSLOT
+    SL_HSPS, SL_TMP, SL_ECARRY, SL_PUB, SL_BOUNDS, SL_BSLOTS, NSLOT
 };
 
 // Small device block: scores, counters and flags of one call.
@@ -951,6 +955,7 @@ struct BatchBufs {
     uint32_t *tp = nullptr, *qp = nullptr, *qm = nullptr;  // packed (padded allocations)
     uint32_t *bcnt = nullptr, *boffs = nullptr;
     uint64_t *entries = nullptr;
+    uint2 *slots = nullptr;  // index build scratch, one per target base
     uint64_t *ha = nullptr, *hb = nullptr;
     unsigned long long hitcap = 0;
     BatchHsp *hsps = nullptr;
@@ -993,7 +998,7 @@ int batch_geometry(const int64_t *toff, const int64_t *qoff, int npairs, const s
     if (g.pbits + 1 + g.dbits > 32) return fail(SFE_EINVAL, "too many pairs for their lengths");
     g.P.assign(npairs, PairInfo{});
     g.nbuckets = 0;
-    const int kbits = 2 * g.pat.weight;
+    const int kbits = batch_table_bits(g.pat.weight);
     for (int p = 0; p < npairs; p++) {
         PairInfo &x = g.P[p];
         x.toff = toff[p];
@@ -1002,7 +1007,7 @@ int batch_geometry(const int64_t *toff, const int64_t *qoff, int npairs, const s
         x.tlen = (int)(toff[p + 1] - toff[p]);
         x.qlen = (int)(qoff[p + 1] - qoff[p]);
         const long long npos = std::max(1LL, (long long)x.tlen - g.pat.span + 1);
-        x.bbits = std::min(kbits, std::max(4, bits_for(npos - 1)));
+        x.bbits = std::min(kbits, std::max(4, bits_for(npos - 1) - kBatchBucketShift));
         x.boff = g.nbuckets;
         x.pad = 0;
         g.nbuckets += 1LL << x.bbits;
@@ -1030,7 +1035,7 @@ size_t batch_meta_bytes(const BatchGeom &g) {
 
 // Scratch shared by the scans and the sorts of a batch.
 size_t batch_tmp_bytes(const BatchGeom &g, unsigned long long hitcap, unsigned long long hcap) {
-    size_t t = std::max(scan_temp_bytes(g.nbuckets), scan_temp_bytes(2 * g.qtot));
+    size_t t = std::max(scan_temp_bytes(2 * g.nbuckets), scan_temp_bytes(2 * g.qtot));
     t = std::max(t, radix_sort_temp_bytes((long long)hitcap));
     return std::max(t, batch_hsp_sort_temp_bytes((long long)hcap));
 }
@@ -1064,13 +1069,13 @@ int batch_pipeline(sfe_ctx *c, const BatchGeom &g, const sfe_params *params, Bat
     {
         Span sp(c, SFE_STAGE_INDEX);
         CK(launch_batch_index(Tp, dpairs, dtpref, g.titems, g.npairs, g.pat, b.bcnt, g.nbuckets,
-                              b.boffs, b.entries, b.tmp, st));
+                              b.boffs, b.entries, b.slots, b.tmp, st));
     }
     {
         Span sp(c, SFE_STAGE_WRITE);
         CK(launch_batch_hit_emit(Qp, Qm, dpairs, dqpref, g.qitems, g.npairs, params->strands, g.pat,
-                                 params->transition, g.dbits, b.boffs, b.entries, &sm->split,
-                                 b.hitcap, b.ha, st));
+                                 params->transition, g.dbits, g.nbuckets, b.boffs, b.entries,
+                                 &sm->split, b.hitcap, b.ha, st));
         g_launches++;
         guard_count_kernel<<<1, 1, 0, st>>>(&sm->split, b.hitcap, b.nhits);
         CK(cudaGetLastError());
@@ -1172,9 +1177,10 @@ int sfe_run_batch(sfe_ctx *c, const uint8_t *targets, const int64_t *toff, const
     TRY(ensure_t(c, SL_TP, packed_words(g.ttot), &b.tp));
     TRY(ensure_t(c, SL_QP, packed_words(g.qtot), &b.qp));
     TRY(ensure_t(c, SL_QM, packed_words(g.qtot), &b.qm));
-    TRY(ensure_t(c, SL_BCOUNT, (size_t)g.nbuckets, &b.bcnt));
-    TRY(ensure_t(c, SL_OFFS, (size_t)g.nbuckets + 1, &b.boffs));
-    TRY(ensure_t(c, SL_BENTRIES, (size_t)std::max(1LL, g.ttot), &b.entries));
+    TRY(ensure_t(c, SL_BCOUNT, 2 * (size_t)g.nbuckets, &b.bcnt));
+    TRY(ensure_t(c, SL_OFFS, 2 * (size_t)g.nbuckets + 1, &b.boffs));
+    TRY(ensure_t(c, SL_BENTRIES, 2 * (size_t)std::max(1LL, g.ttot), &b.entries));
+    TRY(ensure_t(c, SL_BSLOTS, (size_t)std::max(1LL, g.ttot), &b.slots));
     TRY(ensure_t(c, SL_BOUNDS, 1, &b.nhits));
     unsigned long long hitcap = batch_hit_guess(g, c->batch_hits_hint);
     unsigned long long hcap = std::max<unsigned long long>(1ull << 16, (unsigned long long)cap);
@@ -1358,9 +1364,10 @@ int sfe_batch_plan_create(sfe_ctx *c, const int64_t *toff, const int64_t *qoff, 
         (r = plan_alloc_t(pl->fixed, packed_words(G.ttot), &b.tp)) != SFE_OK ||
         (r = plan_alloc_t(pl->fixed, packed_words(G.qtot), &b.qp)) != SFE_OK ||
         (r = plan_alloc_t(pl->fixed, packed_words(G.qtot), &b.qm)) != SFE_OK ||
-        (r = plan_alloc_t(pl->fixed, (size_t)G.nbuckets, &b.bcnt)) != SFE_OK ||
-        (r = plan_alloc_t(pl->fixed, (size_t)G.nbuckets + 1, &b.boffs)) != SFE_OK ||
-        (r = plan_alloc_t(pl->fixed, (size_t)std::max(1LL, G.ttot), &b.entries)) != SFE_OK)
+        (r = plan_alloc_t(pl->fixed, 2 * (size_t)G.nbuckets, &b.bcnt)) != SFE_OK ||
+        (r = plan_alloc_t(pl->fixed, 2 * (size_t)G.nbuckets + 1, &b.boffs)) != SFE_OK ||
+        (r = plan_alloc_t(pl->fixed, 2 * (size_t)std::max(1LL, G.ttot), &b.entries)) != SFE_OK ||
+        (r = plan_alloc_t(pl->fixed, (size_t)std::max(1LL, G.ttot), &b.slots)) != SFE_OK)
         return bail(r);
     b.tin = pl->tin;
     b.qin = pl->qin;

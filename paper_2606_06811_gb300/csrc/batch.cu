@@ -1,19 +1,30 @@
 // Seeding and HSP ordering for a batch of target/query pairs.
 //
-// Every pair has its own seeding index, so no hit ever joins two pairs. A pair
-// with n seed positions gets 2^b buckets, b = ceil(log2 n) clamped to
-// [4, 2 * weight], addressed by the top b bits of the seed key; the buckets of
-// all pairs sit back to back in one CSR table. Entries keep their full key, so
-// a probe scans its bucket (on average under one entry) and keeps the entries
-// whose key is equal. The table is filled by a counting sort (counts, one
-// exclusive scan over all pairs' buckets, atomic placement): the order of the
-// entries inside a bucket is not fixed, and it need not be, because hits of
-// one query position lie on different diagonals and the diagonal grouping that
-// follows only relies on query order within a diagonal.
+// Every pair has its own seeding index, so no hit ever joins two pairs.
+//
+// Two probes per query position instead of 1 + weight. A hit allows at most
+// one transition among the care positions, and a transition keeps a base's
+// purine/pyrimidine class (the low bit of the 2-bit code), so split the care
+// positions into a first half A and a second half B: a hit has A exact, or B
+// exact with the transition in A. Table 1 is keyed by (A's bases, B's
+// classes), table 2 by (B's bases, A's classes). A probe of table 1 keeps the
+// entries with A exact, all classes equal and at most one transition in B; a
+// probe of table 2 keeps those with B exact, all classes equal and exactly one
+// transition in A. Each hit is found once. Without transitions only table 1
+// is probed, for exact keys.
+//
+// A pair with n seed positions gets 2^b buckets per table, b = ceil(log2 n)
+// clamped to [4, table key bits], addressed by the top b bits of the table
+// key; the buckets of all pairs sit back to back, table 2's after table 1's,
+// in one CSR. Entries keep their full seed key and are checked against the
+// probe's. The tables are filled by a counting sort (counts whose atomics also
+// give each entry its place in its bucket, one exclusive scan over all
+// buckets, then placement without atomics): the order inside a bucket is not
+// fixed, and it need not be, because the hits are sorted by their whole word
+// before the walk.
 //
 // Hit words: pair << (dbits + 1) | strand << dbits | local diagonal in the
-// high half, local t in the low half, written in query order per (pair,
-// strand) so a stable sort on the high half groups each diagonal in t order.
+// high half, local t in the low half.
 #include "sfe_internal.cuh"
 
 namespace sfe {
@@ -21,6 +32,45 @@ namespace sfe {
 namespace {
 
 constexpr int MAX_PROBES = MAX_WEIGHT + 1;
+
+// Halves of the care positions: A = the first weight / 2 (the key's high
+// groups), B = the rest (its low groups). Table keys are left-aligned to
+// split_bits() bits.
+struct Split {
+    int hA, hB, ik;          // sizes, table key width
+    uint32_t maskB;          // B's groups in a seed key
+    uint32_t low, highA, highB;  // class bits; transition bits of A and of B
+};
+
+__host__ __device__ __forceinline__ Split split_of(int weight) {
+    Split q;
+    q.hA = weight / 2;
+    q.hB = weight - q.hA;
+    q.ik = 2 * q.hB + q.hA;  // the wider of 2hA + hB and 2hB + hA
+    q.maskB = (1u << (2 * q.hB)) - 1u;
+    const uint32_t all = (weight >= 16) ? 0xFFFFFFFFu : ((1u << (2 * weight)) - 1u);
+    q.low = 0x55555555u & all;
+    q.highB = 0xAAAAAAAAu & q.maskB;
+    q.highA = 0xAAAAAAAAu & all & ~q.maskB;
+    return q;
+}
+
+// The class bits (low bit of each 2-bit group) of the n <= 8 groups of x, packed.
+__device__ __forceinline__ uint32_t classes(uint32_t x) {
+    x &= 0x5555u;
+    x = (x | (x >> 1)) & 0x3333u;
+    x = (x | (x >> 2)) & 0x0F0Fu;
+    return (x | (x >> 4)) & 0x00FFu;
+}
+
+__device__ __forceinline__ uint32_t table1_key(uint32_t k, const Split &q) {
+    const uint32_t key = ((k >> (2 * q.hB)) << q.hB) | classes(k & q.maskB);
+    return key << (q.ik - (2 * q.hA + q.hB));
+}
+
+__device__ __forceinline__ uint32_t table2_key(uint32_t k, const Split &q) {
+    return ((k & q.maskB) << q.hA) | classes(k >> (2 * q.hB));
+}
 
 __device__ __forceinline__ uint32_t spaced_key(const uint32_t *__restrict__ S, long long p,
                                                const SeedPattern &pat) {
@@ -52,16 +102,20 @@ __device__ __forceinline__ int item_pair(const long long *__restrict__ prefix, i
 __global__ void __launch_bounds__(BLOCK) bidx_count(const uint32_t *__restrict__ T,
                                                     const PairInfo *__restrict__ pairs,
                                                     const long long *__restrict__ tprefix,
-                                                    int npairs, SeedPattern pat,
-                                                    uint32_t *__restrict__ cnt) {
+                                                    int npairs, SeedPattern pat, long long nb,
+                                                    uint32_t *__restrict__ cnt,
+                                                    uint2 *__restrict__ slots) {
     const int p = item_pair(tprefix, npairs, blockIdx.x);
     const PairInfo P = pairs[p];
     const long long npos = (long long)P.tlen - pat.span + 1;
     const long long i0 = (blockIdx.x - tprefix[p]) * (long long)ITEM;
-    const int kbits = 2 * pat.weight;
+    const Split q = split_of(pat.weight);
     for (long long i = i0 + threadIdx.x; i < min(npos, i0 + ITEM); i += BLOCK) {
         const uint32_t k = spaced_key(T, P.toff + i, pat);
-        atomicAdd(cnt + P.boff + (k >> (kbits - P.bbits)), 1u);
+        uint2 sl;
+        sl.x = atomicAdd(cnt + P.boff + (table1_key(k, q) >> (q.ik - P.bbits)), 1u);
+        sl.y = atomicAdd(cnt + nb + P.boff + (table2_key(k, q) >> (q.ik - P.bbits)), 1u);
+        slots[P.toff + i] = sl;  // the entry's place in each bucket, used by the fill
     }
 }
 
@@ -69,59 +123,67 @@ __global__ void __launch_bounds__(BLOCK) bidx_count(const uint32_t *__restrict__
 __global__ void __launch_bounds__(BLOCK) bidx_fill(const uint32_t *__restrict__ T,
                                                    const PairInfo *__restrict__ pairs,
                                                    const long long *__restrict__ tprefix,
-                                                   int npairs, SeedPattern pat,
+                                                   int npairs, SeedPattern pat, long long nb,
                                                    const uint32_t *__restrict__ off,
-                                                   uint32_t *__restrict__ cursor,
+                                                   const uint2 *__restrict__ slots,
                                                    uint64_t *__restrict__ entries) {
     const int p = item_pair(tprefix, npairs, blockIdx.x);
     const PairInfo P = pairs[p];
     const long long npos = (long long)P.tlen - pat.span + 1;
     const long long i0 = (blockIdx.x - tprefix[p]) * (long long)ITEM;
-    const int kbits = 2 * pat.weight;
+    const Split q = split_of(pat.weight);
     for (long long i = i0 + threadIdx.x; i < min(npos, i0 + ITEM); i += BLOCK) {
         const uint32_t k = spaced_key(T, P.toff + i, pat);
-        const long long b = P.boff + (k >> (kbits - P.bbits));
-        const uint32_t slot = off[b] + atomicAdd(cursor + b, 1u);
-        entries[slot] = ((uint64_t)k << 32) | (uint32_t)i;
+        const uint64_t ent = ((uint64_t)k << 32) | (uint32_t)i;
+        const uint2 sl = slots[P.toff + i];
+        entries[off[P.boff + (table1_key(k, q) >> (q.ik - P.bbits))] + sl.x] = ent;
+        entries[off[nb + P.boff + (table2_key(k, q) >> (q.ik - P.bbits))] + sl.y] = ent;
     }
 }
 
-// Hits of query position q (pair P, strand s) against P's index: counted, or
-// written from `o` on when WRITE. The bucket bounds of all probes are loaded
-// together so the independent reads overlap; then each bucket is scanned for
-// entries whose key is the probe's.
+// Hits of query position q (pair P, strand s) against P's tables: counted, or
+// written from `o` on when WRITE. Both buckets' bounds are loaded together,
+// then each bucket is scanned for the entries its table accepts.
 template <bool WRITE>
 __device__ __forceinline__ uint32_t bhits_at(const uint32_t *__restrict__ Qs, long long qg,
                                              long long q, const PairInfo &P, int pair, int s,
                                              const SeedPattern &pat, int transition, int dbits,
-                                             const uint32_t *__restrict__ off,
+                                             long long nb, const uint32_t *__restrict__ off,
                                              const uint64_t *__restrict__ entries,
                                              uint64_t *__restrict__ out, unsigned long long o) {
     const uint32_t k = spaced_key(Qs, qg, pat);
-    const int kbits = 2 * pat.weight;
-    const int nprobe = transition ? pat.weight + 1 : 1;
-    uint32_t pk[MAX_PROBES], a[MAX_PROBES], e[MAX_PROBES];
-#pragma unroll
-    for (int i = 0; i < MAX_PROBES; i++) {
-        pk[i] = i == 0 ? k : k ^ (2u << (2 * (i - 1)));
-        const long long b = P.boff + (pk[i] >> (kbits - P.bbits));
-        a[i] = i < nprobe ? __ldg(off + b) : 0u;
-        e[i] = i < nprobe ? __ldg(off + b + 1) : 0u;
-    }
+    const Split sp = split_of(pat.weight);
+    const long long b1 = P.boff + (table1_key(k, sp) >> (sp.ik - P.bbits));
+    const long long b2 = nb + P.boff + (table2_key(k, sp) >> (sp.ik - P.bbits));
+    const uint32_t a1 = __ldg(off + b1), e1 = __ldg(off + b1 + 1);
+    const uint32_t a2 = transition ? __ldg(off + b2) : 0u;
+    const uint32_t e2 = transition ? __ldg(off + b2 + 1) : 0u;
     const uint32_t hi_base = ((uint32_t)pair << (dbits + 1)) | ((uint32_t)s << dbits);
     const long long dq = (long long)P.qlen - pat.span - q;  // D = t + dq
     uint32_t c = 0;
-#pragma unroll
-    for (int i = 0; i < MAX_PROBES; i++) {
-        for (uint32_t j = a[i]; j < e[i]; j++) {
-            const uint64_t ent = __ldg(entries + j);
-            if ((uint32_t)(ent >> 32) != pk[i]) continue;
-            if (WRITE) {
-                const uint32_t t = (uint32_t)ent;
-                out[o + c] = ((uint64_t)(hi_base | (uint32_t)(t + dq)) << 32) | t;
-            }
-            c++;
+    for (uint32_t j = a1; j < e1; j++) {
+        const uint64_t ent = __ldg(entries + j);
+        const uint32_t x = (uint32_t)(ent >> 32) ^ k;
+        // A exact, classes equal, at most one transition in B (none without transitions)
+        const bool hit = transition ? ((x & (sp.low | sp.highA)) == 0 && __popc(x & sp.highB) <= 1)
+                                    : x == 0;
+        if (!hit) continue;
+        if (WRITE) {
+            const uint32_t t = (uint32_t)ent;
+            out[o + c] = ((uint64_t)(hi_base | (uint32_t)(t + dq)) << 32) | t;
         }
+        c++;
+    }
+    for (uint32_t j = a2; j < e2; j++) {
+        const uint64_t ent = __ldg(entries + j);
+        const uint32_t x = (uint32_t)(ent >> 32) ^ k;
+        // B exact, classes equal, exactly one transition in A
+        if ((x & (sp.low | sp.highB)) != 0 || __popc(x & sp.highA) != 1) continue;
+        if (WRITE) {
+            const uint32_t t = (uint32_t)ent;
+            out[o + c] = ((uint64_t)(hi_base | (uint32_t)(t + dq)) << 32) | t;
+        }
+        c++;
     }
     return c;
 }
@@ -134,55 +196,6 @@ __device__ __forceinline__ void query_item(const long long *__restrict__ qprefix
     const long long local = item - qprefix[p];
     s = (int)(local & 1);
     q0 = (local >> 1) * ITEM;
-}
-
-// counts[s * qtotal + qoff + q] for every query position of every item.
-__global__ void __launch_bounds__(BLOCK) bhits_count(const uint32_t *__restrict__ Q,
-                                                     const uint32_t *__restrict__ Qrc,
-                                                     const PairInfo *__restrict__ pairs,
-                                                     const long long *__restrict__ qprefix,
-                                                     int npairs, int strands, SeedPattern pat,
-                                                     int transition, int dbits, long long qtotal,
-                                                     const uint32_t *__restrict__ off,
-                                                     const uint64_t *__restrict__ entries,
-                                                     uint32_t *__restrict__ counts) {
-    int pair, s;
-    long long q0;
-    query_item(qprefix, npairs, blockIdx.x, pair, s, q0);
-    if (!((strands >> s) & 1)) return;
-    const PairInfo P = pairs[pair];
-    if ((long long)P.tlen < pat.span) return;
-    const uint32_t *Qs = s ? Qrc : Q;
-    const long long qb = s ? P.qoff_rc : P.qoff;
-    const long long nq = (long long)P.qlen - pat.span + 1;
-    for (long long q = q0 + threadIdx.x; q < min(nq, q0 + ITEM); q += BLOCK)
-        counts[s * qtotal + P.qoff + q] = bhits_at<false>(Qs, qb + q, q, P, pair, s, pat,
-                                                          transition, dbits, off, entries,
-                                                          nullptr, 0);
-}
-
-__global__ void __launch_bounds__(BLOCK) bhits_write(const uint32_t *__restrict__ Q,
-                                                     const uint32_t *__restrict__ Qrc,
-                                                     const PairInfo *__restrict__ pairs,
-                                                     const long long *__restrict__ qprefix,
-                                                     int npairs, int strands, SeedPattern pat,
-                                                     int transition, int dbits, long long qtotal,
-                                                     const uint32_t *__restrict__ off,
-                                                     const uint64_t *__restrict__ entries,
-                                                     const unsigned long long *__restrict__ starts,
-                                                     uint64_t *__restrict__ hits) {
-    int pair, s;
-    long long q0;
-    query_item(qprefix, npairs, blockIdx.x, pair, s, q0);
-    if (!((strands >> s) & 1)) return;
-    const PairInfo P = pairs[pair];
-    if ((long long)P.tlen < pat.span) return;
-    const uint32_t *Qs = s ? Qrc : Q;
-    const long long qb = s ? P.qoff_rc : P.qoff;
-    const long long nq = (long long)P.qlen - pat.span + 1;
-    for (long long q = q0 + threadIdx.x; q < min(nq, q0 + ITEM); q += BLOCK)
-        bhits_at<true>(Qs, qb + q, q, P, pair, s, pat, transition, dbits, off, entries, hits,
-                       starts[s * qtotal + P.qoff + q]);
 }
 
 // ---------------------------------------------------------------- one-pass hits
@@ -198,7 +211,7 @@ __global__ void __launch_bounds__(BLOCK) bhits_emit(const uint32_t *__restrict__
                                                     const PairInfo *__restrict__ pairs,
                                                     const long long *__restrict__ qprefix,
                                                     int npairs, int strands, SeedPattern pat,
-                                                    int transition, int dbits,
+                                                    int transition, int dbits, long long nb,
                                                     const uint32_t *__restrict__ off,
                                                     const uint64_t *__restrict__ entries,
                                                     unsigned long long *__restrict__ total,
@@ -218,7 +231,7 @@ __global__ void __launch_bounds__(BLOCK) bhits_emit(const uint32_t *__restrict__
         const long long q = base + threadIdx.x;
         const bool valid = q < min(nq, q0 + ITEM);
         const uint32_t c = valid ? bhits_at<false>(Qs, qb + q, q, P, pair, s, pat, transition,
-                                                   dbits, off, entries, nullptr, 0)
+                                                   dbits, nb, off, entries, nullptr, 0)
                                  : 0u;
         uint32_t incl = c;
 #pragma unroll
@@ -232,7 +245,7 @@ __global__ void __launch_bounds__(BLOCK) bhits_emit(const uint32_t *__restrict__
         wbase = __shfl_sync(0xffffffffu, wbase, 31);
         const unsigned long long o = wbase + incl - c;
         if (c && o + c <= cap)
-            bhits_at<true>(Qs, qb + q, q, P, pair, s, pat, transition, dbits, off, entries, hits,
+            bhits_at<true>(Qs, qb + q, q, P, pair, s, pat, transition, dbits, nb, off, entries, hits,
                            o);
     }
 }
@@ -294,73 +307,46 @@ inline unsigned grid_for(long long n) { return (unsigned)((n + BLOCK - 1) / BLOC
 
 cudaError_t launch_batch_index(const uint32_t *T, const PairInfo *pairs, const long long *tprefix,
                                long long titems, int npairs, SeedPattern pat, uint32_t *cnt,
-                               long long nbuckets, uint32_t *off, uint64_t *entries, void *tmp,
-                               cudaStream_t st) {
-    cudaMemsetAsync(cnt, 0, (size_t)nbuckets * 4, st);
-    if (titems > 0) {
-        g_launches++;
-        bidx_count<<<(unsigned)titems, BLOCK, 0, st>>>(T, pairs, tprefix, npairs, pat, cnt);
-    }
-    cudaError_t e = scan_u32_to_u32(cnt, off, nbuckets, tmp, st);
+                               long long nbuckets, uint32_t *off, uint64_t *entries, uint2 *slots,
+                               void *tmp, cudaStream_t st) {
+    const long long nb2 = 2 * nbuckets;  // both tables
+    cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)nb2 * 4, st);
     if (e != cudaSuccess) return e;
-    cudaMemsetAsync(cnt, 0, (size_t)nbuckets * 4, st);  // reused as placement cursors
     if (titems > 0) {
         g_launches++;
-        bidx_fill<<<(unsigned)titems, BLOCK, 0, st>>>(T, pairs, tprefix, npairs, pat, off, cnt,
-                                                      entries);
+        bidx_count<<<(unsigned)titems, BLOCK, 0, st>>>(T, pairs, tprefix, npairs, pat, nbuckets,
+                                                       cnt, slots);
+    }
+    e = scan_u32_to_u32(cnt, off, nb2, tmp, st);
+    if (e != cudaSuccess) return e;
+    if (titems > 0) {
+        g_launches++;
+        bidx_fill<<<(unsigned)titems, BLOCK, 0, st>>>(T, pairs, tprefix, npairs, pat, nbuckets,
+                                                      off, slots, entries);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_hit_count(const uint32_t *Q, const uint32_t *Qrc, const PairInfo *pairs,
-                                   const long long *qprefix, long long qitems, int npairs,
-                                   int strands_mask, SeedPattern pat, int transition, int dbits,
-                                   long long qtotal, const uint32_t *off, const uint64_t *entries,
-                                   uint32_t *counts, cudaStream_t st) {
-    cudaMemsetAsync(counts, 0, (size_t)(2 * qtotal) * 4, st);
-    if (qitems > 0) {
-        g_launches++;
-        bhits_count<<<(unsigned)qitems, BLOCK, 0, st>>>(Q, Qrc, pairs, qprefix, npairs,
-                                                        strands_mask, pat, transition, dbits,
-                                                        qtotal, off, entries, counts);
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_batch_hit_write(const uint32_t *Q, const uint32_t *Qrc, const PairInfo *pairs,
-                                   const long long *qprefix, long long qitems, int npairs,
-                                   int strands_mask, SeedPattern pat, int transition, int dbits,
-                                   long long qtotal, const uint32_t *off, const uint64_t *entries,
-                                   const unsigned long long *starts, uint64_t *hits,
-                                   cudaStream_t st) {
-    if (qitems > 0) {
-        g_launches++;
-        bhits_write<<<(unsigned)qitems, BLOCK, 0, st>>>(Q, Qrc, pairs, qprefix, npairs,
-                                                        strands_mask, pat, transition, dbits,
-                                                        qtotal, off, entries, starts, hits);
-    }
-    return cudaGetLastError();
-}
+int batch_table_bits(int weight) { return split_of(weight).ik; }
 
 int batch_item_size() { return ITEM; }
 
 cudaError_t launch_batch_hit_emit(const uint32_t *Q, const uint32_t *Qrc, const PairInfo *pairs,
                                   const long long *qprefix, long long qitems, int npairs,
                                   int strands_mask, SeedPattern pat, int transition, int dbits,
-                                  const uint32_t *off, const uint64_t *entries,
-                                  unsigned long long *total, unsigned long long cap,
-                                  uint64_t *hits, cudaStream_t st) {
-    cudaMemsetAsync(total, 0, 8, st);
+                                  long long nbuckets, const uint32_t *off,
+                                  const uint64_t *entries, unsigned long long *total,
+                                  unsigned long long cap, uint64_t *hits, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(total, 0, 8, st);
+    if (e != cudaSuccess) return e;
     if (qitems > 0) {
         g_launches++;
         bhits_emit<<<(unsigned)qitems, BLOCK, 0, st>>>(Q, Qrc, pairs, qprefix, npairs,
-                                                       strands_mask, pat, transition, dbits, off,
-                                                       entries, total, cap, hits);
+                                                       strands_mask, pat, transition, dbits,
+                                                       nbuckets, off, entries, total, cap, hits);
     }
     return cudaGetLastError();
 }
-
-
 
 size_t batch_hsp_sort_temp_bytes(long long n) {
     n = n > 0 ? n : 1;

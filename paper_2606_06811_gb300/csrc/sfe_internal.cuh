@@ -261,28 +261,22 @@ cudaError_t hsp_sort(Hsp *hsps, long long n, int tbits, int qbits, void *tmp, ui
 // pair by pair: tprefix / qprefix (npairs + 1 entries, device) give each pair's
 // first item; query items hold both strands of a chunk next to each other.
 int batch_item_size();
+// The two split-key tables of every pair (see batch.cu): nbuckets per table,
+// cnt 2 * nbuckets, off 2 * nbuckets + 1, entries two per target position,
+// slots one per target base (scratch). PairInfo.bbits must be at most
+// batch_table_bits(weight).
+int batch_table_bits(int weight);
 cudaError_t launch_batch_index(const uint32_t *T, const PairInfo *pairs, const long long *tprefix,
                                long long titems, int npairs, SeedPattern pat, uint32_t *cnt,
-                               long long nbuckets, uint32_t *off, uint64_t *entries, void *tmp,
-                               cudaStream_t st);
-cudaError_t launch_batch_hit_count(const uint32_t *Q, const uint32_t *Qrc, const PairInfo *pairs,
-                                   const long long *qprefix, long long qitems, int npairs,
-                                   int strands_mask, SeedPattern pat, int transition, int dbits,
-                                   long long qtotal, const uint32_t *off, const uint64_t *entries,
-                                   uint32_t *counts, cudaStream_t st);
-cudaError_t launch_batch_hit_write(const uint32_t *Q, const uint32_t *Qrc, const PairInfo *pairs,
-                                   const long long *qprefix, long long qitems, int npairs,
-                                   int strands_mask, SeedPattern pat, int transition, int dbits,
-                                   long long qtotal, const uint32_t *off, const uint64_t *entries,
-                                   const unsigned long long *starts, uint64_t *hits,
-                                   cudaStream_t st);
+                               long long nbuckets, uint32_t *off, uint64_t *entries, uint2 *slots,
+                               void *tmp, cudaStream_t st);
 // One pass: hits in no particular order, at most cap written, *total = all.
 cudaError_t launch_batch_hit_emit(const uint32_t *Q, const uint32_t *Qrc, const PairInfo *pairs,
                                   const long long *qprefix, long long qitems, int npairs,
                                   int strands_mask, SeedPattern pat, int transition, int dbits,
-                                  const uint32_t *off, const uint64_t *entries,
-                                  unsigned long long *total, unsigned long long cap,
-                                  uint64_t *hits, cudaStream_t st);
+                                  long long nbuckets, const uint32_t *off,
+                                  const uint64_t *entries, unsigned long long *total,
+                                  unsigned long long cap, uint64_t *hits, cudaStream_t st);
 // Sort of a batch's HSPs by (pair, strand, tpos, qpos, len, score); n is the
 // count, or with `nd` the capacity and *nd the count. *out receives the
 // sorted array (in tmp, or h itself for n <= 1).

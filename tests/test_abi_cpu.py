@@ -51,3 +51,14 @@ def test_product_path_never_reaches_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"\bimport\s+oracle|from\s+oracle|oracle/", txt), f
+
+
+def test_autotune_candidates_skip_meaningless_combinations():
+    from paper_2606_06811_gb300 import autotune, sfe
+    cs = autotune.candidates(autotune.DEFAULT_SPACE)
+    two = [c for c in cs if c["walk_mode"] == sfe.WALK_TWO_LAUNCHES]
+    per = [c for c in cs if c["walk_mode"] == sfe.WALK_PERSISTENT]
+    assert len(two) == 3 and all("walk_chunk" not in c for c in two)
+    assert all(c["walk_schedule"] == sfe.SCHED_NATURAL for c in two)
+    assert len(per) == 3 * 2 * 2
+    assert len({tuple(sorted(c.items())) for c in cs}) == len(cs)

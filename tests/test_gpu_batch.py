@@ -127,3 +127,30 @@ def test_batch_plan_rejects_stage_timing_and_bad_offsets(pkg):
             ctx.batch_plan([0, 100], [0, 100], pkg.default_params(flags=pkg.TIME_STAGES))
         with pytest.raises(pkg.SfeError):
             ctx.batch_plan([0, 100, 50], [0, 10, 20], pkg.default_params())
+
+
+def test_autotuner_keeps_the_output_and_caches_its_choice(pkg, tmp_path):
+    import torch
+    from paper_2606_06811_gb300 import autotune
+    pairs = synth.batch_pairs(seed=13, n_pairs=32, len_lo=1000, len_hi=20_000)
+    T, toff, Q, qoff = concat_batch(pairs)
+    H, *_ = oracle_batch(pairs)
+    space = {"walk_mode": [0, 1], "lane_cap": [32, 256], "walk_chunk": [8, 64],
+             "walk_schedule": [0, 1]}
+    cache = str(tmp_path / "tune.json")
+    with pkg.Context(0) as ctx:
+        def run(c):
+            h, st = ctx.run_batch(T, toff, Q, qoff, pkg.default_params(input_codes=1, **c))
+            return np.ascontiguousarray(h).tobytes(), st
+        sig = autotune.batch_signature(toff, qoff, pkg.default_params())
+        best, table = autotune.tune(run, sig, space=space, reps=1, cache=cache)
+        assert len(table) == len(autotune.candidates(space)) == 2 + 8
+        assert best in [c for c, _ in table]
+        G = np.ascontiguousarray(run(best)[0])
+        assert np.array_equal(np.frombuffer(G, np.int32).reshape(-1, 6), H)
+
+        def never(c):
+            raise AssertionError("a cached workload is not timed again")
+        best2, _ = autotune.tune(never, sig, space=space, reps=1, cache=cache)
+        assert best2 == best
+    torch.cuda.synchronize()
