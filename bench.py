@@ -49,7 +49,8 @@ def args_parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sfe", choices=["sfe", "reference"])
-    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--seed", type=int, default=None,
+                    help="generator seed (default 2; 5 for large_pair_100mb)")
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = 10 Mb)")
     ap.add_argument("--lane-cap", type=int, default=0)
     ap.add_argument("--tile-hits", type=int, default=0)
@@ -65,12 +66,17 @@ def args_parse():
                     help="extension log sampling of the training run (1 in N)")
     ap.add_argument("--learned-chunk", type=int, default=128)
     ap.add_argument("--workload", default="plain_pair_10mb",
-                    choices=["plain_pair_10mb", "batch_pairs"],
+                    choices=["plain_pair_10mb", "batch_pairs", "large_pair_100mb"],
                     help="batch_pairs: 4096 uneven pairs, eager and as a replayed CUDA graph "
                          "(a separate line, not the headline)")
     ap.add_argument("--pairs", type=int, default=4096)
     ap.add_argument("--no-tune", action="store_true", help="batch: skip the autotuner")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.seed is None:
+        a.seed = 5 if a.workload == "large_pair_100mb" else 2
+    if a.workload == "large_pair_100mb":  # a separate line: no oracle sample, no predictor
+        a.no_learned = a.no_cpu_baseline = True
+    return a
 
 
 # --------------------------------------------------------------- helpers
@@ -171,9 +177,9 @@ def kernel_traffic(kernel: str) -> float | None:
 
 # ------------------------------------------------------------ workloads
 
-def make_workload(seed: int, scale: float):
+def make_workload(seed: int, scale: float, name: str = WORKLOAD):
     import synth
-    pair = synth.plain_pair_10mb(seed, scale=scale)
+    pair = getattr(synth, name)(seed, scale=scale)
     return pair, np.frombuffer(synth.decode(pair.T), np.uint8), np.frombuffer(
         synth.decode(pair.Q), np.uint8)
 
@@ -283,7 +289,7 @@ def run_sfe(a, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
 
-    pair, Ta, Qa = make_workload(a.seed, a.scale)
+    pair, Ta, Qa = make_workload(a.seed, a.scale, a.workload)
     T = torch.from_numpy(Ta.copy()).to(dev)
     Q = torch.from_numpy(Qa.copy()).to(dev)
     stream = torch.cuda.Stream(device=dev)
@@ -364,7 +370,7 @@ def run_sfe(a, rank, world, local):
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_ms / a.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "tlen": pair.tlen, "qlen": pair.qlen,
+        "config": {"workload": a.workload, "seed": a.seed, "tlen": pair.tlen, "qlen": pair.qlen,
                    "seed_pattern": "1110100110010101111", "transition": 1, "strands": 2,
                    "scores": "HOXD70", "xdrop": 910, "hsp_thresh": 3000,
                    "lane_cap": a.lane_cap or "default", "parallelism": f"replicas{world}",

@@ -111,7 +111,7 @@ typedef struct {
     int32_t input_codes;      /* 0: ASCII ACGTacgt, 1: codes 0..3 */
     int32_t lane_cap;         /* bases per side a lane extends before handing the diagonal to a warp; 0 = default */
     int32_t lanes_per_sm;     /* lane-tier threads per SM sharing a tile's hits (sizes their hit ranges); 0 = default */
-    int64_t tile_hits;        /* hits per query tile (bounds scratch memory); 0 = default */
+    int64_t tile_hits;        /* hits per query tile (bounds scratch memory); 0 = default (2^30) */
     int32_t walk_chunk;       /* hits a lane takes per grab from the work counter; 0 = default (32) */
     int32_t walk_mode;        /* SFE_WALK_TWO_LAUNCHES (default) or SFE_WALK_PERSISTENT */
     int32_t walk_schedule;    /* order in which the persistent walk hands out chunks (SFE_SCHED_*);

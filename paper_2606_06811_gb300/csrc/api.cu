@@ -43,7 +43,7 @@ const int32_t kHoxd70[16] = {91,   -114, -31, -123, -114, 100,  -125, -31,
 const char *kDefaultPattern = "1110100110010101111";
 
 constexpr int kDefaultLaneCap = 256;
-constexpr long long kDefaultTileHits = 1LL << 28;
+constexpr long long kDefaultTileHits = 1LL << 30;  // 8 GB per hit buffer
 constexpr unsigned long long kQueueMax = 1ull << 20;
 // A batch pair's split-key tables have about npos / 2 buckets each (1 to 2
 // entries per bucket: measured on 4096 pairs, 20.6 ms per batch against 21.2

@@ -19,8 +19,12 @@ constexpr int RS_BLOCK = 256;
 constexpr int RS_WARPS = RS_BLOCK / 32;
 constexpr int RS_ITEMS = 16;
 constexpr int RS_TILE = RS_BLOCK * RS_ITEMS;  // 4096
-constexpr int RS_MAXBITS = 9;                 // widest digit
-constexpr int RS_R = 1 << RS_MAXBITS;         // buckets per pass (+1 for padding lanes)
+// Digits of up to 9 bits (512 buckets); 10 bits (1024) only where that saves a
+// pass, since the wider histograms cost every tile more (measured: a 25-bit
+// key sorts faster with 512 buckets than with 1024, a 28-bit key faster in
+// three passes of up to 10 bits than in four of 7).
+constexpr int RS_MAXBITS = 10;
+constexpr int RS_R = 1 << RS_MAXBITS;  // largest bucket count (sizes the count arrays)
 
 int g_num_sms = 0;
 
@@ -62,14 +66,17 @@ __device__ __forceinline__ void rs_device_count(const unsigned long long *nd, in
     chunk = max(1LL, (tiles + G - 1) / G) * RS_TILE;
 }
 
+// DEVN: the key count is read from *nd (a separate instantiation, so the
+// host-count kernels keep their parameters in the constant bank)
+template <int R, bool DEVN>
 __global__ void __launch_bounds__(RS_BLOCK) rs_hist(const uint64_t *__restrict__ keys,
                                                     long long n, const unsigned long long *nd,
                                                     int shift, unsigned mask, long long chunk,
                                                     unsigned *__restrict__ counts,
                                                     unsigned *__restrict__ totals, int G) {
-    __shared__ unsigned h[RS_WARPS][RS_R];
-    rs_device_count(nd, G, n, chunk);
-    for (int i = threadIdx.x; i < RS_WARPS * RS_R; i += RS_BLOCK) (&h[0][0])[i] = 0;
+    __shared__ unsigned h[RS_WARPS][R];
+    if (DEVN) rs_device_count(nd, G, n, chunk);
+    for (int i = threadIdx.x; i < RS_WARPS * R; i += RS_BLOCK) (&h[0][0])[i] = 0;
     __syncthreads();
     long long beg = (long long)blockIdx.x * chunk;
     long long end = min(n, beg + chunk);
@@ -79,7 +86,7 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_hist(const uint64_t *__restrict__
         atomicAdd(&h[w][d], 1u);
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < RS_R; d += RS_BLOCK) {
+    for (int d = threadIdx.x; d < R; d += RS_BLOCK) {
         unsigned s = 0;
 #pragma unroll
         for (int k = 0; k < RS_WARPS; k++) s += h[k][d];
@@ -152,29 +159,29 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_offsets(unsigned *__restrict__ co
     }
 }
 
-template <bool VALS>
+template <bool VALS, int R, bool DEVN>
 __global__ void __launch_bounds__(RS_BLOCK) rs_scatter(
     const uint64_t *__restrict__ kin, uint64_t *__restrict__ kout,
     const unsigned *__restrict__ vin, unsigned *__restrict__ vout, long long n,
     const unsigned long long *nd, int shift, unsigned mask, long long chunk,
     const unsigned *__restrict__ offsets, int G) {
-    rs_device_count(nd, G, n, chunk);
+    if (DEVN) rs_device_count(nd, G, n, chunk);
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *sk = reinterpret_cast<uint64_t *>(smem);                     // RS_TILE
     unsigned *sv = reinterpret_cast<unsigned *>(sk + RS_TILE);              // RS_TILE (VALS)
     unsigned *wh = sv + (VALS ? RS_TILE : 0);                               // RS_WARPS*(R+1)
-    unsigned *tcount = wh + RS_WARPS * (RS_R + 1);                          // R+1
-    unsigned *tstart = tcount + (RS_R + 1);                                 // R+1
-    unsigned *run = tstart + (RS_R + 1);                                    // R
+    unsigned *tcount = wh + RS_WARPS * (R + 1);                          // R+1
+    unsigned *tstart = tcount + (R + 1);                                 // R+1
+    unsigned *run = tstart + (R + 1);                                    // R
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const long long beg = (long long)blockIdx.x * chunk;
     const long long end = min(n, beg + chunk);
-    for (int d = tid; d < RS_R; d += RS_BLOCK) run[d] = offsets[(long long)d * G + blockIdx.x];
+    for (int d = tid; d < R; d += RS_BLOCK) run[d] = offsets[(long long)d * G + blockIdx.x];
 
     for (long long tb = beg; tb < end; tb += RS_TILE) {
         const unsigned tile_n = (unsigned)min((long long)RS_TILE, end - tb);
-        for (int i = tid; i < RS_WARPS * (RS_R + 1); i += RS_BLOCK) wh[i] = 0;
+        for (int i = tid; i < RS_WARPS * (R + 1); i += RS_BLOCK) wh[i] = 0;
         __syncthreads();
 
         uint64_t k[RS_ITEMS];
@@ -186,9 +193,9 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_scatter(
             bool valid = e < tile_n;
             k[j] = valid ? kin[tb + e] : ~0ull;
             if (VALS) v[j] = valid ? vin[tb + e] : 0u;
-            dg[j] = valid ? ((unsigned)(k[j] >> shift) & mask) : (unsigned)RS_R;
+            dg[j] = valid ? ((unsigned)(k[j] >> shift) & mask) : (unsigned)R;
         }
-        unsigned *myh = wh + w * (RS_R + 1);
+        unsigned *myh = wh + w * (R + 1);
 #pragma unroll
         for (int j = 0; j < RS_ITEMS; j++) {
             unsigned peers = __match_any_sync(0xffffffffu, dg[j]);
@@ -201,12 +208,12 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_scatter(
         }
         __syncthreads();
         // per digit: exclusive prefix across warps, tile totals
-        for (int d = tid; d <= RS_R; d += RS_BLOCK) {
+        for (int d = tid; d <= R; d += RS_BLOCK) {
             unsigned s = 0;
 #pragma unroll
             for (int ww = 0; ww < RS_WARPS; ww++) {
-                unsigned c = wh[ww * (RS_R + 1) + d];
-                wh[ww * (RS_R + 1) + d] = s;
+                unsigned c = wh[ww * (R + 1) + d];
+                wh[ww * (R + 1) + d] = s;
                 s += c;
             }
             tcount[d] = s;
@@ -214,12 +221,12 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_scatter(
         __syncthreads();
         // exclusive scan of tcount[0..R] by warp 0 (17 values per lane)
         if (w == 0) {
-            constexpr int PER = (RS_R + 1 + 31) / 32;
+            constexpr int PER = (R + 1 + 31) / 32;
             unsigned loc[PER], s = 0;
 #pragma unroll
             for (int i = 0; i < PER; i++) {
                 int d = lane * PER + i;
-                loc[i] = (d <= RS_R) ? tcount[d] : 0u;
+                loc[i] = (d <= R) ? tcount[d] : 0u;
                 s += loc[i];
             }
             unsigned inc = warp_incl(s);
@@ -227,7 +234,7 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_scatter(
 #pragma unroll
             for (int i = 0; i < PER; i++) {
                 int d = lane * PER + i;
-                if (d <= RS_R) tstart[d] = ex;
+                if (d <= R) tstart[d] = ex;
                 ex += loc[i];
             }
         }
@@ -247,14 +254,48 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_scatter(
             if (VALS) vout[o] = sv[p];
         }
         __syncthreads();
-        for (int d = tid; d < RS_R; d += RS_BLOCK) run[d] += tcount[d];
+        for (int d = tid; d < R; d += RS_BLOCK) run[d] += tcount[d];
         __syncthreads();
     }
 }
 
-size_t rs_smem(bool vals) {
+size_t rs_smem(bool vals, int R) {
     return (size_t)RS_TILE * 8 + (vals ? (size_t)RS_TILE * 4 : 0) +
-           (size_t)RS_WARPS * (RS_R + 1) * 4 + 2 * (size_t)(RS_R + 1) * 4 + (size_t)RS_R * 4;
+           (size_t)RS_WARPS * (R + 1) * 4 + 2 * (size_t)(R + 1) * 4 + (size_t)R * 4;
+}
+
+// One LSD pass with 2^bits <= R buckets.
+template <int R, bool DEVN>
+cudaError_t rs_pass(const uint64_t *kin, uint64_t *kout, const uint32_t *vin, uint32_t *vout,
+                    long long n, const unsigned long long *nd, int shift, unsigned mask,
+                    const RsGeom &g, unsigned *counts, unsigned *totals, cudaStream_t st) {
+    const bool vals = vin != nullptr;
+    const size_t smem = rs_smem(vals, R);
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[vals]) {
+        cudaError_t e = vals ? cudaFuncSetAttribute(rs_scatter<true, R, DEVN>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)smem)
+                             : cudaFuncSetAttribute(rs_scatter<false, R, DEVN>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set[vals] = true;
+    }
+    cudaError_t me = cudaMemsetAsync(totals, 0, R * 4, st);
+    if (me != cudaSuccess) return me;
+    g_launches += 3;
+    rs_hist<R, DEVN><<<g.G, RS_BLOCK, 0, st>>>(kin, n, nd, shift, mask, g.chunk, counts, totals,
+                                               g.G);
+    rs_offsets<<<R, RS_BLOCK, 0, st>>>(counts, totals, g.G);
+    if (vals)
+        rs_scatter<true, R, DEVN><<<g.G, RS_BLOCK, smem, st>>>(kin, kout, vin, vout, n, nd, shift,
+                                                               mask, g.chunk, counts, g.G);
+    else
+        rs_scatter<false, R, DEVN><<<g.G, RS_BLOCK, smem, st>>>(kin, kout, nullptr, nullptr, n,
+                                                                nd, shift, mask, g.chunk, counts,
+                                                                g.G);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------- scans
@@ -396,40 +437,30 @@ cudaError_t radix_sort_dev(uint64_t *keys_a, uint64_t *keys_b, uint32_t *vals_a,
     RsGeom g = rs_geom(n);
     unsigned *counts = reinterpret_cast<unsigned *>(tmp);
     unsigned *totals = counts + (size_t)RS_R * g.G;
-    const bool vals = vals_a != nullptr;
-    size_t smem = rs_smem(vals);
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[vals]) {
-        cudaError_t e = vals ? cudaFuncSetAttribute(rs_scatter<true>,
-                                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                    (int)smem)
-                             : cudaFuncSetAttribute(rs_scatter<false>,
-                                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                    (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set[vals] = true;
-    }
+    // as few passes as 9-bit digits allow, or 10-bit ones where that saves a
+    // pass, with the bits spread evenly (25 bits: 9 + 9 + 7; 28: 10 + 10 + 8)
+    const int nbits = hi - lo;
+    const int p9 = (nbits + 8) / 9, p10 = (nbits + 9) / 10;
+    const int npass = p10 < p9 ? p10 : p9;
+    const int per = (nbits + npass - 1) / npass;
     uint64_t *kin = keys_a, *kout = keys_b;
     uint32_t *vin = vals_a, *vout = vals_b;
     bool in_b = false;
-    // as few passes as the widest digit allows, with the bits spread evenly
-    // over them (a 25-bit key takes 9 + 8 + 8, not 8 + 8 + 8 + 1)
-    const int npass = (hi - lo + RS_MAXBITS - 1) / RS_MAXBITS;
-    const int per = (hi - lo + npass - 1) / npass;
     for (int shift = lo; shift < hi; shift += per) {
-        int bits = min(per, hi - shift);
-        unsigned mask = (1u << bits) - 1u;
-        cudaError_t me = cudaMemsetAsync(totals, 0, RS_R * 4, st);
-        if (me != cudaSuccess) return me;
-        g_launches += 3;
-        rs_hist<<<g.G, RS_BLOCK, 0, st>>>(kin, n, nd, shift, mask, g.chunk, counts, totals, g.G);
-        rs_offsets<<<RS_R, RS_BLOCK, 0, st>>>(counts, totals, g.G);
-        if (vals)
-            rs_scatter<true><<<g.G, RS_BLOCK, smem, st>>>(kin, kout, vin, vout, n, nd, shift,
-                                                          mask, g.chunk, counts, g.G);
+        const int bits = min(per, hi - shift);
+        const unsigned mask = (1u << bits) - 1u;
+        cudaError_t e;
+        if (nd)
+            e = bits > 9 ? rs_pass<1024, true>(kin, kout, vin, vout, n, nd, shift, mask, g, counts,
+                                               totals, st)
+                         : rs_pass<512, true>(kin, kout, vin, vout, n, nd, shift, mask, g, counts,
+                                              totals, st);
         else
-            rs_scatter<false><<<g.G, RS_BLOCK, smem, st>>>(kin, kout, nullptr, nullptr, n, nd,
-                                                           shift, mask, g.chunk, counts, g.G);
+            e = bits > 9 ? rs_pass<1024, false>(kin, kout, vin, vout, n, nd, shift, mask, g,
+                                                counts, totals, st)
+                         : rs_pass<512, false>(kin, kout, vin, vout, n, nd, shift, mask, g, counts,
+                                               totals, st);
+        if (e != cudaSuccess) return e;
         uint64_t *tk = kin;
         kin = kout;
         kout = tk;
