@@ -722,7 +722,7 @@ int sfe_seed_hits(sfe_ctx *c, const sfe_index *ix, const uint8_t *query, int64_t
         hp.transition = v.transition;
         hp.qlen = qlen;
         hp.qoff = qlen - v.pat.span;
-        CK(launch_hit_write(s ? Qm : Qp, hp, v.offs, v.pos, 0, nq, starts, 0, ha, c->st));
+        CK(launch_hit_write(s ? Qm : Qp, hp, v.offs, v.pos, 0, nq, starts, 0, t2, ha, c->st));
         bool in_b = false;
         CK(radix_sort(ha, hb, nullptr, nullptr, (long long)t2, 32, 32 + DB, tmp, &in_b, &c->small->status, c->st));
         CK(launch_hits_to_public(in_b ? hb : ha, (long long)t2, s, hp.qoff, dst + at, c->st));
@@ -907,7 +907,7 @@ int sfe_run(sfe_ctx *c, const uint8_t *target, int64_t tlen, const uint8_t *quer
                 {
                     Span sp(c, SFE_STAGE_WRITE);
                     CK(launch_hit_write(Qs, hp, offs, pos, qb[k], qb[k + 1], starts + qb[k], hb[k],
-                                        ha, c->st));
+                                        (unsigned long long)nh, ha, c->st));
                 }
                 bool in_b = false;
                 {

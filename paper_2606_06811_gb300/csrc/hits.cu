@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(BLOCK) hit_count_kernel(const uint32_t *__rest
 }
 
 // Hits go out with evict-first stores: the stream of hit records must not push
-// the CSR table out of L2.
+// the CSR table out of L2. Each thread writes the hits of its query position.
 __global__ void __launch_bounds__(BLOCK) hit_write_kernel(
     const uint32_t *__restrict__ Qs, HitParams hp, const uint32_t *__restrict__ off,
     const uint32_t *__restrict__ pos, long long q0, long long q1,
@@ -80,6 +80,71 @@ __global__ void __launch_bounds__(BLOCK) hit_write_kernel(
     }
 }
 
+// The same output, for query ranges with many hits per position (repeat
+// families, long homologous blocks): one warp writes the hits of its 32 query
+// positions together. The warp's output range is contiguous and in q order
+// (lane order, then probe order, then bucket order), so output slot k of the
+// warp is found by two small searches in shared memory (the lane, then the
+// probe), and the position reads and hit writes of consecutive slots are
+// consecutive. The set-up costs shared memory and registers, so positions
+// with few hits are faster with the kernel above.
+constexpr int HW_WARPS = BLOCK / 32;
+
+__global__ void __launch_bounds__(BLOCK) hit_write_warp_kernel(
+    const uint32_t *__restrict__ Qs, HitParams hp, const uint32_t *__restrict__ off,
+    const uint32_t *__restrict__ pos, long long q0, long long q1,
+    const unsigned long long *__restrict__ starts, unsigned long long base,
+    uint64_t *__restrict__ hits) {
+    __shared__ uint32_t s_a[HW_WARPS][32][MAX_PROBES];      // bucket starts
+    __shared__ uint32_t s_p[HW_WARPS][32][MAX_PROBES + 1];  // lane's exclusive prefix over probes
+    __shared__ uint32_t s_o[HW_WARPS][33];                  // warp's exclusive prefix over lanes
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long qw = q0 + (blockIdx.x * (long long)blockDim.x) + w * 32;  // lane 0's q
+    if (qw >= q1) return;
+    const long long q = qw + lane;
+    uint32_t a[MAX_PROBES], b[MAX_PROBES];
+    if (q < q1) {
+        probe_bounds(Qs, q, hp, off, a, b);
+    } else {
+#pragma unroll
+        for (int i = 0; i < MAX_PROBES; i++) a[i] = b[i] = 0u;
+    }
+    uint32_t c = 0;
+#pragma unroll
+    for (int i = 0; i < MAX_PROBES; i++) {
+        s_a[w][lane][i] = a[i];
+        s_p[w][lane][i] = c;
+        c += b[i] - a[i];
+    }
+    s_p[w][lane][MAX_PROBES] = c;
+    uint32_t incl = c;  // a warp's hits lie in one query tile (checked: < 2^32)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    s_o[w][lane] = incl - c;
+    if (lane == 31) s_o[w][32] = incl;
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    const unsigned long long wbase = starts[qw - q0] - base;
+    __syncwarp();
+    for (uint32_t k = lane; k < total; k += 32) {
+        int L = 0;  // last lane whose range starts at or before k
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+            if (s_o[w][L + step] <= k) L += step;
+        const uint32_t r = k - s_o[w][L];
+        int i = 0;  // last probe whose range starts at or before r
+#pragma unroll
+        for (int step = 8; step > 0; step >>= 1)
+            if (i + step < MAX_PROBES && s_p[w][L][i + step] <= r) i += step;
+        const uint32_t t = __ldg(pos + s_a[w][L][i] + (r - s_p[w][L][i]));
+        const long long dq = hp.qoff - (qw + L);  // D = t + dq
+        __stcs(reinterpret_cast<unsigned long long *>(hits) + wbase + k,
+               (unsigned long long)make_hit((uint32_t)(t + dq), t));
+    }
+}
+
 inline unsigned grid_for(long long n) { return (unsigned)((n + BLOCK - 1) / BLOCK); }
 
 }  // namespace
@@ -95,11 +160,17 @@ cudaError_t launch_hit_count(const uint32_t *Qs, HitParams hp, const uint32_t *o
 cudaError_t launch_hit_write(const uint32_t *Qs, HitParams hp, const uint32_t *offsets,
                              const uint32_t *positions, long long q0, long long q1,
                              const unsigned long long *starts, unsigned long long base,
-                             uint64_t *hits, cudaStream_t st) {
+                             unsigned long long nhits, uint64_t *hits, cudaStream_t st) {
     if (q1 <= q0) return cudaSuccess;
     g_launches++;
-    hit_write_kernel<<<grid_for(q1 - q0), BLOCK, 0, st>>>(Qs, hp, offsets, positions, q0, q1,
-                                                          starts, base, hits);
+    // measured: ~10 hits per position (the 10 Mb pair) is faster per thread,
+    // ~95 (the 100 Mb pair's repeats) per warp
+    if (nhits >= 32ull * (unsigned long long)(q1 - q0))
+        hit_write_warp_kernel<<<grid_for(q1 - q0), BLOCK, 0, st>>>(Qs, hp, offsets, positions,
+                                                                   q0, q1, starts, base, hits);
+    else
+        hit_write_kernel<<<grid_for(q1 - q0), BLOCK, 0, st>>>(Qs, hp, offsets, positions, q0, q1,
+                                                              starts, base, hits);
     return cudaGetLastError();
 }
 

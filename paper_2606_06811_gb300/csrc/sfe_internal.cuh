@@ -140,10 +140,11 @@ struct HitParams {
 };
 cudaError_t launch_hit_count(const uint32_t *Qs, HitParams hp, const uint32_t *offsets,
                              long long q0, long long q1, uint32_t *counts, cudaStream_t st);
+// nhits: the hits of [q0, q1) (picks a per-thread or a per-warp writer)
 cudaError_t launch_hit_write(const uint32_t *Qs, HitParams hp, const uint32_t *offsets,
                              const uint32_t *positions, long long q0, long long q1,
                              const unsigned long long *starts, unsigned long long base,
-                             uint64_t *hits, cudaStream_t st);
+                             unsigned long long nhits, uint64_t *hits, cudaStream_t st);
 
 struct WalkParams {
     const uint32_t *T;   // packed target (base 0)

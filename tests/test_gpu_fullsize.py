@@ -93,7 +93,7 @@ def test_plain_pair_10mb_full_size(pkg):
 def test_large_pair_100mb_full_size_tiled(pkg):
     pair = synth.large_pair_100mb(5)
     H, st = run_gpu(pkg, pair)
-    assert st["tiles"] > 20  # the query is tiled, with the skip state carried across tiles
+    assert st["tiles"] > 10  # the query is tiled, with the skip state carried across tiles
     assert H.shape[0] > 1e6
     sub = H[synth.Stream(9, "sub").integers(0, H.shape[0], 200_000)]
     check_scores(pair, sub)
