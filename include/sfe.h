@@ -121,7 +121,18 @@ typedef struct {
                                  (pair, strand, t, q), so it does not depend on the schedule */
     int64_t ext_log_cap;      /* records the buffer holds (further ones are counted, not written) */
     const void *model;        /* device weights of the work predictor (SFE_SCHED_PREDICTED) */
+    int32_t wait_limit;       /* polls of a bounded device wait (the persistent walk's hand-off
+                                 queue) before the call fails with SFE_ETIMEOUT; 0 = default (2^26) */
+    int32_t test_hooks;       /* SFE_TEST_* bits; 0 in normal use */
 } sfe_params;
+
+/* sfe_params.test_hooks (no counterpart in the paper: they let tests drive the
+ * library's error paths without faulting a GPU). SFE_TEST_UNPUBLISHED_QUEUE_ENTRY
+ * reserves one slot of the persistent walk's hand-off queue that is never
+ * written, so the warp that takes it waits until wait_limit runs out and the
+ * call returns SFE_ETIMEOUT (all other work completes; the context stays
+ * usable). */
+#define SFE_TEST_UNPUBLISHED_QUEUE_ENTRY 1
 
 /* sfe_params.walk_schedule: the order of work never changes the output, only
  * how evenly it spreads over the warps */
@@ -164,6 +175,10 @@ int sfe_ctx_create(int device, sfe_ctx **out);
 /* Queue later work on `stream` (a cudaStream_t, e.g. a PyTorch stream); NULL
  * restores the context's own stream. The caller keeps the stream alive. */
 int sfe_ctx_set_stream(sfe_ctx *ctx, void *stream);
+/* Test hook (no counterpart in the paper): the next n device allocations of
+ * the context's scratch arena fail as if the device were out of memory, so
+ * the calls that need them return SFE_ENOMEM. n = 0 clears it. */
+int sfe_ctx_fail_next_allocs(sfe_ctx *ctx, int32_t n);
 void sfe_ctx_destroy(sfe_ctx *ctx);
 
 /*

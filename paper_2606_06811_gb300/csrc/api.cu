@@ -103,6 +103,7 @@ struct sfe_ctx {
     unsigned long long batch_hits_hint = 0;  // hits of the last batch (room for the next)
     StageTimer tm;
     unsigned long long launches0 = 0;
+    int fail_allocs = 0;  // test hook: allocations still to fail
 };
 
 struct sfe_index {
@@ -121,6 +122,10 @@ namespace {
 int ensure(sfe_ctx *c, int slot, size_t bytes, void **out) {
     if (bytes < 256) bytes = 256;
     if (c->cap[slot] < bytes) {
+        if (c->fail_allocs > 0) {
+            c->fail_allocs--;
+            return fail(SFE_ENOMEM, "device allocation failed (injected by the test hook)");
+        }
         if (c->buf[slot]) {
             CK(cudaFreeAsync(c->buf[slot], c->st));
             c->buf[slot] = nullptr;
@@ -448,6 +453,8 @@ int walk_tiers(sfe_ctx *c, const uint64_t *hits, long long n, WalkParams &wp, ui
     wp.queue_take = &sm->queue_take;
     wp.chunk = p->walk_chunk > 0 ? (uint32_t)p->walk_chunk : 32u;
     wp.order = nullptr;
+    wp.spin_limit = p->wait_limit > 0 ? p->wait_limit : (1LL << 26);
+    wp.phantom = (p->test_hooks & SFE_TEST_UNPUBLISHED_QUEUE_ENTRY) ? 1 : 0;
     if (p->walk_schedule != SFE_SCHED_NATURAL) {
         Span sp(c, SFE_STAGE_SCHEDULE);
         void *tmp = sched_tmp;
@@ -592,6 +599,12 @@ int sfe_ctx_create(int device, sfe_ctx **out) {
     }
     c->st = c->own;
     *out = c;
+    return SFE_OK;
+}
+
+int sfe_ctx_fail_next_allocs(sfe_ctx *c, int32_t n) {
+    if (!c || n < 0) return fail(SFE_EINVAL, "bad context or count");
+    c->fail_allocs = n;
     return SFE_OK;
 }
 

@@ -182,6 +182,8 @@ struct WalkParams {
     // hit count in device memory (at most the launch's n), for launches that
     // must not wait for the host (graph replay); null: the launch's n
     const unsigned long long *nd;
+    long long spin_limit;  // polls of the hand-off queue before ST_TIMEOUT
+    int phantom;           // test hook: reserve one queue slot that is never written
     // sampled log of extensions (elog == nullptr: none)
     sfe_ext_record *elog;
     unsigned long long elog_cap;

@@ -15,6 +15,8 @@ namespace sfe {
 
 namespace {
 
+// 256 threads x 16 keys per tile: measured against 256 x 8, 512 x 8, 512 x 16
+// and 128 x 32 on the 10 Mb pair's hit sort (5.5 ms against 5.9-7.3 ms).
 constexpr int RS_BLOCK = 256;
 constexpr int RS_WARPS = RS_BLOCK / 32;
 constexpr int RS_ITEMS = 16;

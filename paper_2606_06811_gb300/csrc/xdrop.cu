@@ -31,7 +31,6 @@ namespace {
 
 constexpr int W_BLOCK = 256;
 constexpr int SCORE_LIMIT = 1 << 30;  // a best score above this flags overflow
-constexpr long long QUEUE_SPIN_LIMIT = 1LL << 26;  // polls of an empty hand-off queue before giving up
 
 struct Side {
     int best;    // maximum of the running sum (0 for the empty extension)
@@ -302,6 +301,8 @@ __global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__r
     }
     __syncthreads();
     const int span = wp.span, X = wp.xdrop;
+    if (PERSIST && wp.phantom && blockIdx.x == 0 && threadIdx.x == 0)
+        atomicAdd(wp.queue_len, 1u);  // test hook: a queue slot nobody will publish
     uint32_t nchunks = wp.nchunks;
     if (wp.nd) {  // the hit count lives on the device: ranges and chunks follow it
         n = (uint32_t)min((unsigned long long)n, *wp.nd);
@@ -475,7 +476,7 @@ __global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__r
                         const unsigned wd = *(volatile unsigned *)wp.warps_done;
                         const unsigned ql = *(volatile unsigned *)wp.queue_len;
                         if (wd >= total_warps && e >= min(ql, (unsigned)wp.queue_cap)) state = 2;
-                        else if (++spins > QUEUE_SPIN_LIMIT) {
+                        else if (++spins > wp.spin_limit) {
                             status |= ST_TIMEOUT;
                             state = 2;
                         }

@@ -21,6 +21,7 @@ SKIP_PASSING_ONLY = 1
 TIME_STAGES = 2
 WALK_TWO_LAUNCHES, WALK_PERSISTENT = 0, 1
 SCHED_NATURAL, SCHED_LARGEST_FIRST, SCHED_PREDICTED, SCHED_RANDOM = 0, 1, 2, 3
+TEST_UNPUBLISHED_QUEUE_ENTRY = 1
 EXT_DTYPE = np.dtype([("pair", "<i4"), ("strand", "<i4"), ("t", "<i4"), ("q", "<i4"),
                       ("right", "<i4"), ("left", "<i4")])
 STAGES = ("pack", "index", "count", "write", "sort", "schedule", "walk_lanes", "walk_warps",
@@ -46,7 +47,7 @@ class Params(C.Structure):
                 ("lane_cap", C.c_int32), ("lanes_per_sm", C.c_int32), ("tile_hits", C.c_int64),
                 ("walk_chunk", C.c_int32), ("walk_mode", C.c_int32), ("walk_schedule", C.c_int32),
                 ("ext_log_every", C.c_int32), ("ext_log", C.c_void_p), ("ext_log_cap", C.c_int64),
-                ("model", C.c_void_p)]
+                ("model", C.c_void_p), ("wait_limit", C.c_int32), ("test_hooks", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -83,6 +84,8 @@ def lib() -> C.CDLL:
         L.sfe_last_error.restype = C.c_char_p
         L.sfe_ctx_create.argtypes = [C.c_int, C.POINTER(vp)]
         L.sfe_ctx_set_stream.argtypes = [vp, vp]
+        L.sfe_ctx_fail_next_allocs.argtypes = [vp, i32]
+        L.sfe_ctx_fail_next_allocs.restype = C.c_int
         L.sfe_ctx_destroy.argtypes = [vp]
         L.sfe_ctx_destroy.restype = None
         L.sfe_index_build.argtypes = [vp, vp, i64, C.POINTER(Params), C.POINTER(vp)]
@@ -186,6 +189,10 @@ class Context:
 
     def set_stream(self, stream) -> None:
         _check(lib().sfe_ctx_set_stream(self.h, _stream_handle(stream)))
+
+    def fail_next_allocs(self, n: int) -> None:
+        """Test hook: the next n scratch allocations fail with SFE_ENOMEM."""
+        _check(lib().sfe_ctx_fail_next_allocs(self.h, int(n)))
 
     def close(self) -> None:
         if getattr(self, "h", None):

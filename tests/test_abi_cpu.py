@@ -62,3 +62,33 @@ def test_autotune_candidates_skip_meaningless_combinations():
     assert all(c["walk_schedule"] == sfe.SCHED_NATURAL for c in two)
     assert len(per) == 3 * 2 * 2
     assert len({tuple(sorted(c.items())) for c in cs}) == len(cs)
+
+
+def _c_layout(struct: str, fields: list[str], tmp) -> dict:
+    """sizeof and offsetof of a struct of include/sfe.h, from a C compiler."""
+    import subprocess
+    lines = [f'printf("size %zu\\n", sizeof({struct}));']
+    lines += [f'printf("{f} %zu\\n", offsetof({struct}, {f}));' for f in fields]
+    src = "#include <stdio.h>\n#include <stddef.h>\n#include \"sfe.h\"\nint main(void){" + \
+        "".join(lines) + "return 0;}\n"
+    c = tmp / "layout.c"
+    c.write_text(src)
+    exe = tmp / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)]).decode().split("\n")
+    return {k: int(v) for k, v in (l.split() for l in out if l)}
+
+
+@pytest.mark.parametrize("name", ["Params", "Stats"])
+def test_ctypes_mirrors_match_the_c_layout(name, tmp_path):
+    import shutil
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    from paper_2606_06811_gb300 import sfe
+    cls = getattr(sfe, name)
+    struct = {"Params": "sfe_params", "Stats": "sfe_stats"}[name]
+    fields = [f for f, _ in cls._fields_]
+    lay = _c_layout(struct, fields, tmp_path)
+    assert lay["size"] == ctypes.sizeof(cls)
+    for f in fields:
+        assert lay[f] == getattr(cls, f).offset, f
