@@ -88,6 +88,17 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_over_ranks(dist, device, ms: float, counts: list) -> tuple[float, list]:
+    """Replicas: the job takes as long as its slowest rank (max of the timed
+    milliseconds) and does the work of all ranks (sum of the counts)."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(x) for x in counts], dtype=torch.float64, device=device)
+    dist.all_reduce(c)
+    return float(t.item()), [float(x) for x in c.tolist()]
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
 
@@ -339,12 +350,8 @@ def run_sfe(a, rank, world, local):
     stage_launch = {k: sum(s["stage_launches"][k] for s in stats) / a.steps for k in pkg.STAGES}
 
     if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        tot = torch.tensor([cells, hsps, hits], dtype=torch.float64, device=dev)
-        dist.all_reduce(tot)
-        cells, hsps, hits = (float(x) for x in tot.tolist())
+        total_ms, (cells, hsps, hits) = reduce_over_ranks(dist, dev, total_ms,
+                                                          [cells, hsps, hits])
 
     secs = total_ms / 1e3
     gcups = cells / secs / 1e9
