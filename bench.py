@@ -54,6 +54,9 @@ def args_parse():
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = 10 Mb)")
     ap.add_argument("--lane-cap", type=int, default=0)
     ap.add_argument("--tile-hits", type=int, default=0)
+    ap.add_argument("--walk-mode", type=int, default=None,
+                    help="0: two launches, 1: persistent (default: the library's)")
+    ap.add_argument("--walk-chunk", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -305,8 +308,11 @@ def run_sfe(a, rank, world, local):
     Q = torch.from_numpy(Qa.copy()).to(dev)
     stream = torch.cuda.Stream(device=dev)
     ctx = pkg.Context(local, stream=stream)
+    walk = {} if a.walk_mode is None else {"walk_mode": a.walk_mode}
+    if a.walk_chunk:
+        walk["walk_chunk"] = a.walk_chunk
     params = pkg.default_params(flags=pkg.TIME_STAGES, lane_cap=a.lane_cap,
-                                tile_hits=a.tile_hits)
+                                tile_hits=a.tile_hits, **walk)
     cap = 1 << 22
     out = torch.zeros((cap, 5), dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
@@ -380,7 +386,8 @@ def run_sfe(a, rank, world, local):
         "config": {"workload": a.workload, "seed": a.seed, "tlen": pair.tlen, "qlen": pair.qlen,
                    "seed_pattern": "1110100110010101111", "transition": 1, "strands": 2,
                    "scores": "HOXD70", "xdrop": 910, "hsp_thresh": 3000,
-                   "lane_cap": a.lane_cap or "default", "parallelism": f"replicas{world}",
+                   "lane_cap": a.lane_cap or "default", "walk": walk or "default",
+                   "parallelism": f"replicas{world}",
                    "l2": "256 MiB write between steps, outside the per-step events",
                    "input": "ASCII bytes resident in HBM"},
         "hsps_per_s": hsps / secs, "hits_per_s": hits / secs,
@@ -441,7 +448,7 @@ def run_sfe(a, rank, world, local):
         Th = torch.from_numpy(Ta.copy()).pin_memory()
         Qh = torch.from_numpy(Qa.copy()).pin_memory()
         hout = np.zeros(cap, dtype=pkg.HSP_DTYPE)
-        pe = pkg.default_params(lane_cap=a.lane_cap, tile_hits=a.tile_hits)
+        pe = pkg.default_params(lane_cap=a.lane_cap, tile_hits=a.tile_hits, **walk)
         ctx.run(Th, Qh, pe, out=hout)  # warm the host path
         ts = []
         e_cells = 0

@@ -112,8 +112,8 @@ typedef struct {
     int32_t lane_cap;         /* bases per side a lane extends before handing the diagonal to a warp; 0 = default */
     int32_t lanes_per_sm;     /* lane-tier threads per SM sharing a tile's hits (sizes their hit ranges); 0 = default */
     int64_t tile_hits;        /* hits per query tile (bounds scratch memory); 0 = default (2^30) */
-    int32_t walk_chunk;       /* hits a lane takes per grab from the work counter; 0 = default (32) */
-    int32_t walk_mode;        /* SFE_WALK_TWO_LAUNCHES (default) or SFE_WALK_PERSISTENT */
+    int32_t walk_chunk;       /* hits a lane takes per grab from the work counter; 0 = 32 */
+    int32_t walk_mode;        /* SFE_WALK_PERSISTENT or SFE_WALK_TWO_LAUNCHES */
     int32_t walk_schedule;    /* order in which the persistent walk hands out chunks (SFE_SCHED_*);
                                  anything but SFE_SCHED_NATURAL needs SFE_WALK_PERSISTENT */
     int32_t ext_log_every;    /* log about 1 in ext_log_every extensions (0: no log) */
@@ -164,7 +164,8 @@ typedef struct {
 } sfe_stats;
 
 /* Fill *p with the defaults: 12of19 with one transition, both strands,
- * HOXD70 scores, X = 910, hsp_thresh = 3000. Returns SFE_OK. */
+ * HOXD70 scores, X = 910, hsp_thresh = 3000, the persistent walk with chunks
+ * of 64 hits. Returns SFE_OK. */
 int sfe_params_default(sfe_params *p);
 
 const char *sfe_strerror(int code);

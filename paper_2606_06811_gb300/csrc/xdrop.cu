@@ -126,19 +126,28 @@ __device__ __forceinline__ uint32_t rev2(uint32_t x) {
 
 __device__ __forceinline__ uint32_t diag_of(uint64_t h) { return (uint32_t)(h >> 32); }
 
-// First index j in [i, n) whose diagonal word differs from `d` (hits are sorted
-// by diagonal word, so this is an upper bound search).
+// First index j > i whose diagonal word differs from `d`, the word of hits[i]
+// (hits are sorted by diagonal word). Diagonals are short, so the search
+// gallops from i (i + 1, i + 2, i + 4, ...: a few nearby loads) before it
+// bisects, instead of bisecting the whole array.
 __device__ __forceinline__ uint32_t segment_end(const uint64_t *__restrict__ hits, uint32_t i,
                                                 uint32_t n, uint32_t d) {
-    uint32_t lo = i, hi = n;
-    while (lo < hi) {
-        uint32_t mid = lo + (hi - lo) / 2;
-        if (diag_of(hits[mid]) <= d)
-            lo = mid + 1;
-        else
-            hi = mid;
+    uint32_t lo = i, hi, step = 1;  // diag(hits[lo]) <= d
+    while (true) {
+        hi = (n - lo > step) ? lo + step : n;
+        if (hi >= n || diag_of(hits[hi]) > d) break;
+        lo = hi;
+        step <<= 1;
     }
-    return lo;
+    uint32_t a = lo + 1, b = hi;  // the first index in (lo, hi] with a larger word
+    while (a < b) {
+        const uint32_t mid = a + (b - a) / 2;
+        if (diag_of(hits[mid]) <= d)
+            a = mid + 1;
+        else
+            b = mid;
+    }
+    return a;
 }
 
 // Score of the seed span [t, t + span) from a table of pair sums: entry
@@ -284,7 +293,7 @@ __device__ void warp_walk_diagonal(const uint64_t *__restrict__ hits, uint32_t n
 // work on different hits and diagonals. A side that passes `lane_cap` bases
 // hands the rest of its diagonal to the warp tier.
 template <bool PACKED, bool BATCH, bool PERSIST>
-__global__ void __launch_bounds__(W_BLOCK) walk_lanes_kernel(const uint64_t *__restrict__ hits,
+__global__ void __launch_bounds__(W_BLOCK, PERSIST ? 1 : 0) walk_lanes_kernel(const uint64_t *__restrict__ hits,
                                                              uint32_t n, uint32_t chunk,
                                                              WalkParams wp) {
     __shared__ int lut[16];

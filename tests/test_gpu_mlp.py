@@ -57,7 +57,7 @@ def test_extension_log_is_every_extension_of_the_oracle(pkg, ctx, tiny):
     p, ref = tiny
     want = {(int(e["strand"]), int(e["t"]), int(e["q"]), int(e["rscored"]), int(e["lscored"]))
             for e in ref.ext}
-    for kw in ({}, {"lane_cap": 1}, {"walk_mode": pkg.WALK_PERSISTENT},
+    for kw in ({}, {"lane_cap": 1}, {"walk_mode": pkg.WALK_TWO_LAUNCHES},
                {"walk_mode": pkg.WALK_PERSISTENT, "walk_schedule": pkg.SCHED_RANDOM,
                 "walk_chunk": 4}):
         recs, st = ext_records(pkg, ctx, p.T, p.Q, 1, **kw)
@@ -71,7 +71,8 @@ def test_sampled_log_does_not_depend_on_the_schedule(pkg, ctx, tiny):
     p, ref = tiny
     base = None
     P_ = pkg.WALK_PERSISTENT
-    for kw in ({}, {"lane_cap": 8}, {"walk_mode": P_, "walk_schedule": pkg.SCHED_LARGEST_FIRST},
+    for kw in ({}, {"walk_mode": pkg.WALK_TWO_LAUNCHES, "lane_cap": 8},
+               {"walk_mode": P_, "walk_schedule": pkg.SCHED_LARGEST_FIRST},
                {"walk_mode": P_, "walk_schedule": pkg.SCHED_RANDOM}):
         recs, st = ext_records(pkg, ctx, p.T, p.Q, 7, **kw)
         s = rec_set(recs.cpu().numpy())
@@ -187,7 +188,8 @@ def test_bad_records_and_missing_model_are_rejected(pkg, ctx, torch, tiny):
         ctx.run(p.T, p.Q, pkg.default_params(input_codes=1, walk_mode=pkg.WALK_PERSISTENT,
                                              walk_schedule=pkg.SCHED_PREDICTED))
     with pytest.raises(pkg.SfeError):  # a schedule orders the persistent walk only
-        ctx.run(p.T, p.Q, pkg.default_params(input_codes=1, walk_schedule=pkg.SCHED_RANDOM))
+        ctx.run(p.T, p.Q, pkg.default_params(input_codes=1, walk_mode=pkg.WALK_TWO_LAUNCHES,
+                                             walk_schedule=pkg.SCHED_RANDOM))
 
 
 @pytest.fixture(scope="module")
