@@ -67,7 +67,7 @@ def args_parse():
                     help="generator seed of the predictor's training pair")
     ap.add_argument("--log-every", type=int, default=20,
                     help="extension log sampling of the training run (1 in N)")
-    ap.add_argument("--learned-chunk", type=int, default=128)
+    ap.add_argument("--learned-chunk", type=int, default=64)
     ap.add_argument("--workload", default="plain_pair_10mb",
                     choices=["plain_pair_10mb", "batch_pairs", "large_pair_100mb"],
                     help="batch_pairs: 4096 uneven pairs, eager and as a replayed CUDA graph "
@@ -420,17 +420,6 @@ def run_sfe(a, rank, world, local):
         l_cells = sum(x["cells"] for x in lst)
         same = (lrecs[-1][3] == plain_out.shape[0] and
                 torch.equal(out[: lrecs[-1][3]], plain_out))
-        # the same persistent walk in hit order: what the predicted order changes
-        np_ = pkg.default_params(flags=pkg.TIME_STAGES, lane_cap=a.lane_cap,
-                                 tile_hits=a.tile_hits, walk_mode=pkg.WALK_PERSISTENT,
-                                 walk_chunk=a.learned_chunk)
-        for _ in range(a.warmup):
-            step(np_)
-        torch.cuda.synchronize()
-        nrecs = [step(np_) for _ in range(a.steps)]
-        torch.cuda.synchronize()
-        n_ms = [e0.elapsed_time(e1) for e0, e1, _, _ in nrecs]
-        n_cells = sum(st["cells"] for _, _, st, _ in nrecs)
         line["learned_binned"] = {
             "value": l_cells / (sum(l_ms) / 1e3) / 1e9, "unit": "GCUPS",
             "ms_per_step": sum(l_ms) / a.steps,
@@ -439,8 +428,6 @@ def run_sfe(a, rank, world, local):
             "walk": f"persistent, chunks of {a.learned_chunk} hits ordered by predicted work",
             "stage_ms": {k: round(sum(x["stage_ms"][k] for x in lst) / a.steps, 4)
                          for k in pkg.STAGES},
-            "persistent_hit_order": {"value": n_cells / (sum(n_ms) / 1e3) / 1e9,
-                                     "ms_per_step": sum(n_ms) / a.steps},
             "predictor": dict(info, **predictor_r2(a, pkg, ctx, pred, pair)),
         }
 

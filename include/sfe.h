@@ -334,7 +334,9 @@ int sfe_mlp_loss_grad(sfe_ctx *ctx, const sfe_mlp_data *data, const float *param
 
 /*
  * Predictions of the FP16 inference model (sfe_mlp_pack) for every sample,
- * into preds (device, n floats) in record order.
+ * into preds (device, n floats) in record order. They run on the tensor cores
+ * (FP16 inputs, FP32 accumulation), so the first layer's hidden units are
+ * rounded to FP16 before the second layer.
  */
 int sfe_mlp_predict(sfe_ctx *ctx, const sfe_mlp_data *data, const void *model, float *preds);
 

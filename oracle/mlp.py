@@ -133,6 +133,17 @@ def adam_step(theta, g, m, v, lr: float, step: int, b1=0.9, b2=0.999, eps=1e-8):
     return theta - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
+def forward_fp16(theta, X) -> np.ndarray:
+    """The inference model as the tensor cores compute it: weights rounded to
+    IEEE half, and the hidden units of the first layer rounded to half after
+    the ReLU (they are the half-precision inputs of the second product); sums
+    in float64 here (float32 on the device)."""
+    P = unpack(fp16_weights(theta))
+    h1 = np.maximum(X @ P["W1"] + P["b1"], 0.0).astype(np.float16).astype(np.float64)
+    h2 = np.maximum(h1 @ P["W2"] + P["b2"], 0.0)
+    return h2 @ P["W3"] + P["b3"]
+
+
 def fp16_weights(theta) -> np.ndarray:
     """The inference model's parameters: weights rounded to IEEE half (nearest,
     ties to even), biases kept."""

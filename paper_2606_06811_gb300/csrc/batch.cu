@@ -31,7 +31,6 @@ namespace sfe {
 
 namespace {
 
-constexpr int MAX_PROBES = MAX_WEIGHT + 1;
 
 // Halves of the care positions: A = the first weight / 2 (the key's high
 // groups), B = the rest (its low groups). Table keys are left-aligned to

@@ -241,85 +241,266 @@ __global__ void pack_kernel16(const float *__restrict__ P, __half *__restrict__ 
         w16[i] = __float2half_rn(P[i]);
 }
 
-// Predicted work of each chunk of hits for the learned schedule: the mean of
-// exp(prediction) over two hits of the chunk (its first and its middle hit),
-// times the chunk's hit count. One warp per chunk; FP16 weights, FP32
-// accumulation. Key: (~cost, chunk) so an ascending sort puts the most work
-// first.
-__global__ void __launch_bounds__(MLP_BLOCK) chunk_predict_kernel(
-    const uint64_t *__restrict__ hits, uint32_t n, uint32_t chunk, uint32_t nchunks,
-    WalkParams wp, const __half *__restrict__ w16, const float *__restrict__ b32,
-    uint64_t *__restrict__ keys) {
-    const int lane = threadIdx.x & 31;
-    const long long k = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    if (k >= nchunks) return;
-    if (wp.nd) n = (uint32_t)min((unsigned long long)n, *wp.nd);
-    const uint32_t i0 = (uint32_t)k * chunk;
-    if ((unsigned long long)i0 >= n) {  // past a device-side hit count: last
-        if (lane == 0) keys[k] = (0xFFFFFFFFull << 32) | (uint32_t)k;
-        return;
+// ---------------------------------------------------------------------------
+// Inference on the tensor cores (mma.sync m16n8k16, FP16 inputs, FP32
+// accumulation). One warp evaluates 16 samples: layer 1 is the dense product
+// of the 16 x 256 one-hot inputs with W1 (16 k-steps x 8 n-tiles), layer 2
+// the product of the 16 x 64 hidden activations, rounded to FP16, with W2 (4 x
+// 8); the accumulator fragments of layer 1 are, register for register, the
+// input fragments of layer 2. Weights sit in shared memory transposed (one row
+// per hidden unit) with 8 halves of padding, so the eight rows a fragment load
+// touches fall in different banks.
+constexpr int MMA_WARPS = 4, MMA_BLOCK = MMA_WARPS * 32;
+constexpr int W1T_LD = IN + 8, W2T_LD = H + 8;
+
+struct MmaSmem {
+    __half w1t[H * W1T_LD];
+    __half w2t[H * W2T_LD];
+    float b1[H], b2[H], w3[H];
+    float b3;
+    unsigned long long cls[MMA_WARPS][16][2];  // per sample, per flank: 32 classes (2 bits)
+    uint32_t valid[MMA_WARPS][16][2];          // per sample, per flank: columns inside
+};
+
+__device__ void mma_load_weights(MmaSmem &sm, const __half *__restrict__ w16,
+                                 const float *__restrict__ b32) {
+    for (int i = threadIdx.x; i < IN * H; i += blockDim.x)  // W1[k][n] -> w1t[n][k]
+        sm.w1t[(i % H) * W1T_LD + i / H] = w16[OFF_W1 + i];
+    for (int i = threadIdx.x; i < H * H; i += blockDim.x)
+        sm.w2t[(i % H) * W2T_LD + i / H] = w16[OFF_W2 + i];
+    for (int i = threadIdx.x; i < H; i += blockDim.x) {
+        sm.b1[i] = b32[OFF_B1 + i];
+        sm.b2[i] = b32[OFF_B2 + i];
+        sm.w3[i] = __half2float(w16[OFF_W3 + i]);
     }
-    const uint32_t len = min(chunk, n - i0);
-    float cost = 0.f;
-    int used = 0;
-    for (int j = 0; j < 2; j++) {
-        const uint32_t i = i0 + (uint32_t)((len * (uint32_t)j) / 2u);
-        if (j > 0 && i == i0) continue;
-        const uint64_t h = hits[i];
-        const uint32_t word = (uint32_t)(h >> 32);
-        const long long t = (long long)(uint32_t)h;
-        sfe_ext_record r;
-        long long D, qlen;
-        if (wp.pairs) {
-            r.pair = (int)(word >> (wp.dbits + 1));
-            r.strand = (int)((word >> wp.dbits) & 1u);
-            D = (long long)(word & ((1u << wp.dbits) - 1u));
-            qlen = wp.pairs[r.pair].qlen;
-        } else {
-            r.pair = 0;
-            r.strand = wp.strand;
-            D = (long long)(word & 0x7FFFFFFFu);
-            qlen = wp.qlen;
+    if (threadIdx.x == 0) sm.b3 = b32[OFF_B3];
+}
+
+// Classes (T xor Q) of the 32 columns of one flank of a hit, and which of
+// them lie inside both sequences. side 0: t - 32 .. t - 1, side 1: t + span ..
+__device__ __forceinline__ void flank(const uint32_t *__restrict__ T, long long tb, long long tl,
+                                      const uint32_t *__restrict__ Qs, long long qb,
+                                      long long ql, long long t, long long q, int span, int side,
+                                      unsigned long long &cls, uint32_t &valid) {
+    const long long pt = side ? t + span : t - 32, pq = side ? q + span : q - 32;
+    cls = 0;
+    valid = 0;
+    // reads stay inside the padded buffers only for flanks that start within
+    // 32 bases before a sequence and not after its end
+    if (pt < -32 || pt > tl || pq < -32 || pq > ql) return;
+    const unsigned long long tw =
+        (unsigned long long)win16(T, tb + pt) | ((unsigned long long)win16(T, tb + pt + 16) << 32);
+    const unsigned long long qw = (unsigned long long)win16(Qs, qb + pq) |
+                                  ((unsigned long long)win16(Qs, qb + pq + 16) << 32);
+    cls = tw ^ qw;
+    const long long lo = max(0LL, max(-pt, -pq));          // first column inside
+    const long long hi = min(32LL, min(tl - pt, ql - pq));  // one past the last
+    if (hi > lo) valid = (hi >= 32 ? 0xFFFFFFFFu : ((1u << hi) - 1u)) & (0xFFFFFFFFu << lo);
+}
+
+__device__ __forceinline__ uint32_t onehot2(const MmaSmem &sm, int w, int row, int col, int slot) {
+    const int side = col >> 5, i = col & 31;
+    const uint32_t c = (uint32_t)(sm.cls[w][row][side] >> (2 * i)) & 3u;
+    const bool v = (sm.valid[w][row][side] >> i) & 1u;
+    return ((v && c == (uint32_t)slot) ? 0x3C00u : 0u) |  // FP16 1.0 in the low half
+           ((v && c == (uint32_t)slot + 1u) ? 0x3C000000u : 0u);
+}
+
+__device__ __forceinline__ void mma16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t pack_half2(float lo, float hi) {
+    const __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+// The network on the 16 samples whose flanks are in sm.cls[w] / sm.valid[w].
+// Lane l returns the predictions of samples l / 4 and l / 4 + 8 (every lane
+// of a quad holds the same two).
+__device__ __forceinline__ void mma_forward16(const MmaSmem &sm, int w, int lane, float &y_lo,
+                                              float &y_hi) {
+    const int g = lane >> 2, tq = lane & 3;
+    float acc[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+#pragma unroll 2
+    for (int kk = 0; kk < IN / 16; kk++) {
+        const int col0 = kk * 4 + (tq >> 1), slot = (tq & 1) * 2;
+        const uint32_t a0 = onehot2(sm, w, g, col0, slot), a1 = onehot2(sm, w, g + 8, col0, slot);
+        const uint32_t a2 = onehot2(sm, w, g, col0 + 2, slot);
+        const uint32_t a3 = onehot2(sm, w, g + 8, col0 + 2, slot);
+        const int k0 = kk * 16 + tq * 2;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const __half *row = sm.w1t + (j * 8 + g) * W1T_LD + k0;
+            mma16816(acc[j], a0, a1, a2, a3, *reinterpret_cast<const uint32_t *>(row),
+                     *reinterpret_cast<const uint32_t *>(row + 8));
         }
-        r.t = (int)t;
-        r.q = (int)(t - D + qlen - wp.span);
-        // one pair: wp.Q is already the walked strand's query
-        const SampleCtx sc{wp.T, wp.Q, wp.pairs ? wp.Qrc : wp.Q, wp.tlen, wp.qlen, wp.pairs,
-                           wp.span};
-        int in_t, in_q;
-        sample_inputs(sc, r, lane, in_t, in_q);
-        float z1[2], a1[2], z2[2], a2[2];
-        const float y = forward_warp<__half>(w16 + OFF_W1, b32 + OFF_B1, w16 + OFF_W2,
-                                             b32 + OFF_B2, w16 + OFF_W3, b32[OFF_B3], in_t, in_q,
-                                             lane, z1, a1, z2, a2);
-        cost += expf(fminf(y, 20.f));
-        used++;
     }
-    if (lane == 0) {
-        const float work = cost / (float)max(used, 1) * (float)len;
-        const uint32_t qk = (uint32_t)fmaxf(1.f, fminf(work * 16.f, 4.0e9f));
-        keys[k] = ((uint64_t)(0xFFFFFFFFu - qk) << 32) | (uint32_t)k;
+    // bias, ReLU, FP16: the A fragments of layer 2
+    uint32_t h[8][2];
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const int c = j * 8 + tq * 2;
+        h[j][0] = pack_half2(fmaxf(acc[j][0] + sm.b1[c], 0.f), fmaxf(acc[j][1] + sm.b1[c + 1], 0.f));
+        h[j][1] = pack_half2(fmaxf(acc[j][2] + sm.b1[c], 0.f), fmaxf(acc[j][3] + sm.b1[c + 1], 0.f));
+    }
+    float acc2[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; j++) acc2[j][0] = acc2[j][1] = acc2[j][2] = acc2[j][3] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < H / 16; kk++) {
+        const int k0 = kk * 16 + tq * 2;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const __half *row = sm.w2t + (j * 8 + g) * W2T_LD + k0;
+            mma16816(acc2[j], h[2 * kk][0], h[2 * kk][1], h[2 * kk + 1][0], h[2 * kk + 1][1],
+                     *reinterpret_cast<const uint32_t *>(row),
+                     *reinterpret_cast<const uint32_t *>(row + 8));
+        }
+    }
+    float plo = 0.f, phi = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const int c = j * 8 + tq * 2;
+        plo += fmaxf(acc2[j][0] + sm.b2[c], 0.f) * sm.w3[c] +
+               fmaxf(acc2[j][1] + sm.b2[c + 1], 0.f) * sm.w3[c + 1];
+        phi += fmaxf(acc2[j][2] + sm.b2[c], 0.f) * sm.w3[c] +
+               fmaxf(acc2[j][3] + sm.b2[c + 1], 0.f) * sm.w3[c + 1];
+    }
+    plo += __shfl_xor_sync(0xffffffffu, plo, 1);
+    plo += __shfl_xor_sync(0xffffffffu, plo, 2);
+    phi += __shfl_xor_sync(0xffffffffu, phi, 1);
+    phi += __shfl_xor_sync(0xffffffffu, phi, 2);
+    y_lo = plo + sm.b3;
+    y_hi = phi + sm.b3;
+}
+
+// A hit's record fields from its walk word.
+__device__ __forceinline__ sfe_ext_record hit_record(uint64_t h, const WalkParams &wp) {
+    const uint32_t word = (uint32_t)(h >> 32);
+    sfe_ext_record r;
+    long long D, qlen;
+    if (wp.pairs) {
+        r.pair = (int)(word >> (wp.dbits + 1));
+        r.strand = (int)((word >> wp.dbits) & 1u);
+        D = (long long)(word & ((1u << wp.dbits) - 1u));
+        qlen = wp.pairs[r.pair].qlen;
+    } else {
+        r.pair = 0;
+        r.strand = wp.strand;
+        D = (long long)(word & 0x7FFFFFFFu);
+        qlen = wp.qlen;
+    }
+    r.t = (int)(uint32_t)h;
+    r.q = (int)((long long)(uint32_t)h - D + qlen - wp.span);
+    r.right = r.left = 0;
+    return r;
+}
+
+// Flanks of a record into the warp's sample slot s (lane: s + 16 * side).
+__device__ __forceinline__ void record_flank(MmaSmem &sm, int w, int s, int side,
+                                             const SampleCtx &sc, const sfe_ext_record &r) {
+    long long tb = 0, qb = 0, tl = sc.tlen, ql = sc.qlen;
+    if (sc.pairs) {
+        const PairInfo P = sc.pairs[r.pair];
+        tb = P.toff;
+        qb = r.strand ? P.qoff_rc : P.qoff;
+        tl = P.tlen;
+        ql = P.qlen;
+    }
+    flank(sc.T, tb, tl, r.strand ? sc.Qrc : sc.Q, qb, ql, r.t, r.q, sc.span, side,
+          sm.cls[w][s][side], sm.valid[w][s][side]);
+}
+
+// Predictions of the FP16 model for extension records, 16 per warp.
+__global__ void __launch_bounds__(MMA_BLOCK) mlp_predict_mma(SampleCtx sc,
+                                                             const sfe_ext_record *__restrict__ recs,
+                                                             long long n,
+                                                             const __half *__restrict__ w16,
+                                                             const float *__restrict__ b32,
+                                                             float *__restrict__ preds) {
+    __shared__ MmaSmem sm;
+    mma_load_weights(sm, w16, b32);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long groups = (n + 15) / 16;
+    for (long long grp = blockIdx.x * (long long)MMA_WARPS + w; grp < groups;
+         grp += (long long)gridDim.x * MMA_WARPS) {
+        const long long idx = grp * 16 + (lane & 15);
+        const int side = lane >> 4;
+        if (idx < n) {
+            record_flank(sm, w, lane & 15, side, sc, recs[idx]);
+        } else {
+            sm.cls[w][lane & 15][side] = 0;
+            sm.valid[w][lane & 15][side] = 0;
+        }
+        __syncwarp();
+        float ylo, yhi;
+        mma_forward16(sm, w, lane, ylo, yhi);
+        if ((lane & 3) == 0) {
+            const long long r0 = grp * 16 + (lane >> 2), r1 = r0 + 8;
+            if (r0 < n) preds[r0] = ylo;
+            if (r1 < n) preds[r1] = yhi;
+        }
+        __syncwarp();
     }
 }
 
-// Predictions of the FP16 inference model, one warp per record.
-__global__ void __launch_bounds__(MLP_BLOCK) mlp_predict16(SampleCtx sc,
-                                                           const sfe_ext_record *__restrict__ recs,
-                                                           long long n,
-                                                           const __half *__restrict__ w16,
-                                                           const float *__restrict__ b32,
-                                                           float *__restrict__ preds) {
-    const int lane = threadIdx.x & 31;
-    const long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    if (s >= n) return;
-    const sfe_ext_record r = recs[s];
-    int in_t, in_q;
-    sample_inputs(sc, r, lane, in_t, in_q);
-    float z1[2], a1[2], z2[2], a2[2];
-    const float y = forward_warp<__half>(w16 + OFF_W1, b32 + OFF_B1, w16 + OFF_W2, b32 + OFF_B2,
-                                         w16 + OFF_W3, b32[OFF_B3], in_t, in_q, lane, z1, a1, z2,
-                                         a2);
-    if (lane == 0) preds[s] = y;
+// Predicted work of each chunk of hits for the learned schedule: exp of the
+// prediction for the chunk's first hit times the chunk's hit count, 16 chunks
+// per warp. Key: (~work, chunk), so an ascending sort puts the most work
+// first; chunks past a device-side hit count get the largest key.
+__global__ void __launch_bounds__(MMA_BLOCK) chunk_predict_mma(
+    const uint64_t *__restrict__ hits, uint32_t n, uint32_t chunk, uint32_t nchunks,
+    WalkParams wp, const __half *__restrict__ w16, const float *__restrict__ b32,
+    uint64_t *__restrict__ keys) {
+    __shared__ MmaSmem sm;
+    mma_load_weights(sm, w16, b32);
+    __syncthreads();
+    if (wp.nd) n = (uint32_t)min((unsigned long long)n, *wp.nd);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // one pair: wp.Q is already the walked strand's query
+    const SampleCtx sc{wp.T, wp.Q, wp.pairs ? wp.Qrc : wp.Q, wp.tlen, wp.qlen, wp.pairs, wp.span};
+    const long long groups = ((long long)nchunks + 15) / 16;
+    for (long long grp = blockIdx.x * (long long)MMA_WARPS + w; grp < groups;
+         grp += (long long)gridDim.x * MMA_WARPS) {
+        const long long k = grp * 16 + (lane & 15);
+        const int side = lane >> 4;
+        const unsigned long long i0 = (unsigned long long)k * chunk;
+        if (k < nchunks && i0 < n) {
+            record_flank(sm, w, lane & 15, side, sc, hit_record(hits[i0], wp));
+        } else {
+            sm.cls[w][lane & 15][side] = 0;
+            sm.valid[w][lane & 15][side] = 0;
+        }
+        __syncwarp();
+        float ylo, yhi;
+        mma_forward16(sm, w, lane, ylo, yhi);
+        if ((lane & 3) == 0) {
+#pragma unroll
+            for (int hsel = 0; hsel < 2; hsel++) {
+                const long long kc = grp * 16 + (lane >> 2) + 8 * hsel;
+                if (kc >= nchunks) continue;
+                const unsigned long long c0 = (unsigned long long)kc * chunk;
+                if (c0 >= n) {
+                    keys[kc] = (0xFFFFFFFFull << 32) | (uint32_t)kc;
+                    continue;
+                }
+                const float len = (float)min((unsigned long long)chunk, n - c0);
+                const float work = expf(fminf(hsel ? yhi : ylo, 20.f)) * len;
+                const uint32_t qk = (uint32_t)fmaxf(1.f, fminf(work * 16.f, 4.0e9f));
+                keys[kc] = ((uint64_t)(0xFFFFFFFFu - qk) << 32) | (uint32_t)kc;
+            }
+        }
+        __syncwarp();
+    }
 }
 
 // A record is usable when its pair and strand exist; positions need no
@@ -367,9 +548,11 @@ cudaError_t launch_mlp_predict16(const uint32_t *T, long long tlen, const uint32
     const __half *w16 = reinterpret_cast<const __half *>(model);
     const float *b32 = reinterpret_cast<const float *>(reinterpret_cast<const char *>(model) +
                                                        ((size_t)NPARAM * 2 + 255) / 256 * 256);
+    const long long groups = (n + 15) / 16;
+    const long long want = (groups + MMA_WARPS - 1) / MMA_WARPS;
     g_launches++;
-    mlp_predict16<<<blocks_for(n * 32, MLP_BLOCK), MLP_BLOCK, 0, st>>>(sc, recs, n, w16, b32,
-                                                                        preds);
+    mlp_predict_mma<<<(unsigned)min(want, 4LL * 152), MMA_BLOCK, 0, st>>>(sc, recs, n, w16, b32,
+                                                                         preds);
     return cudaGetLastError();
 }
 
@@ -403,9 +586,10 @@ cudaError_t launch_chunk_predict(const uint64_t *hits, long long n, uint32_t chu
     const __half *w16 = reinterpret_cast<const __half *>(model);
     const float *b32 = reinterpret_cast<const float *>(reinterpret_cast<const char *>(model) +
                                                        ((size_t)NPARAM * 2 + 255) / 256 * 256);
-    const long long threads = (long long)nchunks * 32;
+    const long long groups = ((long long)nchunks + 15) / 16;
+    const long long want = (groups + MMA_WARPS - 1) / MMA_WARPS;
     g_launches++;
-    chunk_predict_kernel<<<(unsigned)((threads + MLP_BLOCK - 1) / MLP_BLOCK), MLP_BLOCK, 0, st>>>(
+    chunk_predict_mma<<<(unsigned)max(1LL, min(want, 4LL * 152)), MMA_BLOCK, 0, st>>>(
         hits, (uint32_t)n, chunk, nchunks, wp, w16, b32, keys);
     return cudaGetLastError();
 }

@@ -185,3 +185,16 @@ def test_parameter_layout():
     assert P["W1"][1, 0] == 64 and P["b1"][0] == 16384 and P["W2"][0, 1] == 16449
     assert P["b3"] == 20672
     assert np.array_equal(mlp.pack(P), theta)
+
+
+def test_fp16_forward_rounds_weights_and_hidden_units():
+    """forward_fp16 equals forward on half-rounded weights when the hidden
+    units are exact halves (small integers), and differs from it otherwise by
+    at most the rounding of the hidden units."""
+    theta = _counting_net(0.0)  # integer weights and biases
+    T, Qs = _seq(500, 5), _seq(500, 6)
+    X = np.stack([mlp.features(T, Qs, t, q) for t, q in [(40, 20), (200, 3), (90, 90)]])
+    assert np.array_equal(mlp.forward_fp16(theta, X), mlp.forward(theta, X)[0])
+    th, X2, _ = _random_problem(n=8, seed=3)
+    a, b = mlp.forward_fp16(th, X2), mlp.forward(mlp.fp16_weights(th), X2)[0]
+    assert not np.array_equal(a, b) and np.abs(a - b).max() < 0.05
