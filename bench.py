@@ -366,7 +366,10 @@ def run_sfe(a, rank, world, local):
     # dominant kernel: the lane walk (skip + X-drop), integer-ALU bound
     peaks = measured_peaks()
     lane_ms = stage_ms["walk_lanes"] / max(1.0, stage_launch["walk_lanes"])
-    lane_cells = (s0["cells"] - s0["warp_cells"]) / max(1.0, stage_launch["walk_lanes"])
+    # the persistent walk scores the warp tier's cells in the same launch
+    persistent = stage_launch["walk_warps"] == 0
+    lane_cells = (s0["cells"] - (0 if persistent else s0["warp_cells"])) / \
+        max(1.0, stage_launch["walk_lanes"])
     achieved = lane_cells * OPS_PER_CELL / (lane_ms / 1e3) / 1e12
     peak = alu_peak_tops(sm_count, peaks["sm_max_mhz"])
     roofline = {"kernel": "walk_lanes_kernel", "bound": "alu", "achieved": achieved,
