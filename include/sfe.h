@@ -112,7 +112,8 @@ typedef struct {
     int32_t lane_cap;         /* bases per side a lane extends before handing the diagonal to a warp; 0 = default */
     int32_t lanes_per_sm;     /* lane-tier threads per SM sharing a tile's hits (sizes their hit ranges); 0 = default */
     int64_t tile_hits;        /* hits per query tile (bounds scratch memory); 0 = default (2^30) */
-    int32_t walk_chunk;       /* hits a lane takes per grab from the work counter; 0 = 32 */
+    int32_t walk_chunk;       /* hits a lane takes per grab from the work counter; 0 = from the hit
+                                 count (16 to 64, about 8 chunks per resident lane) */
     int32_t walk_mode;        /* SFE_WALK_PERSISTENT or SFE_WALK_TWO_LAUNCHES */
     int32_t walk_schedule;    /* order in which the persistent walk hands out chunks (SFE_SCHED_*);
                                  anything but SFE_SCHED_NATURAL needs SFE_WALK_PERSISTENT */
@@ -122,7 +123,8 @@ typedef struct {
     int64_t ext_log_cap;      /* records the buffer holds (further ones are counted, not written) */
     const void *model;        /* device weights of the work predictor (SFE_SCHED_PREDICTED) */
     int32_t wait_limit;       /* polls of a bounded device wait (the persistent walk's hand-off
-                                 queue) before the call fails with SFE_ETIMEOUT; 0 = default (2^26) */
+                                 queue, at most about 1 us each) before the call fails with
+                                 SFE_ETIMEOUT; 0 = default (2^23) */
     int32_t test_hooks;       /* SFE_TEST_* bits; 0 in normal use */
 } sfe_params;
 
@@ -165,7 +167,7 @@ typedef struct {
 
 /* Fill *p with the defaults: 12of19 with one transition, both strands,
  * HOXD70 scores, X = 910, hsp_thresh = 3000, the persistent walk with chunks
- * of 64 hits. Returns SFE_OK. */
+ * sized from the hit count. Returns SFE_OK. */
 int sfe_params_default(sfe_params *p);
 
 const char *sfe_strerror(int code);

@@ -476,6 +476,7 @@ __global__ void __launch_bounds__(W_BLOCK, PERSIST ? 1 : 0) walk_lanes_kernel(co
             if (e >= wp.queue_cap) break;
             int state = 0;  // 1: entry ready, 2: no entry will come
             long long spins = 0;
+            unsigned backoff = 32;  // ns: a waiting warp leaves the issue slots to working ones
             while (state == 0) {
                 if (lane == 0) {
                     volatile uint4 *qe = wp.queue + e;
@@ -488,6 +489,9 @@ __global__ void __launch_bounds__(W_BLOCK, PERSIST ? 1 : 0) walk_lanes_kernel(co
                         else if (++spins > wp.spin_limit) {
                             status |= ST_TIMEOUT;
                             state = 2;
+                        } else {
+                            __nanosleep(backoff);
+                            backoff = min(backoff * 2u, 1024u);
                         }
                     }
                 }
@@ -759,10 +763,17 @@ cudaError_t launch_persistent_t(const uint64_t *hits, long long n, const WalkPar
     return cudaGetLastError();
 }
 
+uint32_t walk_auto_chunk(long long n) {
+    // about 8 chunks per resident lane (4 CTAs of W_BLOCK per SM), 16 to 64 hits
+    const long long lanes = 4LL * sms() * W_BLOCK;
+    const long long c = (n + 8 * lanes - 1) / (8 * lanes);
+    return (uint32_t)(c < 16 ? 16 : (c > 64 ? 64 : c));
+}
+
 cudaError_t launch_walk_persistent(const uint64_t *hits, long long n, WalkParams wp,
                                    cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    if (wp.chunk == 0) wp.chunk = 32;
+    if (wp.chunk == 0) wp.chunk = walk_auto_chunk(n);
     wp.nchunks = (uint32_t)((n + wp.chunk - 1) / wp.chunk);
     const bool packed = wp.xdrop < PACKED_X_LIMIT, batch = wp.pairs != nullptr;
     if (packed && !batch) return launch_persistent_t<true, false>(hits, n, wp, st);
