@@ -115,6 +115,7 @@ struct sfe_index {
     uint32_t *tp_alloc = nullptr;  // packed target with padding
     uint32_t *offs = nullptr;      // 4^weight + 1
     uint32_t *pos = nullptr;       // tlen - span + 1
+    uint32_t *ncount = nullptr;    // 4^weight: hits of each key's probe set
 };
 
 namespace {
@@ -314,11 +315,14 @@ struct IndexView {
     int transition;
     const uint32_t *offs;
     const uint32_t *pos;
+    const uint32_t *ncount;
 };
 
 // Spaced keys -> stable radix sort -> CSR (offsets, positions).
+// ncount (4^weight entries, may be the arena's bucket counts once the scan is
+// done) receives the hits of every key's probe set under `transition`.
 int build_index(sfe_ctx *c, const uint32_t *T, long long tlen, const SeedPattern &pat,
-                uint32_t *offs, uint32_t *pos) {
+                int transition, uint32_t *offs, uint32_t *pos, uint32_t **ncount_io) {
     const long long npos = std::max(0LL, tlen - pat.span + 1);
     const long long nbuckets = 1LL << (2 * pat.weight);
     uint32_t *counts = nullptr;
@@ -336,6 +340,8 @@ int build_index(sfe_ctx *c, const uint32_t *T, long long tlen, const SeedPattern
         CK(launch_csr_counts(in_b ? kb : ka, npos, counts, pos, c->st));
     }
     CK(scan_u32_to_u32(counts, offs, nbuckets, tmp, c->st));
+    if (!*ncount_io) *ncount_io = counts;  // the per-key counts are no longer needed
+    CK(launch_neighbor_counts(offs, pat, transition, *ncount_io, c->st));
     return SFE_OK;
 }
 
@@ -360,7 +366,7 @@ int count_hits(sfe_ctx *c, const IndexView &ix, const uint32_t *Qs, long long ql
     TRY(ensure_t(c, SL_COUNTS, (size_t)nq, &counts));
     TRY(ensure_t(c, SL_STARTS, (size_t)nq + 1, &starts));
     TRY(ensure(c, SL_TMP, scan_temp_bytes(nq), &tmp));
-    CK(launch_hit_count(Qs, hp, ix.offs, 0, nq, counts, c->st));
+    CK(launch_hit_count(Qs, hp, ix.offs, ix.ncount, 0, nq, counts, c->st));
     CK(scan_u32_to_u64(counts, starts, nq, tmp, c->st));
     CK(cudaMemcpyAsync(total, starts + nq, 8, cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
@@ -657,6 +663,7 @@ int sfe_index_build(sfe_ctx *c, const uint8_t *target, int64_t tlen, const sfe_p
     cudaError_t e = cudaMalloc(&ix->tp_alloc, packed_words(tlen) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&ix->offs, (size_t)(nbuckets + 1) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&ix->pos, (size_t)std::max(1LL, npos) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&ix->ncount, (size_t)nbuckets * 4);
     if (e != cudaSuccess) {
         cudaGetLastError();
         sfe_index_free(ix);
@@ -664,7 +671,8 @@ int sfe_index_build(sfe_ctx *c, const uint8_t *target, int64_t tlen, const sfe_p
     }
     uint32_t *T = nullptr;
     int r = pack_into(c, reinterpret_cast<const uint8_t *>(tdev), tlen, codes, ix->tp_alloc, &T);
-    if (r == SFE_OK) r = build_index(c, T, tlen, pat, ix->offs, ix->pos);
+    if (r == SFE_OK)
+        r = build_index(c, T, tlen, pat, ix->transition, ix->offs, ix->pos, &ix->ncount);
     if (r == SFE_OK) r = sync_small(c);
     if (r == SFE_OK) r = check_status(c->host_small->status);
     if (r != SFE_OK) {
@@ -681,6 +689,7 @@ void sfe_index_free(sfe_index *ix) {
     if (ix->tp_alloc) cudaFree(ix->tp_alloc);
     if (ix->offs) cudaFree(ix->offs);
     if (ix->pos) cudaFree(ix->pos);
+    if (ix->ncount) cudaFree(ix->ncount);
     delete ix;
 }
 
@@ -692,6 +701,7 @@ static IndexView view_of(const sfe_index *ix) {
     v.transition = ix->transition;
     v.offs = ix->offs;
     v.pos = ix->pos;
+    v.ncount = ix->ncount;
     return v;
 }
 
@@ -851,11 +861,12 @@ int sfe_run(sfe_ctx *c, const uint8_t *target, int64_t tlen, const uint8_t *quer
     uint32_t *offs = nullptr, *pos = nullptr;
     TRY(ensure_t(c, SL_OFFS, (size_t)(1LL << (2 * pat.weight)) + 1, &offs));
     TRY(ensure_t(c, SL_POS, (size_t)std::max(1LL, npos), &pos));
+    uint32_t *ncount = nullptr;
     {
         Span sp(c, SFE_STAGE_INDEX);
-        TRY(build_index(c, Tp, tlen, pat, offs, pos));
+        TRY(build_index(c, Tp, tlen, pat, params->transition, offs, pos, &ncount));
     }
-    IndexView v{Tp, tlen, pat, params->transition, offs, pos};
+    IndexView v{Tp, tlen, pat, params->transition, offs, pos, ncount};
 
     const long long tile_hits = params->tile_hits > 0 ? params->tile_hits : kDefaultTileHits;
     const int DB = bits_for(tlen + qlen);

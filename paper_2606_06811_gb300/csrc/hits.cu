@@ -42,6 +42,32 @@ __device__ __forceinline__ int probe_bounds(const uint32_t *__restrict__ Qs, lon
     return nprobe;
 }
 
+// Hits of every key's probe set (the key and, with transitions, its weight
+// transition variants), from the CSR offsets: the count pass then reads one
+// word per query position instead of 1 + weight bucket bounds.
+__global__ void neighbor_count_kernel(const uint32_t *__restrict__ off, int weight,
+                                      int transition, uint32_t *__restrict__ ncount) {
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= (1LL << (2 * weight))) return;
+    uint32_t c = __ldg(off + k + 1) - __ldg(off + k);
+    if (transition)
+        for (int i = 0; i < weight; i++) {
+            const long long p = k ^ (2LL << (2 * i));
+            c += __ldg(off + p + 1) - __ldg(off + p);
+        }
+    ncount[k] = c;
+}
+
+__global__ void __launch_bounds__(BLOCK) hit_count_table_kernel(const uint32_t *__restrict__ Qs,
+                                                                HitParams hp,
+                                                                const uint32_t *__restrict__ ncount,
+                                                                long long q0, long long q1,
+                                                                uint32_t *__restrict__ counts) {
+    long long q = q0 + blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= q1) return;
+    counts[q - q0] = __ldg(ncount + spaced_key(Qs, q, hp.pat));
+}
+
 __global__ void __launch_bounds__(BLOCK) hit_count_kernel(const uint32_t *__restrict__ Qs,
                                                           HitParams hp,
                                                           const uint32_t *__restrict__ off,
@@ -149,11 +175,24 @@ inline unsigned grid_for(long long n) { return (unsigned)((n + BLOCK - 1) / BLOC
 
 }  // namespace
 
+cudaError_t launch_neighbor_counts(const uint32_t *offsets, const SeedPattern &pat,
+                                   int transition, uint32_t *ncount, cudaStream_t st) {
+    g_launches++;
+    neighbor_count_kernel<<<grid_for(1LL << (2 * pat.weight)), BLOCK, 0, st>>>(
+        offsets, pat.weight, transition, ncount);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_hit_count(const uint32_t *Qs, HitParams hp, const uint32_t *offsets,
-                             long long q0, long long q1, uint32_t *counts, cudaStream_t st) {
+                             const uint32_t *ncount, long long q0, long long q1, uint32_t *counts,
+                             cudaStream_t st) {
     if (q1 <= q0) return cudaSuccess;
     g_launches++;
-    hit_count_kernel<<<grid_for(q1 - q0), BLOCK, 0, st>>>(Qs, hp, offsets, q0, q1, counts);
+    if (ncount)
+        hit_count_table_kernel<<<grid_for(q1 - q0), BLOCK, 0, st>>>(Qs, hp, ncount, q0, q1,
+                                                                    counts);
+    else
+        hit_count_kernel<<<grid_for(q1 - q0), BLOCK, 0, st>>>(Qs, hp, offsets, q0, q1, counts);
     return cudaGetLastError();
 }
 

@@ -138,8 +138,13 @@ struct HitParams {
     long long qlen;
     long long qoff;  // qlen - span, so D = t - q + qoff >= 0
 };
+// ncount[k]: hits of key k's probe set (launch_neighbor_counts), or null to
+// count by probing the offsets.
+cudaError_t launch_neighbor_counts(const uint32_t *offsets, const SeedPattern &pat,
+                                   int transition, uint32_t *ncount, cudaStream_t st);
 cudaError_t launch_hit_count(const uint32_t *Qs, HitParams hp, const uint32_t *offsets,
-                             long long q0, long long q1, uint32_t *counts, cudaStream_t st);
+                             const uint32_t *ncount, long long q0, long long q1, uint32_t *counts,
+                             cudaStream_t st);
 // nhits: the hits of [q0, q1) (picks a per-thread or a per-warp writer)
 cudaError_t launch_hit_write(const uint32_t *Qs, HitParams hp, const uint32_t *offsets,
                              const uint32_t *positions, long long q0, long long q1,
