@@ -53,7 +53,7 @@ constexpr int kBatchBucketShift = 1;
 enum Slot {
     SL_TIN, SL_QIN, SL_TP, SL_QP, SL_QM, SL_KEYS_A, SL_KEYS_B, SL_BCOUNT, SL_OFFS, SL_POS,
     SL_COUNTS, SL_STARTS, SL_HITS_A, SL_HITS_B, SL_QUEUE, SL_PAIRS, SL_BENTRIES, SL_SCHED,
-    SL_HSPS, SL_TMP, SL_ECARRY, SL_PUB, SL_BOUNDS, SL_BSLOTS, NSLOT
+    SL_HSPS, SL_TMP, SL_ECARRY, SL_PUB, SL_BOUNDS, SL_BSLOTS, SL_OFF2, SL_POS2, NSLOT
 };
 
 // Small device block: scores, counters and flags of one call.
@@ -116,6 +116,8 @@ struct sfe_index {
     uint32_t *offs = nullptr;      // 4^weight + 1
     uint32_t *pos = nullptr;       // tlen - span + 1
     uint32_t *ncount = nullptr;    // 4^weight: hits of each key's probe set
+    uint32_t *off2 = nullptr;      // merged probe-set lists (optional): 4^weight + 1
+    uint32_t *pos2 = nullptr;      //   and (1 + weight) x positions
 };
 
 namespace {
@@ -316,13 +318,28 @@ struct IndexView {
     const uint32_t *offs;
     const uint32_t *pos;
     const uint32_t *ncount;
+    const uint32_t *off2, *pos2;  // merged probe-set lists, or null
 };
+
+// Entries of the merged probe-set lists: every position is read by the probe
+// sets of 1 + weight keys (the relation "is a probe of" is symmetric). They
+// are kept while they fit u32 offsets and a memory budget.
+long long merged_entries(const SeedPattern &pat, int transition, long long tlen) {
+    const long long npos = std::max(0LL, tlen - pat.span + 1);
+    return (transition ? pat.weight + 1 : 1) * npos;
+}
+bool use_merged(const SeedPattern &pat, int transition, long long tlen) {
+    const long long m = merged_entries(pat, transition, tlen);
+    return m < (1LL << 32) - 1 && m * 4 <= (16LL << 30);
+}
 
 // Spaced keys -> stable radix sort -> CSR (offsets, positions).
 // ncount (4^weight entries, may be the arena's bucket counts once the scan is
 // done) receives the hits of every key's probe set under `transition`.
+// off2 / pos2 (optional) receive the merged probe-set lists.
 int build_index(sfe_ctx *c, const uint32_t *T, long long tlen, const SeedPattern &pat,
-                int transition, uint32_t *offs, uint32_t *pos, uint32_t **ncount_io) {
+                int transition, uint32_t *offs, uint32_t *pos, uint32_t **ncount_io,
+                uint32_t *off2 = nullptr, uint32_t *pos2 = nullptr) {
     const long long npos = std::max(0LL, tlen - pat.span + 1);
     const long long nbuckets = 1LL << (2 * pat.weight);
     uint32_t *counts = nullptr;
@@ -342,6 +359,10 @@ int build_index(sfe_ctx *c, const uint32_t *T, long long tlen, const SeedPattern
     CK(scan_u32_to_u32(counts, offs, nbuckets, tmp, c->st));
     if (!*ncount_io) *ncount_io = counts;  // the per-key counts are no longer needed
     CK(launch_neighbor_counts(offs, pat, transition, *ncount_io, c->st));
+    if (off2 && pos2) {
+        CK(scan_u32_to_u32(*ncount_io, off2, nbuckets, tmp, c->st));
+        CK(launch_merged_fill(offs, pos, pat, transition, off2, pos2, c->st));
+    }
     return SFE_OK;
 }
 
@@ -664,6 +685,12 @@ int sfe_index_build(sfe_ctx *c, const uint8_t *target, int64_t tlen, const sfe_p
     if (e == cudaSuccess) e = cudaMalloc(&ix->offs, (size_t)(nbuckets + 1) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&ix->pos, (size_t)std::max(1LL, npos) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&ix->ncount, (size_t)nbuckets * 4);
+    if (e == cudaSuccess && use_merged(pat, ix->transition, tlen)) {
+        e = cudaMalloc(&ix->off2, (size_t)(nbuckets + 1) * 4);
+        if (e == cudaSuccess)
+            e = cudaMalloc(&ix->pos2,
+                           (size_t)std::max(1LL, merged_entries(pat, ix->transition, tlen)) * 4);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         sfe_index_free(ix);
@@ -672,7 +699,8 @@ int sfe_index_build(sfe_ctx *c, const uint8_t *target, int64_t tlen, const sfe_p
     uint32_t *T = nullptr;
     int r = pack_into(c, reinterpret_cast<const uint8_t *>(tdev), tlen, codes, ix->tp_alloc, &T);
     if (r == SFE_OK)
-        r = build_index(c, T, tlen, pat, ix->transition, ix->offs, ix->pos, &ix->ncount);
+        r = build_index(c, T, tlen, pat, ix->transition, ix->offs, ix->pos, &ix->ncount,
+                        ix->off2, ix->pos2);
     if (r == SFE_OK) r = sync_small(c);
     if (r == SFE_OK) r = check_status(c->host_small->status);
     if (r != SFE_OK) {
@@ -690,6 +718,8 @@ void sfe_index_free(sfe_index *ix) {
     if (ix->offs) cudaFree(ix->offs);
     if (ix->pos) cudaFree(ix->pos);
     if (ix->ncount) cudaFree(ix->ncount);
+    if (ix->off2) cudaFree(ix->off2);
+    if (ix->pos2) cudaFree(ix->pos2);
     delete ix;
 }
 
@@ -702,6 +732,8 @@ static IndexView view_of(const sfe_index *ix) {
     v.offs = ix->offs;
     v.pos = ix->pos;
     v.ncount = ix->ncount;
+    v.off2 = ix->off2;
+    v.pos2 = ix->pos2;
     return v;
 }
 
@@ -750,7 +782,8 @@ int sfe_seed_hits(sfe_ctx *c, const sfe_index *ix, const uint8_t *query, int64_t
         hp.transition = v.transition;
         hp.qlen = qlen;
         hp.qoff = qlen - v.pat.span;
-        CK(launch_hit_write(s ? Qm : Qp, hp, v.offs, v.pos, 0, nq, starts, 0, t2, ha, c->st));
+        CK(launch_hit_write(s ? Qm : Qp, hp, v.offs, v.pos, v.off2, v.pos2, 0, nq, starts, 0, t2, ha,
+                            c->st));
         bool in_b = false;
         CK(radix_sort(ha, hb, nullptr, nullptr, (long long)t2, 32, 32 + DB, tmp, &in_b, &c->small->status, c->st));
         CK(launch_hits_to_public(in_b ? hb : ha, (long long)t2, s, hp.qoff, dst + at, c->st));
@@ -861,12 +894,17 @@ int sfe_run(sfe_ctx *c, const uint8_t *target, int64_t tlen, const uint8_t *quer
     uint32_t *offs = nullptr, *pos = nullptr;
     TRY(ensure_t(c, SL_OFFS, (size_t)(1LL << (2 * pat.weight)) + 1, &offs));
     TRY(ensure_t(c, SL_POS, (size_t)std::max(1LL, npos), &pos));
-    uint32_t *ncount = nullptr;
+    uint32_t *ncount = nullptr, *off2 = nullptr, *pos2 = nullptr;
+    if (use_merged(pat, params->transition, tlen)) {
+        TRY(ensure_t(c, SL_OFF2, (size_t)(1LL << (2 * pat.weight)) + 1, &off2));
+        TRY(ensure_t(c, SL_POS2,
+                     (size_t)std::max(1LL, merged_entries(pat, params->transition, tlen)), &pos2));
+    }
     {
         Span sp(c, SFE_STAGE_INDEX);
-        TRY(build_index(c, Tp, tlen, pat, params->transition, offs, pos, &ncount));
+        TRY(build_index(c, Tp, tlen, pat, params->transition, offs, pos, &ncount, off2, pos2));
     }
-    IndexView v{Tp, tlen, pat, params->transition, offs, pos, ncount};
+    IndexView v{Tp, tlen, pat, params->transition, offs, pos, ncount, off2, pos2};
 
     const long long tile_hits = params->tile_hits > 0 ? params->tile_hits : kDefaultTileHits;
     const int DB = bits_for(tlen + qlen);
@@ -935,8 +973,8 @@ int sfe_run(sfe_ctx *c, const uint8_t *target, int64_t tlen, const uint8_t *quer
                 tiles_total++;
                 {
                     Span sp(c, SFE_STAGE_WRITE);
-                    CK(launch_hit_write(Qs, hp, offs, pos, qb[k], qb[k + 1], starts + qb[k], hb[k],
-                                        (unsigned long long)nh, ha, c->st));
+                    CK(launch_hit_write(Qs, hp, offs, pos, v.off2, v.pos2, qb[k], qb[k + 1],
+                                        starts + qb[k], hb[k], (unsigned long long)nh, ha, c->st));
                 }
                 bool in_b = false;
                 {

@@ -171,6 +171,83 @@ __global__ void __launch_bounds__(BLOCK) hit_write_warp_kernel(
     }
 }
 
+// Merged probe-set lists: for every key, the positions of all the buckets its
+// probe set reads, back to back (probe order, then bucket order), so writing
+// the hits of a query position copies one contiguous range.
+__global__ void merged_fill_kernel(const uint32_t *__restrict__ off,
+                                   const uint32_t *__restrict__ pos, int weight, int transition,
+                                   const uint32_t *__restrict__ off2, uint32_t *__restrict__ pos2) {
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= (1LL << (2 * weight))) return;
+    uint32_t o = off2[k];
+    const int nprobe = transition ? weight + 1 : 1;
+    for (int i = 0; i < nprobe; i++) {
+        const long long p = i == 0 ? k : (k ^ (2LL << (2 * (i - 1))));
+        for (uint32_t j = __ldg(off + p); j < __ldg(off + p + 1); j++) pos2[o++] = __ldg(pos + j);
+    }
+}
+
+__global__ void __launch_bounds__(BLOCK) hit_write_merged_kernel(
+    const uint32_t *__restrict__ Qs, HitParams hp, const uint32_t *__restrict__ off2,
+    const uint32_t *__restrict__ pos2, long long q0, long long q1,
+    const unsigned long long *__restrict__ starts, unsigned long long base,
+    uint64_t *__restrict__ hits) {
+    long long q = q0 + blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= q1) return;
+    const uint32_t k = spaced_key(Qs, q, hp.pat);
+    const uint32_t a = __ldg(off2 + k), b = __ldg(off2 + k + 1);
+    unsigned long long o = starts[q - q0] - base;
+    const long long dq = hp.qoff - q;  // D = t + dq
+    for (uint32_t j = a; j < b; j++) {
+        const uint32_t t = __ldg(pos2 + j);
+        __stcs(reinterpret_cast<unsigned long long *>(hits) + o++,
+               (unsigned long long)make_hit((uint32_t)(t + dq), t));
+    }
+}
+
+// The per-warp writer over merged lists: one range per lane, so an output slot
+// needs only the search for its lane.
+__global__ void __launch_bounds__(BLOCK) hit_write_merged_warp_kernel(
+    const uint32_t *__restrict__ Qs, HitParams hp, const uint32_t *__restrict__ off2,
+    const uint32_t *__restrict__ pos2, long long q0, long long q1,
+    const unsigned long long *__restrict__ starts, unsigned long long base,
+    uint64_t *__restrict__ hits) {
+    __shared__ uint32_t s_a[HW_WARPS][32];
+    __shared__ uint32_t s_o[HW_WARPS][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long qw = q0 + (blockIdx.x * (long long)blockDim.x) + w * 32;
+    if (qw >= q1) return;
+    const long long q = qw + lane;
+    uint32_t a = 0, c = 0;
+    if (q < q1) {
+        const uint32_t k = spaced_key(Qs, q, hp.pat);
+        a = __ldg(off2 + k);
+        c = __ldg(off2 + k + 1) - a;
+    }
+    uint32_t incl = c;  // a warp's hits lie in one query tile (checked: < 2^32)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    s_a[w][lane] = a;
+    s_o[w][lane] = incl - c;
+    if (lane == 31) s_o[w][32] = incl;
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    const unsigned long long wbase = starts[qw - q0] - base;
+    __syncwarp();
+    for (uint32_t k = lane; k < total; k += 32) {
+        int L = 0;  // last lane whose range starts at or before k
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+            if (s_o[w][L + step] <= k) L += step;
+        const uint32_t t = __ldg(pos2 + s_a[w][L] + (k - s_o[w][L]));
+        const long long dq = hp.qoff - (qw + L);
+        __stcs(reinterpret_cast<unsigned long long *>(hits) + wbase + k,
+               (unsigned long long)make_hit((uint32_t)(t + dq), t));
+    }
+}
+
 inline unsigned grid_for(long long n) { return (unsigned)((n + BLOCK - 1) / BLOCK); }
 
 }  // namespace
@@ -196,12 +273,31 @@ cudaError_t launch_hit_count(const uint32_t *Qs, HitParams hp, const uint32_t *o
     return cudaGetLastError();
 }
 
+cudaError_t launch_merged_fill(const uint32_t *offsets, const uint32_t *positions,
+                               const SeedPattern &pat, int transition, const uint32_t *off2,
+                               uint32_t *pos2, cudaStream_t st) {
+    g_launches++;
+    merged_fill_kernel<<<grid_for(1LL << (2 * pat.weight)), BLOCK, 0, st>>>(
+        offsets, positions, pat.weight, transition, off2, pos2);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_hit_write(const uint32_t *Qs, HitParams hp, const uint32_t *offsets,
-                             const uint32_t *positions, long long q0, long long q1,
+                             const uint32_t *positions, const uint32_t *off2,
+                             const uint32_t *pos2, long long q0, long long q1,
                              const unsigned long long *starts, unsigned long long base,
                              unsigned long long nhits, uint64_t *hits, cudaStream_t st) {
     if (q1 <= q0) return cudaSuccess;
     g_launches++;
+    if (off2) {
+        if (nhits >= 32ull * (unsigned long long)(q1 - q0))
+            hit_write_merged_warp_kernel<<<grid_for(q1 - q0), BLOCK, 0, st>>>(
+                Qs, hp, off2, pos2, q0, q1, starts, base, hits);
+        else
+            hit_write_merged_kernel<<<grid_for(q1 - q0), BLOCK, 0, st>>>(Qs, hp, off2, pos2, q0,
+                                                                         q1, starts, base, hits);
+        return cudaGetLastError();
+    }
     // measured: ~10 hits per position (the 10 Mb pair) is faster per thread,
     // ~95 (the 100 Mb pair's repeats) per warp
     if (nhits >= 32ull * (unsigned long long)(q1 - q0))

@@ -145,9 +145,16 @@ cudaError_t launch_neighbor_counts(const uint32_t *offsets, const SeedPattern &p
 cudaError_t launch_hit_count(const uint32_t *Qs, HitParams hp, const uint32_t *offsets,
                              const uint32_t *ncount, long long q0, long long q1, uint32_t *counts,
                              cudaStream_t st);
-// nhits: the hits of [q0, q1) (picks a per-thread or a per-warp writer)
+// Merged probe-set lists (off2: exclusive scan of the probe-set sizes, 4^weight
+// + 1 entries; pos2: their positions back to back).
+cudaError_t launch_merged_fill(const uint32_t *offsets, const uint32_t *positions,
+                               const SeedPattern &pat, int transition, const uint32_t *off2,
+                               uint32_t *pos2, cudaStream_t st);
+// nhits: the hits of [q0, q1) (picks a per-thread or a per-warp writer);
+// off2 / pos2: merged lists, or null to read the probes' buckets
 cudaError_t launch_hit_write(const uint32_t *Qs, HitParams hp, const uint32_t *offsets,
-                             const uint32_t *positions, long long q0, long long q1,
+                             const uint32_t *positions, const uint32_t *off2,
+                             const uint32_t *pos2, long long q0, long long q1,
                              const unsigned long long *starts, unsigned long long base,
                              unsigned long long nhits, uint64_t *hits, cudaStream_t st);
 
