@@ -113,7 +113,7 @@ typedef struct {
     int32_t lanes_per_sm;     /* lane-tier threads per SM sharing a tile's hits (sizes their hit ranges); 0 = default */
     int64_t tile_hits;        /* hits per query tile (bounds scratch memory); 0 = default (2^30) */
     int32_t walk_chunk;       /* hits a lane takes per grab from the work counter; 0 = from the hit
-                                 count (16 to 256, about 8 chunks per resident lane) */
+                                 count (16 to 256, about 16 chunks per resident lane) */
     int32_t walk_mode;        /* SFE_WALK_PERSISTENT or SFE_WALK_TWO_LAUNCHES */
     int32_t walk_schedule;    /* order in which the persistent walk hands out chunks (SFE_SCHED_*);
                                  anything but SFE_SCHED_NATURAL needs SFE_WALK_PERSISTENT */

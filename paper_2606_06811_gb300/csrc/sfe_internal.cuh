@@ -227,7 +227,7 @@ cudaError_t launch_walk_warps(const uint64_t *hits, long long n, WalkParams wp, 
 // SFE_SCHED_PREDICTED ranks chunks with the work predictor `model`.
 size_t walk_schedule_temp_bytes(long long n, uint32_t chunk);
 // Hits per chunk of the persistent walk when the caller leaves it to the
-// library: about 8 chunks per resident lane, 16 to 256 hits.
+// library: about 16 chunks per resident lane, 16 to 256 hits.
 uint32_t walk_auto_chunk(long long n);
 cudaError_t launch_walk_schedule(const uint64_t *hits, long long n, const WalkParams &wp,
                                  int schedule, const void *model, void *tmp, uint32_t **order,

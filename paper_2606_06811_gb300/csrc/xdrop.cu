@@ -764,11 +764,12 @@ cudaError_t launch_persistent_t(const uint64_t *hits, long long n, const WalkPar
 }
 
 uint32_t walk_auto_chunk(long long n) {
-    // about 8 chunks per resident lane (4 CTAs of W_BLOCK per SM), 16 to 256
+    // about 16 chunks per resident lane (4 CTAs of W_BLOCK per SM), 16 to 256
     // hits (measured: 100 Mb pair tiles of ~1e9 hits walk 1.6% faster with
-    // 256 than with 64; a 3 Mb pair needs 16 for the counter to balance lanes)
+    // 256 than with 64, the 10 Mb pair slower with 81 than with 32-64, and a
+    // 3 Mb pair needs 16 for the counter to balance the lanes)
     const long long lanes = 4LL * sms() * W_BLOCK;
-    const long long c = (n + 8 * lanes - 1) / (8 * lanes);
+    const long long c = (n + 16 * lanes - 1) / (16 * lanes);
     return (uint32_t)(c < 16 ? 16 : (c > 256 ? 256 : c));
 }
 
