@@ -200,14 +200,17 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_scatter(
         unsigned *myh = wh + w * (R + 1);
 #pragma unroll
         for (int j = 0; j < RS_ITEMS; j++) {
-            unsigned peers = __match_any_sync(0xffffffffu, dg[j]);
-            unsigned lt = peers & ((1u << lane) - 1u);
-            unsigned cnt = myh[dg[j]];
-            rk[j] = cnt + __popc(lt);
-            __syncwarp();
-            if (lt == 0) myh[dg[j]] = cnt + __popc(peers);
-            __syncwarp();
+            // the digit's lowest lane adds the group's size and shares the old
+            // count; the next item's atomics follow this item's shuffle, so
+            // the ranks keep the item order (a stable ranking)
+            const unsigned peers = __match_any_sync(0xffffffffu, dg[j]);
+            const int leader = __ffs(peers) - 1;
+            unsigned old = 0;
+            if (lane == leader) old = atomicAdd(myh + dg[j], (unsigned)__popc(peers));
+            old = __shfl_sync(0xffffffffu, old, leader);
+            rk[j] = old + __popc(peers & ((1u << lane) - 1u));
         }
+        __syncwarp();
         __syncthreads();
         // per digit: exclusive prefix across warps, tile totals
         for (int d = tid; d <= R; d += RS_BLOCK) {
