@@ -396,7 +396,9 @@ def run_sfe(a, rank, world, local):
         "hsps_per_s": hsps / secs, "hits_per_s": hits / secs,
         "per_step": {"cells": s0["cells"], "hits": s0["hits"], "extended": s0["extended"],
                      "hsps": recs[0][3], "warp_tasks": s0["warp_tasks"],
-                     "warp_cells": s0["warp_cells"], "tiles": s0["tiles"]},
+                     "warp_cells": s0["warp_cells"], "tiles": s0["tiles"],
+                     "shadow_cells": s0["shadow_cells"],
+                     "shadow_fraction": s0["shadow_cells"] / max(1, s0["cells"])},
         "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "dominant_stage": dom,
         "roofline": roofline,

@@ -161,6 +161,9 @@ typedef struct {
     int64_t tiles;      /* query tiles processed */
     int64_t launches;   /* kernels this call launched */
     int64_t ext_logged; /* extensions selected for the log (may exceed ext_log_cap) */
+    int64_t shadow_cells; /* work done twice: the cells a lane scored on an extension before it
+                             handed the diagonal to the warp tier, which scores it again (not in
+                             cells) */
     double stage_ms[SFE_NSTAGES];        /* device time per stage (with SFE_TIME_STAGES) */
     int64_t stage_launches[SFE_NSTAGES]; /* kernels launched per stage (with SFE_TIME_STAGES) */
 } sfe_stats;

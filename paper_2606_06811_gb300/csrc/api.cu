@@ -551,6 +551,7 @@ void fill_stats(const Small &s, sfe_stats *st, long long hits, long long tiles) 
     st->warp_tasks = (int64_t)s.ctr.warp_tasks;
     st->warp_cells = (int64_t)s.ctr.warp_cells;
     st->ext_logged = (int64_t)s.ctr.ext_logged;
+    st->shadow_cells = (int64_t)s.ctr.shadow;
     st->tiles = tiles;
 }
 

@@ -43,6 +43,7 @@ struct DevCounters {
     unsigned long long warp_tasks; // queue entries
     unsigned long long warp_cells; // cells scored by the warp tier
     unsigned long long ext_logged; // extensions selected for the extension log
+    unsigned long long shadow;     // lane cells of extensions handed to the warp tier
     unsigned int status;
     unsigned int pad;
 };

@@ -228,6 +228,7 @@ extern "C" int sfe_ungapped_xdrop_static(const uint8_t *target, int64_t tlen,
         stats->lane_tasks = (int64_t)hs.ctr.lane_tasks;
         stats->warp_tasks = (int64_t)hs.ctr.warp_tasks;
         stats->warp_cells = (int64_t)hs.ctr.warp_cells;
+        stats->shadow_cells = (int64_t)hs.ctr.shadow;
         stats->tiles = 1;
     }
     if ((long long)hs.ctr.hsps > cap) return SFE_EOVERFLOW;

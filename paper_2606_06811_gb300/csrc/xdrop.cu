@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(W_BLOCK, PERSIST ? 1 : 0) walk_lanes_kernel(co
     long long t = 0, q = 0;
     int E = INT_MIN, cap = wp.lane_cap, ravail = 0, lavail = 0;
     LaneSide R{0, 0, 0, 0, true}, L{0, 0, 0, 0, true};
-    unsigned long long ext = 0, cells = 0, tasks = 0;
+    unsigned long long ext = 0, cells = 0, tasks = 0, shadow = 0;
     uint32_t status = 0;
 
     while (true) {
@@ -441,6 +441,7 @@ __global__ void __launch_bounds__(W_BLOCK, PERSIST ? 1 : 0) walk_lanes_kernel(co
                     wp.queue[slot] = make_uint4(i, (uint32_t)E, 0u, 0u);
                 }
                 handed = true;
+                shadow += (unsigned long long)(span + R.n + L.n);  // the warp scores it again
                 i = segment_end(hits, i, n, D);
                 cur = i < n ? hits[i] : ~0ull;
                 in_seg = false;
@@ -455,6 +456,7 @@ __global__ void __launch_bounds__(W_BLOCK, PERSIST ? 1 : 0) walk_lanes_kernel(co
         ext += __shfl_down_sync(0xffffffffu, ext, o);
         cells += __shfl_down_sync(0xffffffffu, cells, o);
         tasks += __shfl_down_sync(0xffffffffu, tasks, o);
+        shadow += __shfl_down_sync(0xffffffffu, shadow, o);
         status |= __shfl_down_sync(0xffffffffu, status, o);
     }
     const int lane = threadIdx.x & 31;
@@ -462,6 +464,7 @@ __global__ void __launch_bounds__(W_BLOCK, PERSIST ? 1 : 0) walk_lanes_kernel(co
         if (ext) atomicAdd(&wp.ctr->extended, ext);
         if (cells) atomicAdd(&wp.ctr->cells, cells);
         if (tasks) atomicAdd(&wp.ctr->lane_tasks, tasks);
+        if (shadow) atomicAdd(&wp.ctr->shadow, shadow);
     }
     if (PERSIST) {
         // this warp's lanes are out of work: consume the hand-off queue

@@ -54,12 +54,12 @@ class Stats(C.Structure):
     _fields_ = [("hits", C.c_int64), ("extended", C.c_int64), ("cells", C.c_int64),
                 ("hsps", C.c_int64), ("lane_tasks", C.c_int64), ("warp_tasks", C.c_int64),
                 ("warp_cells", C.c_int64), ("tiles", C.c_int64), ("launches", C.c_int64),
-                ("ext_logged", C.c_int64),
+                ("ext_logged", C.c_int64), ("shadow_cells", C.c_int64),
                 ("stage_ms", C.c_double * len(STAGES)),
                 ("stage_launches", C.c_int64 * len(STAGES))]
 
     def as_dict(self) -> dict:
-        d = {k: int(getattr(self, k)) for k, _ in self._fields_[:10]}
+        d = {k: int(getattr(self, k)) for k, _ in self._fields_[:11]}
         d["stage_ms"] = {n: float(self.stage_ms[i]) for i, n in enumerate(STAGES)}
         d["stage_launches"] = {n: int(self.stage_launches[i]) for i, n in enumerate(STAGES)}
         return d

@@ -68,6 +68,13 @@ def test_lane_cap_does_not_change_output(pkg, ctx, lane_cap):
     p = synth.tiny_pair(2, length=60_000, n_blocks=15)
     got, st, ref = run_both(pkg, ctx, p.T, p.Q, lane_cap=lane_cap)
     assert_same(got, st, ref)
+    # shadow work: what lanes scored on the extensions they handed to warps,
+    # at most the seed span plus both sides up to the cap and one window more
+    if lane_cap < (1 << 30):
+        assert st["warp_tasks"] > 0 and st["shadow_cells"] > 0
+        assert st["shadow_cells"] <= st["warp_tasks"] * (19 + 2 * (lane_cap + 16))
+    else:
+        assert st["shadow_cells"] == 0
 
 
 @pytest.mark.parametrize("tile_hits", [1, 777, 5000])
