@@ -161,6 +161,21 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_offsets(unsigned *__restrict__ co
     }
 }
 
+// Asynchronous copy of a tile's keys (count <= RS_TILE) into shared memory,
+// 16 bytes per copy, the ragged end zero-filled; the scatter issues it for
+// the next tile while it ranks and writes the current one. The keys must be
+// 16-byte aligned (checked by the host).
+__device__ __forceinline__ void rs_prefetch(uint64_t *dst, const uint64_t *src, unsigned count) {
+    for (unsigned c = threadIdx.x; 2 * c < count; c += RS_BLOCK) {
+        const unsigned bytes = (2 * c + 1 < count) ? 16u : 8u;
+        const unsigned saddr = (unsigned)__cvta_generic_to_shared(dst + 2 * c);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr),
+                     "l"(src + 2 * c), "r"(bytes)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 template <bool VALS, int R, bool DEVN>
 __global__ void __launch_bounds__(RS_BLOCK) rs_scatter(
     const uint64_t *__restrict__ kin, uint64_t *__restrict__ kout,
@@ -169,7 +184,8 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_scatter(
     const unsigned *__restrict__ offsets, int G) {
     if (DEVN) rs_device_count(nd, G, n, chunk);
     extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t *sk = reinterpret_cast<uint64_t *>(smem);                     // RS_TILE
+    uint64_t *sraw = reinterpret_cast<uint64_t *>(smem);                   // RS_TILE: next tile
+    uint64_t *sk = sraw + RS_TILE;                                          // RS_TILE
     unsigned *sv = reinterpret_cast<unsigned *>(sk + RS_TILE);              // RS_TILE (VALS)
     unsigned *wh = sv + (VALS ? RS_TILE : 0);                               // RS_WARPS*(R+1)
     unsigned *tcount = wh + RS_WARPS * (R + 1);                          // R+1
@@ -180,10 +196,12 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_scatter(
     const long long beg = (long long)blockIdx.x * chunk;
     const long long end = min(n, beg + chunk);
     for (int d = tid; d < R; d += RS_BLOCK) run[d] = offsets[(long long)d * G + blockIdx.x];
+    if (beg < end) rs_prefetch(sraw, kin + beg, (unsigned)min((long long)RS_TILE, end - beg));
 
     for (long long tb = beg; tb < end; tb += RS_TILE) {
         const unsigned tile_n = (unsigned)min((long long)RS_TILE, end - tb);
         for (int i = tid; i < RS_WARPS * (R + 1); i += RS_BLOCK) wh[i] = 0;
+        asm volatile("cp.async.wait_group 0;" ::: "memory");  // this tile's keys have landed
         __syncthreads();
 
         uint64_t k[RS_ITEMS];
@@ -193,10 +211,14 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_scatter(
         for (int j = 0; j < RS_ITEMS; j++) {
             unsigned e = wbase + j * 32 + lane;
             bool valid = e < tile_n;
-            k[j] = valid ? kin[tb + e] : ~0ull;
+            k[j] = valid ? sraw[e] : ~0ull;
             if (VALS) v[j] = valid ? vin[tb + e] : 0u;
             dg[j] = valid ? ((unsigned)(k[j] >> shift) & mask) : (unsigned)R;
         }
+        __syncthreads();  // every thread has its keys: the buffer takes the next tile
+        if (tb + RS_TILE < end)
+            rs_prefetch(sraw, kin + tb + RS_TILE,
+                        (unsigned)min((long long)RS_TILE, end - (tb + RS_TILE)));
         unsigned *myh = wh + w * (R + 1);
 #pragma unroll
         for (int j = 0; j < RS_ITEMS; j++) {
@@ -265,7 +287,7 @@ __global__ void __launch_bounds__(RS_BLOCK) rs_scatter(
 }
 
 size_t rs_smem(bool vals, int R) {
-    return (size_t)RS_TILE * 8 + (vals ? (size_t)RS_TILE * 4 : 0) +
+    return 2 * (size_t)RS_TILE * 8 + (vals ? (size_t)RS_TILE * 4 : 0) +
            (size_t)RS_WARPS * (R + 1) * 4 + 2 * (size_t)(R + 1) * 4 + (size_t)R * 4;
 }
 
@@ -439,6 +461,9 @@ cudaError_t radix_sort_dev(uint64_t *keys_a, uint64_t *keys_b, uint32_t *vals_a,
     *result_in_b = false;
     if (hi <= lo || n <= 0 || (n <= 1 && !nd)) return cudaSuccess;
     if (n >= (1LL << 32)) return cudaErrorInvalidValue;
+    // the scatter copies keys 16 bytes at a time
+    if ((reinterpret_cast<uintptr_t>(keys_a) | reinterpret_cast<uintptr_t>(keys_b)) & 15)
+        return cudaErrorInvalidValue;
     RsGeom g = rs_geom(n);
     unsigned *counts = reinterpret_cast<unsigned *>(tmp);
     unsigned *totals = counts + (size_t)RS_R * g.G;
