@@ -185,6 +185,13 @@ int sfe_ctx_set_stream(sfe_ctx *ctx, void *stream);
  * the context's scratch arena fail as if the device were out of memory, so
  * the calls that need them return SFE_ENOMEM. n = 0 clears it. */
 int sfe_ctx_fail_next_allocs(sfe_ctx *ctx, int32_t n);
+/* Test hook (no counterpart in the paper): the library's stable LSD radix
+ * sort on n 64-bit keys in device memory, ordered by bits [lo, hi) (0 <= lo <
+ * hi <= 64), in place; with device_count != 0 the count is first copied to
+ * the device and the sort runs in the form a captured batch uses (grids for n,
+ * count read on the device). Keys must be 16-byte aligned. */
+int sfe_test_radix_sort(sfe_ctx *ctx, uint64_t *keys, int64_t n, int32_t lo, int32_t hi,
+                        int32_t device_count);
 void sfe_ctx_destroy(sfe_ctx *ctx);
 
 /*

@@ -635,6 +635,32 @@ int sfe_ctx_create(int device, sfe_ctx **out) {
     return SFE_OK;
 }
 
+int sfe_test_radix_sort(sfe_ctx *c, uint64_t *keys, int64_t n, int32_t lo, int32_t hi,
+                        int32_t device_count) {
+    TRY(begin(c));
+    if (n < 0 || n >= (1LL << 32) || lo < 0 || hi > 64 || lo >= hi)
+        return fail(SFE_EINVAL, "bad count or bit range");
+    if (n > 0 && !is_device_ptr(keys)) return fail(SFE_EINVAL, "keys must be device memory");
+    if (n <= 1) return SFE_OK;
+    uint64_t *other = nullptr;
+    void *tmp = nullptr;
+    unsigned long long *nd = nullptr;
+    TRY(ensure_t(c, SL_HITS_B, (size_t)n, &other));
+    TRY(ensure(c, SL_TMP, radix_sort_temp_bytes(n), &tmp));
+    if (device_count) {
+        TRY(ensure_t(c, SL_BOUNDS, 1, &nd));
+        const unsigned long long hn = (unsigned long long)n;
+        CK(cudaMemcpyAsync(nd, &hn, 8, cudaMemcpyHostToDevice, c->st));
+    }
+    bool in_b = false;
+    CK(radix_sort_dev(keys, other, nullptr, nullptr, n, nd, lo, hi, tmp, &in_b,
+                      &c->small->status, c->st));
+    if (in_b)
+        CK(cudaMemcpyAsync(keys, other, (size_t)n * 8, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return SFE_OK;
+}
+
 int sfe_ctx_fail_next_allocs(sfe_ctx *c, int32_t n) {
     if (!c || n < 0) return fail(SFE_EINVAL, "bad context or count");
     c->fail_allocs = n;

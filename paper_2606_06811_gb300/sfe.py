@@ -85,6 +85,8 @@ def lib() -> C.CDLL:
         L.sfe_ctx_create.argtypes = [C.c_int, C.POINTER(vp)]
         L.sfe_ctx_set_stream.argtypes = [vp, vp]
         L.sfe_ctx_fail_next_allocs.argtypes = [vp, i32]
+        L.sfe_test_radix_sort.argtypes = [vp, vp, i64, i32, i32, i32]
+        L.sfe_test_radix_sort.restype = C.c_int
         L.sfe_ctx_fail_next_allocs.restype = C.c_int
         L.sfe_ctx_destroy.argtypes = [vp]
         L.sfe_ctx_destroy.restype = None
@@ -189,6 +191,13 @@ class Context:
 
     def set_stream(self, stream) -> None:
         _check(lib().sfe_ctx_set_stream(self.h, _stream_handle(stream)))
+
+    def test_radix_sort(self, keys, lo: int, hi: int, device_count: bool = False) -> None:
+        """Test hook: the library's stable radix sort of a device tensor of int64 keys
+        by bits [lo, hi), in place."""
+        ptr, nbytes, keep = _buf(keys)
+        _check(lib().sfe_test_radix_sort(self.h, ptr, nbytes // 8, int(lo), int(hi),
+                                         int(bool(device_count))))
 
     def fail_next_allocs(self, n: int) -> None:
         """Test hook: the next n scratch allocations fail with SFE_ENOMEM."""
