@@ -219,7 +219,9 @@ def run_reference(a, rank, world):
     if rank != 0:
         return 0
     pair, _, _ = make_workload(a.seed, a.scale)
-    per = max(2.0, a.cpu_seconds / max(1, a.steps + a.warmup))
+    # at least 6 s per step: each sample indexes the full target once, and a
+    # query prefix of a few hundred kb keeps that cost from dominating
+    per = max(6.0, a.cpu_seconds / max(1, a.steps + a.warmup))
     cells = hsps = hits = 0
     secs = 0.0
     qlen = 0
