@@ -57,6 +57,8 @@ def args_parse():
     ap.add_argument("--walk-mode", type=int, default=None,
                     help="0: two launches, 1: persistent (default: the library's)")
     ap.add_argument("--walk-chunk", type=int, default=0)
+    ap.add_argument("--no-cell-planes", action="store_true",
+                    help="lane windows read the 2-bit words (an ablation)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -313,7 +315,8 @@ def run_sfe(a, rank, world, local):
     walk = {} if a.walk_mode is None else {"walk_mode": a.walk_mode}
     if a.walk_chunk:
         walk["walk_chunk"] = a.walk_chunk
-    params = pkg.default_params(flags=pkg.TIME_STAGES, lane_cap=a.lane_cap,
+    base_flags = pkg.TIME_STAGES | (pkg.NO_CELL_PLANES if a.no_cell_planes else 0)
+    params = pkg.default_params(flags=base_flags, lane_cap=a.lane_cap,
                                 tile_hits=a.tile_hits, **walk)
     cap = 1 << 22
     out = torch.zeros((cap, 5), dtype=torch.int32, device=dev)
@@ -392,6 +395,7 @@ def run_sfe(a, rank, world, local):
                    "seed_pattern": "1110100110010101111", "transition": 1, "strands": 2,
                    "scores": "HOXD70", "xdrop": 910, "hsp_thresh": 3000,
                    "lane_cap": a.lane_cap or "default", "walk": walk or "default",
+                   "cell_planes": not a.no_cell_planes,
                    "parallelism": f"replicas{world}",
                    "l2": "256 MiB write between steps, outside the per-step events",
                    "input": "ASCII bytes resident in HBM"},
@@ -413,7 +417,7 @@ def run_sfe(a, rank, world, local):
         # learned-binned arm: persistent walk, chunks ordered by predicted work
         plain_out = out[: recs[0][3]].clone()
         pred, info = train_predictor(a, pkg, ctx, dev)
-        lp = pkg.default_params(flags=pkg.TIME_STAGES, lane_cap=a.lane_cap,
+        lp = pkg.default_params(flags=base_flags, lane_cap=a.lane_cap,
                                 tile_hits=a.tile_hits, walk_mode=pkg.WALK_PERSISTENT,
                                 walk_schedule=pkg.SCHED_PREDICTED, walk_chunk=a.learned_chunk,
                                 model=pred.model.data_ptr())

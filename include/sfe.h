@@ -61,6 +61,10 @@ extern "C" {
 /* sfe_params.flags */
 #define SFE_SKIP_PASSING_ONLY 1 /* advance E only for HSPs with score >= hsp_thresh */
 #define SFE_TIME_STAGES 2       /* time each stage with CUDA events on the context's stream */
+#define SFE_NO_CELL_PLANES 4    /* sfe_run: lane windows read the 2-bit words even where the
+                                   4-bit cell planes (1 byte per base of T and of each query
+                                   strand, built when they take at most 64 MB) would fit; the
+                                   output is the same either way */
 
 /* Stages of a call, indexes of sfe_stats.stage_ms / stage_launches. */
 enum {
@@ -107,7 +111,7 @@ typedef struct {
     int32_t scores[16];       /* scores[4 * target_base + query_base] */
     int32_t xdrop;            /* X >= 0 (and < 2^30) */
     int32_t hsp_thresh;       /* HSPs with score >= hsp_thresh are reported */
-    int32_t flags;            /* SFE_SKIP_PASSING_ONLY */
+    int32_t flags;            /* SFE_SKIP_PASSING_ONLY, SFE_TIME_STAGES, SFE_NO_CELL_PLANES */
     int32_t input_codes;      /* 0: ASCII ACGTacgt, 1: codes 0..3 */
     int32_t lane_cap;         /* bases per side a lane extends before handing the diagonal to a warp; 0 = default */
     int32_t lanes_per_sm;     /* lane-tier threads per SM sharing a tile's hits (sizes their hit ranges); 0 = default */

@@ -186,6 +186,20 @@ __device__ __forceinline__ uint32_t spread8(uint32_t x, uint32_t sel) {
     return (x | (x << 2)) & 0x33333333u;
 }
 
+// Cell planes: a sequence at 4 bits per base, nibble k of word w holding the
+// code of base 8w + k (forward plane) or of base len - 1 - 8w - k (reversed
+// plane); target codes sit in bits 2-3 of their nibble and query codes in
+// bits 0-1, so the OR of a target and a query window is the packed window's
+// table index per cell with no bit shuffling. Sixteen nibbles from base p:
+// three word loads and two funnel shifts. A plane holds ceil(len / 8) + 4
+// words; windows start below len, so the third word is always inside it.
+__device__ __forceinline__ uint2 plane_win16(const uint32_t *__restrict__ P, long long p) {
+    const long long w = p >> 3;
+    const uint32_t sh = (uint32_t)(p & 7) * 4u;
+    const uint32_t a = __ldg(P + w), b = __ldg(P + w + 1), c = __ldg(P + w + 2);
+    return make_uint2(__funnelshift_r(a, b, sh), __funnelshift_r(b, c, sh));
+}
+
 // Largest X for which the packed-key window below cannot overflow int32
 // (scores are limited to |M| <= 2^20).
 constexpr int PACKED_X_LIMIT = 1 << 23;
@@ -204,17 +218,34 @@ constexpr int PACKED_X_LIMIT = 1 << 23;
 // fails. A predicate `on` freezes acc once the side stops. Per cell: one
 // table load, an add under the predicate, a max and a compare folded into the
 // predicate (measured 0.7% faster than multiplying the score by a 0/1 flag).
-template <bool PACKED>
+//
+// PLANES (packed, one pair): the window comes from the cell planes of
+// `wp` instead of the 2-bit words: pt and pq are then positions in the pair's
+// own target and query strand, and a left window reads the reversed planes
+// forward from len - pt + n.
+template <bool PACKED, bool PLANES = false>
 __device__ __forceinline__ void lane_window(const uint32_t *__restrict__ T,
                                             const uint32_t *__restrict__ Q, long long pt,
                                             long long pq, int dir, int avail, int X,
-                                            const int *lut, const int *lut64, LaneSide &sd) {
-    const long long wt = dir > 0 ? pt + sd.n : pt - sd.n - 16;
-    const long long wq = dir > 0 ? pq + sd.n : pq - sd.n - 16;
-    uint32_t tw = win16(T, wt), qw = win16(Q, wq);
-    if (dir < 0) {
-        tw = rev2(tw);
-        qw = rev2(qw);
+                                            const int *lut, const int *lut64, LaneSide &sd,
+                                            const WalkParams &wp) {
+    uint32_t tw = 0, qw = 0;
+    uint2 zp = make_uint2(0u, 0u);
+    if (PLANES) {
+        const uint2 tz = dir > 0 ? plane_win16(wp.TN, pt + sd.n)
+                                 : plane_win16(wp.TNR, wp.tlen - pt + sd.n);
+        const uint2 qz = dir > 0 ? plane_win16(wp.QN, pq + sd.n)
+                                 : plane_win16(wp.QNR, wp.qlen - pq + sd.n);
+        zp = make_uint2(tz.x | qz.x, tz.y | qz.y);
+    } else {
+        const long long wt = dir > 0 ? pt + sd.n : pt - sd.n - 16;
+        const long long wq = dir > 0 ? pq + sd.n : pq - sd.n - 16;
+        tw = win16(T, wt);
+        qw = win16(Q, wq);
+        if (dir < 0) {
+            tw = rev2(tw);
+            qw = rev2(qw);
+        }
     }
     const int lim = avail - sd.n;
     int cnt = 0, a = 1, bj = -1, gain = 0, sum = 0;
@@ -223,8 +254,9 @@ __device__ __forceinline__ void lane_window(const uint32_t *__restrict__ T,
         int acc = -64 * sd.d;
         int bk = 0;  // key of the current maximum
         // table index of cell j (4 * t + q) in nibble j of z[j / 8]
-        const uint32_t z[2] = {spread8(tw, 0x4140u) * 4u + spread8(qw, 0x4140u),
-                               spread8(tw, 0x4342u) * 4u + spread8(qw, 0x4342u)};
+        const uint32_t z[2] = {
+            PLANES ? zp.x : spread8(tw, 0x4140u) * 4u + spread8(qw, 0x4140u),
+            PLANES ? zp.y : spread8(tw, 0x4342u) * 4u + spread8(qw, 0x4342u)};
         if (lim >= 16) {
             bool on = true;
 #pragma unroll
@@ -297,7 +329,7 @@ __device__ void warp_walk_diagonal(const uint64_t *__restrict__ hits, uint32_t n
 // hits finish in one iteration, so the warp stays converged while its lanes
 // work on different hits and diagonals. A side that passes `lane_cap` bases
 // hands the rest of its diagonal to the warp tier.
-template <bool PACKED, bool BATCH, bool PERSIST>
+template <bool PACKED, bool BATCH, bool PERSIST, bool PLANES = false>
 __global__ void __launch_bounds__(W_BLOCK, PERSIST ? 1 : 0) walk_lanes_kernel(const uint64_t *__restrict__ hits,
                                                              uint32_t n, uint32_t chunk,
                                                              WalkParams wp) {
@@ -407,12 +439,13 @@ __global__ void __launch_bounds__(W_BLOCK, PERSIST ? 1 : 0) walk_lanes_kernel(co
         // (2) right sides
         const bool needR = busy && !R.done;
         if (__any_sync(0xffffffffu, needR) && needR)
-            lane_window<PACKED>(wp.T, c.Q, c.tb + t + span, c.qb + q + span, 1, ravail, X, lut,
-                                lut64, R);
+            lane_window<PACKED, PLANES>(wp.T, c.Q, c.tb + t + span, c.qb + q + span, 1, ravail,
+                                        X, lut, lut64, R, wp);
         // (3) left sides
         const bool needL = busy && !L.done;
         if (__any_sync(0xffffffffu, needL) && needL)
-            lane_window<PACKED>(wp.T, c.Q, c.tb + t, c.qb + q, -1, lavail, X, lut, lut64, L);
+            lane_window<PACKED, PLANES>(wp.T, c.Q, c.tb + t, c.qb + q, -1, lavail, X, lut, lut64,
+                                        L, wp);
         if (busy && (R.best > SCORE_LIMIT || L.best > SCORE_LIMIT)) status |= ST_SCORE_OVERFLOW;
         // (4) finish or hand off
         if (busy && R.done && L.done) {
@@ -689,7 +722,9 @@ cudaError_t launch_walk_lanes(const uint64_t *hits, long long n, WalkParams wp, 
     g_launches++;
     const unsigned grid = grid_for(nthreads, W_BLOCK);
     const bool packed = wp.xdrop < PACKED_X_LIMIT, batch = wp.pairs != nullptr;
-    if (packed && !batch)
+    if (packed && !batch && wp.TN)
+        walk_lanes_kernel<true, false, false, true><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, (uint32_t)chunk, wp);
+    else if (packed && !batch)
         walk_lanes_kernel<true, false, false><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, (uint32_t)chunk, wp);
     else if (!packed && !batch)
         walk_lanes_kernel<false, false, false><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, (uint32_t)chunk, wp);
@@ -756,18 +791,18 @@ __global__ void chunk_order_kernel(const uint64_t *__restrict__ keys, uint32_t n
     if (k < nchunks) order[k] = (uint32_t)keys[k];
 }
 
-template <bool PACKED, bool BATCH>
+template <bool PACKED, bool BATCH, bool PLANES = false>
 cudaError_t launch_persistent_t(const uint64_t *hits, long long n, const WalkParams &wp,
                                 cudaStream_t st) {
     // every CTA resident at once: consumers wait on producers of other CTAs
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, walk_lanes_kernel<PACKED, BATCH, true>, W_BLOCK, 0);
+        &per_sm, walk_lanes_kernel<PACKED, BATCH, true, PLANES>, W_BLOCK, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     g_launches++;
-    walk_lanes_kernel<PACKED, BATCH, true><<<per_sm * sms(), W_BLOCK, 0, st>>>(hits, (uint32_t)n,
-                                                                              wp.chunk, wp);
+    walk_lanes_kernel<PACKED, BATCH, true, PLANES><<<per_sm * sms(), W_BLOCK, 0, st>>>(
+        hits, (uint32_t)n, wp.chunk, wp);
     return cudaGetLastError();
 }
 
@@ -787,6 +822,7 @@ cudaError_t launch_walk_persistent(const uint64_t *hits, long long n, WalkParams
     if (wp.chunk == 0) wp.chunk = walk_auto_chunk(n);
     wp.nchunks = (uint32_t)((n + wp.chunk - 1) / wp.chunk);
     const bool packed = wp.xdrop < PACKED_X_LIMIT, batch = wp.pairs != nullptr;
+    if (packed && !batch && wp.TN) return launch_persistent_t<true, false, true>(hits, n, wp, st);
     if (packed && !batch) return launch_persistent_t<true, false>(hits, n, wp, st);
     if (!packed && !batch) return launch_persistent_t<false, false>(hits, n, wp, st);
     if (packed) return launch_persistent_t<true, true>(hits, n, wp, st);

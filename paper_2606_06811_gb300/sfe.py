@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsfe.so")
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW = 0, -1, -2, -3, -4, -5
 SKIP_PASSING_ONLY = 1
 TIME_STAGES = 2
+NO_CELL_PLANES = 4
 WALK_TWO_LAUNCHES, WALK_PERSISTENT = 0, 1
 SCHED_NATURAL, SCHED_LARGEST_FIRST, SCHED_PREDICTED, SCHED_RANDOM = 0, 1, 2, 3
 TEST_UNPUBLISHED_QUEUE_ENTRY = 1

@@ -229,6 +229,24 @@ def test_walk_modes_chunks_and_schedules(pkg, ctx, mode, chunk, sched, cap):
     assert_same(got, st, ref)
 
 
+@pytest.mark.parametrize("n,m", [(19, 19), (20, 27), (33, 41), (9_001, 7_333), (60_007, 40_003)])
+@pytest.mark.parametrize("planes", [True, False])
+def test_cell_planes_and_two_bit_windows_agree(pkg, ctx, n, m, planes):
+    """The lane windows read either the 4-bit cell planes (forward and
+    reversed copies of T and of each query strand) or the 2-bit words; both
+    give the oracle's output, on lengths with ragged ends of the planes'
+    8-base words and of the 2-bit words' 16-base words."""
+    T, Q = _pair(40 + n % 7, n, m, blocks=6)
+    ref = oracle.run(T, Q)
+    flags = 0 if planes else pkg.NO_CELL_PLANES
+    got, st = ctx.run(T, Q, pkg.default_params(input_codes=1, flags=flags, lane_cap=16))
+    assert_same(got, st, ref)
+    # the same with the skip advanced only by passing HSPs
+    ref = oracle.run(T, Q, flags=1)
+    got, st = ctx.run(T, Q, pkg.default_params(input_codes=1, flags=flags | 1))
+    assert_same(got, st, ref)
+
+
 def test_persistent_walk_on_identical_sequences(pkg, ctx):
     st = synth.Stream(32, "ident2")
     T = synth.iid_bases(st, 30_000, 0.5)
