@@ -62,9 +62,9 @@ extern "C" {
 #define SFE_SKIP_PASSING_ONLY 1 /* advance E only for HSPs with score >= hsp_thresh */
 #define SFE_TIME_STAGES 2       /* time each stage with CUDA events on the context's stream */
 #define SFE_NO_CELL_PLANES 4    /* sfe_run: lane windows read the 2-bit words even where the
-                                   4-bit cell planes (1 byte per base of T and of each query
-                                   strand, built when they take at most 64 MB) would fit; the
-                                   output is the same either way */
+                                   4-bit cell planes of T and of each query strand (built
+                                   when they take at most 64 MB) would fit; the output is the
+                                   same either way */
 
 /* Stages of a call, indexes of sfe_stats.stage_ms / stage_launches. */
 enum {

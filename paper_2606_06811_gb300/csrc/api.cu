@@ -49,7 +49,7 @@ constexpr unsigned long long kQueueMax = 1ull << 20;
 // entries per bucket: measured on 4096 pairs, 20.6 ms per batch against 21.2
 // with one bucket per position and 21.2 / 23.8 with 4 / 8 per bucket).
 constexpr int kBatchBucketShift = 1;
-// Cell planes of a single pair (1 byte per base of T and of each query
+// Cell planes of a single pair (half a byte per base of T and of each query
 // strand) are built up to half of the GB300's 126 MB L2.
 constexpr size_t kPlanesMaxBytes = 64ull << 20;
 
@@ -447,7 +447,7 @@ struct WalkSetup {
     int32_t *Ecarry;
     Hsp *hsps;
     unsigned long long hsp_cap;
-    const uint32_t *planes[4] = {nullptr, nullptr, nullptr, nullptr};  // TN, TNR, QN, QNR
+    const uint32_t *planes[2] = {nullptr, nullptr};  // cell planes of T and of Qs
 };
 
 // The lane and warp tiers over hits sorted by (diagonal word, t), in one
@@ -512,9 +512,7 @@ int walk_sorted(sfe_ctx *c, const uint64_t *hits, long long n, const WalkSetup &
     wp.T = ws.T;
     wp.Q = ws.Qs;
     wp.TN = ws.planes[0];
-    wp.TNR = ws.planes[1];
-    wp.QN = ws.planes[2];
-    wp.QNR = ws.planes[3];
+    wp.QN = ws.planes[1];
     wp.tlen = ws.tlen;
     wp.qlen = ws.qlen;
     wp.span = ws.span;
@@ -927,24 +925,22 @@ int sfe_run(sfe_ctx *c, const uint8_t *target, int64_t tlen, const uint8_t *quer
     }
     // cell planes of T and of each query strand for the lane windows, when
     // they fit well inside L2 (the lanes read them at random positions)
-    const uint32_t *planes[2][4] = {};
+    const uint32_t *planes[2][2] = {};
     {
         const size_t tw = plane_words(tlen), qw = plane_words(qlen);
-        const size_t words = 2 * tw + 4 * qw;
+        const size_t words = tw + 2 * qw;
         if (!(params->flags & SFE_NO_CELL_PLANES) && words * 4 <= kPlanesMaxBytes) {
             Span sp(c, SFE_STAGE_PACK);
             uint32_t *pl = nullptr;
             TRY(ensure_t(c, SL_PLANES, words, &pl));
-            uint32_t *tn = pl, *tnr = pl + tw;
-            CK(launch_planes(Tp, tlen, 2, tn, tnr, c->st));
+            uint32_t *tn = pl + PLANE_PAD;
+            CK(launch_plane(Tp, tlen, 2, tn, c->st));
             for (int s = 0; s < 2; s++) {
                 if (!(params->strands & (1 << s))) continue;
-                uint32_t *qn = pl + 2 * tw + 2 * s * qw, *qnr = qn + qw;
-                CK(launch_planes(s ? Qm : Qp, qlen, 0, qn, qnr, c->st));
+                uint32_t *qn = pl + tw + s * qw + PLANE_PAD;
+                CK(launch_plane(s ? Qm : Qp, qlen, 0, qn, c->st));
                 planes[s][0] = tn;
-                planes[s][1] = tnr;
-                planes[s][2] = qn;
-                planes[s][3] = qnr;
+                planes[s][1] = qn;
             }
         }
     }
@@ -1040,7 +1036,8 @@ int sfe_run(sfe_ctx *c, const uint8_t *target, int64_t tlen, const uint8_t *quer
                     CK(radix_sort(ha, hbuf, nullptr, nullptr, nh, 32, 32 + DB, tmp, &in_b, &c->small->status, c->st));
                 }
                 WalkSetup ws{Tp, tlen, Qs, qlen, s, pat.span, params, Ecarry, hd, hcap};
-                for (int k = 0; k < 4; k++) ws.planes[k] = planes[s][k];
+                ws.planes[0] = planes[s][0];
+                ws.planes[1] = planes[s][1];
                 TRY(walk_sorted(c, in_b ? hbuf : ha, nh, ws));
             }
         }

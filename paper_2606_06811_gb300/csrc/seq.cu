@@ -75,40 +75,29 @@ __global__ void revcomp_kernel(const uint32_t *__restrict__ src, long long n,
     dst[w - SEQ_PAD] = out;
 }
 
-// Cell planes of a packed sequence of n bases (layout in WalkParams): word w
-// of the forward plane holds bases 8w..8w+7, word w of the reversed plane
-// bases n-1-8w down to n-8-8w, one per nibble, each code shifted left by
-// `shift`; bases past either end read as 0. A word is one half of a 2-bit
-// word (forward) or a 2-bit window ending at base n-1-8w with its codes in
-// reverse order, spread to nibbles. S must have the packed buffers' padding
-// (the reversed window of the last word starts up to 7 bases before 0).
+// Cell plane of a packed sequence of n bases (layout in WalkParams): word j
+// holds bases 8j..8j+7 (one half of a 2-bit word spread to nibbles), each
+// code shifted left by `shift`; bases past the end and the PLANE_PAD words on
+// either side read as 0. dst is the base 0 pointer.
 __device__ __forceinline__ uint32_t spread_nibbles(uint32_t x) {
     x = (x | (x << 8)) & 0x00FF00FFu;
     x = (x | (x << 4)) & 0x0F0F0F0Fu;
     return (x | (x << 2)) & 0x33333333u;
 }
 
-__global__ void planes_kernel(const uint32_t *__restrict__ S, long long n, int shift,
-                              uint32_t *__restrict__ fwd, uint32_t *__restrict__ rev,
-                              long long nw) {
+__global__ void plane_kernel(const uint32_t *__restrict__ S, long long n, int shift,
+                             uint32_t *__restrict__ dst, long long nw) {
     const long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (w >= nw) return;
-    const long long p = 8 * w;
-    uint32_t f = 0, r = 0;
-    if (p < n) {
+    if (w >= nw + 2 * PLANE_PAD) return;
+    const long long j = w - PLANE_PAD;  // may be negative (front padding)
+    uint32_t f = 0;
+    if (j >= 0 && j < nw) {
+        const long long p = 8 * j;
         const uint32_t h = (__ldg(S + (p >> 4)) >> (16 * ((p >> 3) & 1))) & 0xFFFFu;
-        uint32_t g = __brev(win16(S, n - 8 - p) & 0xFFFFu) >> 16;  // 8 codes, bits reversed
-        g = ((g >> 1) & 0x5555u) | ((g & 0x5555u) << 1);             // codes reversed
         f = spread_nibbles(h) << shift;
-        r = spread_nibbles(g) << shift;
-        if (n - p < 8) {
-            const uint32_t m = (1u << (4 * (n - p))) - 1u;
-            f &= m;
-            r &= m;
-        }
+        if (n - p < 8) f &= (1u << (4 * (n - p))) - 1u;
     }
-    fwd[w] = f;
-    rev[w] = r;
+    dst[j] = f;
 }
 
 __global__ void seed_keys_kernel(const uint32_t *__restrict__ S, long long npos, SeedPattern pat,
@@ -187,13 +176,13 @@ cudaError_t launch_revcomp(const uint32_t *src, long long n, uint32_t *dst, cuda
     return cudaGetLastError();
 }
 
-size_t plane_words(long long n) { return (size_t)((n + 7) / 8) + 4; }
+size_t plane_words(long long n) { return (size_t)((n + 7) / 8) + 2 * PLANE_PAD; }
 
-cudaError_t launch_planes(const uint32_t *S, long long n, int shift, uint32_t *fwd, uint32_t *rev,
-                          cudaStream_t st) {
-    const long long nw = (long long)plane_words(n);
+cudaError_t launch_plane(const uint32_t *S, long long n, int shift, uint32_t *dst,
+                         cudaStream_t st) {
+    const long long nw = (n + 7) / 8;
     g_launches++;
-    planes_kernel<<<grid_for(nw), BLOCK, 0, st>>>(S, n, shift, fwd, rev, nw);
+    plane_kernel<<<grid_for(nw + 2 * PLANE_PAD), BLOCK, 0, st>>>(S, n, shift, dst, nw);
     return cudaGetLastError();
 }
 

@@ -102,10 +102,11 @@ cudaError_t launch_pack(const uint8_t *src, long long n, int codes, uint32_t *ds
                         uint32_t *status, cudaStream_t st);
 // Reverse complement of a packed sequence of n bases into another padded buffer.
 cudaError_t launch_revcomp(const uint32_t *src, long long n, uint32_t *dst, cudaStream_t st);
-// cell planes (forward and reversed, 4 bits per base) of a packed sequence
+// cell plane (4 bits per base, PLANE_PAD zero words on each side) of a packed
+// sequence: plane_words is the allocation, dst the base 0 pointer
+constexpr int PLANE_PAD = 4;
 size_t plane_words(long long n);
-cudaError_t launch_planes(const uint32_t *S, long long n, int shift, uint32_t *fwd, uint32_t *rev,
-                          cudaStream_t st);
+cudaError_t launch_plane(const uint32_t *S, long long n, int shift, uint32_t *dst, cudaStream_t st);
 // keys[p] = (seed key of p) << 32 | p, for p in [0, n - span].
 cudaError_t launch_seed_keys(const uint32_t *S, long long n, SeedPattern pat, uint64_t *keys,
                              cudaStream_t st);
@@ -166,9 +167,9 @@ cudaError_t launch_hit_write(const uint32_t *Qs, HitParams hp, const uint32_t *o
 struct WalkParams {
     const uint32_t *T;   // packed target (base 0)
     const uint32_t *Q;   // packed query strand (base 0)
-    // cell planes of the target and of the query strand, forward and reversed
-    // (4 bits per base; one pair only, nullptr: the walk reads T and Q)
-    const uint32_t *TN, *TNR, *QN, *QNR;
+    // cell planes of the target and of the query strand (4 bits per base,
+    // base 0 pointers; one pair only, nullptr: the walk reads T and Q)
+    const uint32_t *TN, *QN;
     long long tlen, qlen;
     int span;
     int strand;

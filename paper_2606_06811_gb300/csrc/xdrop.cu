@@ -187,12 +187,14 @@ __device__ __forceinline__ uint32_t spread8(uint32_t x, uint32_t sel) {
 }
 
 // Cell planes: a sequence at 4 bits per base, nibble k of word w holding the
-// code of base 8w + k (forward plane) or of base len - 1 - 8w - k (reversed
-// plane); target codes sit in bits 2-3 of their nibble and query codes in
-// bits 0-1, so the OR of a target and a query window is the packed window's
-// table index per cell with no bit shuffling. Sixteen nibbles from base p:
-// three word loads and two funnel shifts. A plane holds ceil(len / 8) + 4
-// words; windows start below len, so the third word is always inside it.
+// code of base 8w + k, target codes in bits 2-3 of their nibble and query
+// codes in bits 0-1, so the OR of a target and a query window is the packed
+// window's table index per cell with no bit shuffling. Sixteen nibbles from
+// base p (p >= -16): three word loads and two funnel shifts. A plane has
+// PLANE_PAD zero words before base 0 and after its last word. A left window
+// reads the 16 bases that end where the side stands and takes their nibbles
+// in reverse order (a constant index per cell), so both sides of a hit read
+// the same lines of the plane.
 __device__ __forceinline__ uint2 plane_win16(const uint32_t *__restrict__ P, long long p) {
     const long long w = p >> 3;
     const uint32_t sh = (uint32_t)(p & 7) * 4u;
@@ -220,9 +222,7 @@ constexpr int PACKED_X_LIMIT = 1 << 23;
 // predicate (measured 0.7% faster than multiplying the score by a 0/1 flag).
 //
 // PLANES (packed, one pair): the window comes from the cell planes of
-// `wp` instead of the 2-bit words: pt and pq are then positions in the pair's
-// own target and query strand, and a left window reads the reversed planes
-// forward from len - pt + n.
+// `wp` instead of the 2-bit words; cell j of a left window is nibble 15 - j.
 template <bool PACKED, bool PLANES = false>
 __device__ __forceinline__ void lane_window(const uint32_t *__restrict__ T,
                                             const uint32_t *__restrict__ Q, long long pt,
@@ -232,10 +232,8 @@ __device__ __forceinline__ void lane_window(const uint32_t *__restrict__ T,
     uint32_t tw = 0, qw = 0;
     uint2 zp = make_uint2(0u, 0u);
     if (PLANES) {
-        const uint2 tz = dir > 0 ? plane_win16(wp.TN, pt + sd.n)
-                                 : plane_win16(wp.TNR, wp.tlen - pt + sd.n);
-        const uint2 qz = dir > 0 ? plane_win16(wp.QN, pq + sd.n)
-                                 : plane_win16(wp.QNR, wp.qlen - pq + sd.n);
+        const uint2 tz = plane_win16(wp.TN, dir > 0 ? pt + sd.n : pt - sd.n - 16);
+        const uint2 qz = plane_win16(wp.QN, dir > 0 ? pq + sd.n : pq - sd.n - 16);
         zp = make_uint2(tz.x | qz.x, tz.y | qz.y);
     } else {
         const long long wt = dir > 0 ? pt + sd.n : pt - sd.n - 16;
@@ -261,7 +259,8 @@ __device__ __forceinline__ void lane_window(const uint32_t *__restrict__ T,
             bool on = true;
 #pragma unroll
             for (int j = 0; j < 16; j++) {
-                const int sc = lut64[(z[j >> 3] >> (4 * (j & 7))) & 15u];
+                const int k = (PLANES && dir < 0) ? 15 - j : j;  // nibble of cell j
+                const int sc = lut64[(z[k >> 3] >> (4 * (k & 7))) & 15u];
                 acc = on ? acc + sc : acc;
                 bk = max(bk, acc);
                 on = on && (acc + thr > bk);
@@ -271,7 +270,8 @@ __device__ __forceinline__ void lane_window(const uint32_t *__restrict__ T,
             bool on = true;
 #pragma unroll
             for (int j = 0; j < 16; j++) {
-                const int sc = lut64[(z[j >> 3] >> (4 * (j & 7))) & 15u];
+                const int k = (PLANES && dir < 0) ? 15 - j : j;
+                const int sc = lut64[(z[k >> 3] >> (4 * (k & 7))) & 15u];
                 on = on && j < lim;
                 acc = on ? acc + sc : acc;
                 bk = max(bk, acc);
