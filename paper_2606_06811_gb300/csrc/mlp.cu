@@ -539,6 +539,19 @@ unsigned blocks_for(long long threads, int block) {
 
 }  // namespace
 
+// Inference grids: four CTAs per SM at most (the kernels stride over sample
+// groups).
+static long long predict_grid(long long want) {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return max(1LL, min(want, 4LL * sms));
+}
+
 cudaError_t launch_mlp_predict16(const uint32_t *T, long long tlen, const uint32_t *Q,
                                  const uint32_t *Qrc, long long qlen, const PairInfo *pairs,
                                  int span, const sfe_ext_record *recs, long long n,
@@ -551,8 +564,8 @@ cudaError_t launch_mlp_predict16(const uint32_t *T, long long tlen, const uint32
     const long long groups = (n + 15) / 16;
     const long long want = (groups + MMA_WARPS - 1) / MMA_WARPS;
     g_launches++;
-    mlp_predict_mma<<<(unsigned)min(want, 4LL * 152), MMA_BLOCK, 0, st>>>(sc, recs, n, w16, b32,
-                                                                         preds);
+    mlp_predict_mma<<<(unsigned)predict_grid(want), MMA_BLOCK, 0, st>>>(sc, recs, n, w16, b32,
+                                                                       preds);
     return cudaGetLastError();
 }
 
@@ -589,7 +602,7 @@ cudaError_t launch_chunk_predict(const uint64_t *hits, long long n, uint32_t chu
     const long long groups = ((long long)nchunks + 15) / 16;
     const long long want = (groups + MMA_WARPS - 1) / MMA_WARPS;
     g_launches++;
-    chunk_predict_mma<<<(unsigned)max(1LL, min(want, 4LL * 152)), MMA_BLOCK, 0, st>>>(
+    chunk_predict_mma<<<(unsigned)predict_grid(want), MMA_BLOCK, 0, st>>>(
         hits, (uint32_t)n, chunk, nchunks, wp, w16, b32, keys);
     return cudaGetLastError();
 }
