@@ -238,7 +238,10 @@ int sfe_ungapped_xdrop(sfe_ctx *ctx, const sfe_index *index, const uint8_t *quer
  * The whole filter stage for one pair: index, hits on the requested strands,
  * skip and X-drop, sorted HSPs. Inputs and outputs host or device; the query
  * is processed in tiles of at most params->tile_hits hits with the skip state
- * carried across tiles, so the result does not depend on the tiling.
+ * carried across tiles, so the result does not depend on the tiling. Scratch
+ * (context-owned, reused by later calls): the index, two hit buffers per
+ * tile, and, unless SFE_NO_CELL_PLANES, 4-bit copies of the target and the
+ * query strands when they take at most 64 MB.
  */
 int sfe_run(sfe_ctx *ctx, const uint8_t *target, int64_t tlen, const uint8_t *query, int64_t qlen,
             const sfe_params *params, sfe_hsp *hsps, int64_t cap, int64_t *nhsps,
