@@ -20,6 +20,18 @@ SRC = os.path.join(os.path.dirname(os.path.dirname(__file__)), "oracle", "sfe_or
 
 # (name, old text, new text, occurrences to replace: 0 = all)
 MUTANTS = [
+    # range edges: the last target or query position, the last base of a side
+    ("last_target_position_dropped", "int64_t nt = tlen - p->span + 1;",
+     "int64_t nt = tlen - p->span;", 1),
+    ("last_query_position_dropped", "for (int64_t q = 0; q + p->span <= qlen; q++) {",
+     "for (int64_t q = 0; q + p->span < qlen; q++) {", 1),
+    ("right_side_stops_one_short", "while (t + span + n < tlen && q + span + n < qlen) {",
+     "while (t + span + n + 1 < tlen && q + span + n < qlen) {", 1),
+    ("left_side_stops_one_short", "while (t - 1 - n >= 0 && q - 1 - n >= 0) {",
+     "while (t - 1 - n >= 1 && q - 1 - n >= 0) {", 1),
+    # seed pattern parsing: the first care position lost
+    ("first_care_position_dropped", "            p->care[p->weight++] = i;",
+     "            if (i > 0) p->care[p->weight++] = i;", 1),
     ("xdrop_ge", "if (best - sum > X)", "if (best - sum >= X)", 0),
     ("latest_argmax", "if (sum > best) {", "if (sum >= best) {", 0),
     ("transversion_tolerated", "k ^ (2u << (2 * (p->weight - j)))",
@@ -61,6 +73,7 @@ def battery() -> dict:
     return {
         "hand": _safe(lambda: all(pins.check_hand_case(c) for c in pins._hand_cases())),
         "hits": _safe(pins.check_hits_bruteforce, 7, 1200, 1000),
+        "hits_identical": _safe(pins.check_hits_adversarial, "identical"),
         "xdrop": _safe(pins.check_xdrop_exhaustive, 3, None, 910, 80),
         "xdrop_asym": _safe(pins.check_xdrop_exhaustive, 1, pins._rand_asym_scores(1), 300, 80),
         "serial": _safe(pins.check_serial_loop, 4, 1500, 1400),

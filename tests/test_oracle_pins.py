@@ -81,8 +81,7 @@ def test_hits_match_bruteforce(pattern, transition, gc):
     assert check_hits_bruteforce(7, 2000, 1500, pattern, transition, gc)
 
 
-@pytest.mark.parametrize("kind", ["polyA", "period19", "identical", "short", "empty"])
-def test_hits_adversarial(kind):
+def _adversarial_pair(kind):
     st = synth.Stream(5, kind)
     if kind == "polyA":
         T = np.zeros(300, np.uint8)
@@ -101,10 +100,24 @@ def test_hits_adversarial(kind):
     else:
         T = np.zeros(0, np.uint8)
         Q = synth.iid_bases(st, 40, 0.5)
+    return T, Q
+
+
+def check_hits_adversarial(kind):
+    """The oracle's hits on a degenerate pair equal the brute force's (identical
+    sequences and repeats put hits on the first and last positions)."""
+    T, Q = _adversarial_pair(kind)
     for Qs in (Q, bf.revcomp(Q)):
         t1, q1 = oracle.seed_hits(T, Qs)
         t2, q2 = bf.hits_by_diagonal(T, Qs, P19, True)
-        assert np.array_equal(t1, t2) and np.array_equal(q1, q2)
+        if not (np.array_equal(t1, t2) and np.array_equal(q1, q2)):
+            return False
+    return True
+
+
+@pytest.mark.parametrize("kind", ["polyA", "period19", "identical", "short", "empty"])
+def test_hits_adversarial(kind):
+    assert check_hits_adversarial(kind)
 
 
 def check_xdrop_exhaustive(seed=3, scores=None, X=910, nhits=300):
