@@ -36,6 +36,19 @@ def test_library_exports_every_declared_symbol(built):
         assert hasattr(lib, n), n
 
 
+def test_every_exported_c_symbol_is_declared(built):
+    """The reverse of the check above: the library exports no sfe_* C function
+    that include/*.h does not declare (names from the symbol table)."""
+    import shutil
+    import subprocess
+    if not shutil.which("nm"):
+        pytest.skip("no nm")
+    out = subprocess.check_output(["nm", "-D", "--defined-only", built]).decode().split("\n")
+    exported = {f[2] for f in (l.split() for l in out) if len(f) == 3 and f[1] == "T"
+                and f[2].startswith("sfe_")}
+    assert exported and exported <= set(declared()), sorted(exported - set(declared()))
+
+
 def test_host_only_calls(built):
     import paper_2606_06811_gb300 as P
     p = P.default_params()
