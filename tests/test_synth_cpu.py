@@ -139,3 +139,26 @@ def test_plain_workload_recipe_at_small_scale():
     for blk in a.blocks:
         assert 1000 <= blk.tlen <= 20_000 and 0.70 <= blk.identity <= 0.90
         assert 0 <= blk.qstart and blk.qstart + blk.qlen <= a.qlen
+
+
+def test_batch_workload_recipe():
+    from synth.workloads import concat_batch
+    pairs = synth.batch_pairs(3, n_pairs=200)
+    assert len(pairs) == 200
+    tl = np.array([p.tlen for p in pairs])
+    assert tl.min() >= 1000 and tl.max() <= 256_000
+    # log-uniform lengths: about half below the geometric mean of the range
+    assert abs(np.mean(tl < math.sqrt(1000 * 256_001)) - 0.5) < 5 * math.sqrt(0.25 / 200)
+    assert all(0.35 <= p.gc <= 0.60 and len(p.blocks) <= 20 for p in pairs)
+    T, toff, Q, qoff = concat_batch(pairs[:5])
+    assert toff[-1] == T.size == sum(p.tlen for p in pairs[:5])
+    assert np.array_equal(T[toff[2]:toff[3]], pairs[2].T)
+    assert np.array_equal(Q[qoff[4]:qoff[5]], pairs[4].Q)
+
+
+def test_large_workload_recipe_at_small_scale():
+    p = synth.large_pair_100mb(5, scale=0.001)
+    assert p.tlen == p.qlen == 100_000 and len(p.blocks) == 20
+    assert abs(np.mean((p.T == 1) | (p.T == 2)) - 0.41) < 0.015
+    for blk in p.blocks:
+        assert 1000 <= blk.tlen <= 50_000 and 0.65 <= blk.identity <= 0.90
