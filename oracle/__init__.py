@@ -73,6 +73,10 @@ def _bind(path: str):
     L.or_run.argtypes = [u8p, C.c_int64, u8p, C.c_int64, C.c_char_p, C.c_int, C.c_int,
                          i32p, C.c_int32, C.c_int32, C.c_int, C.c_int, C.POINTER(C.c_int)]
     L.or_run.restype = C.c_void_p
+    L.or_run_par.argtypes = [u8p, C.c_int64, u8p, C.c_int64, C.c_char_p, C.c_int, C.c_int,
+                             i32p, C.c_int32, C.c_int32, C.c_int, C.c_int64, C.c_int,
+                             C.POINTER(C.c_int)]
+    L.or_run_par.restype = C.c_void_p
     L.or_run_diagonal.argtypes = [u8p, C.c_int64, u8p, C.c_int64, C.c_int, C.c_int64,
                                   C.c_int64, C.c_char_p, C.c_int, i32p, C.c_int32,
                                   C.c_int32, C.c_int, C.c_int, C.POINTER(C.c_int)]
@@ -103,6 +107,23 @@ def lib():
     if _lib is None:
         _lib = _bind(_build.build())
     return _lib
+
+
+# When set, run() computes through the multi-threaded form (or_run_par) with
+# these (qtile, threads); the pin battery runs in both forms.
+_parallel: tuple | None = None
+
+
+@contextlib.contextmanager
+def use_parallel(qtile: int = 0, threads: int = 0):
+    """Route run() through the multi-threaded form of the oracle."""
+    global _parallel
+    saved = _parallel
+    _parallel = (int(qtile), int(threads))
+    try:
+        yield
+    finally:
+        _parallel = saved
 
 
 @contextlib.contextmanager
@@ -196,6 +217,9 @@ def run(T, Q, pattern: str = DEFAULT_PATTERN, transition: bool = True, strands: 
         scores=HOXD70, X: int = XDROP, thresh: int = HSP_THRESH, flags: int = 0,
         keep_log: bool = False) -> Result:
     """The filter stage on one pair: hits -> per-diagonal skip -> X-drop -> sorted HSPs."""
+    if _parallel is not None and not keep_log:
+        return run_par(T, Q, pattern, transition, strands, scores, X, thresh, flags,
+                       qtile=_parallel[0], threads=_parallel[1])
     T, Q = _u8(T), _u8(Q)
     M = _scores(scores)
     err = C.c_int(0)
@@ -203,6 +227,32 @@ def run(T, Q, pattern: str = DEFAULT_PATTERN, transition: bool = True, strands: 
                      int(transition), int(strands), _ptr(M, C.c_int32), int(X), int(thresh),
                      int(flags), int(keep_log), C.byref(err))
     return _collect(h, err, keep_log)
+
+
+def run_par(T, Q, pattern: str = DEFAULT_PATTERN, transition: bool = True, strands: int = 3,
+            scores=HOXD70, X: int = XDROP, thresh: int = HSP_THRESH, flags: int = 0,
+            qtile: int = 0, threads: int = 0) -> Result:
+    """run() on several threads (or_run_par): query tiles of qtile positions
+    (0: one tile), the skip state carried across tiles, blocks of diagonals
+    walked in parallel; threads 0 = every core OpenMP offers. Same result as
+    run(), without the extension log."""
+    T, Q = _u8(T), _u8(Q)
+    M = _scores(scores)
+    err = C.c_int(0)
+    h = lib().or_run_par(_ptr(T, C.c_uint8), T.size, _ptr(Q, C.c_uint8), Q.size,
+                         pattern.encode(), int(transition), int(strands), _ptr(M, C.c_int32),
+                         int(X), int(thresh), int(flags), int(qtile), int(threads),
+                         C.byref(err))
+    return _collect(h, err, False)
+
+
+def host_cores() -> int:
+    """Cores this process may run on (the oracle's default thread count)."""
+    import os
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
 
 
 def run_diagonal(T, Qs, strand: int, d: int, E0: int = -(1 << 62), pattern: str = DEFAULT_PATTERN,

@@ -40,6 +40,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_OK 0
 #define OR_EINVAL (-1)
@@ -198,13 +201,19 @@ static int cmp_diag_t(const void *a, const void *b)
     return (x->t > y->t) - (x->t < y->t);
 }
 
-/* Every hit of one strand, sorted by (diagonal t-q, t). */
-static int enumerate_hits(const uint8_t *T, int64_t tlen, const uint8_t *Qs, int64_t qlen,
-                          const or_pattern *p, int transition, tq_vec *out)
+/*
+ * The position table of the target: (seed key, position) for every position
+ * t in [0, tlen - span], sorted by key and then position. With nthreads > 1
+ * the entries are first split by the top bits of their key (a stable
+ * counting pass) and each part is sorted on its own thread; the order of
+ * (key, position) pairs is total, so the table is the same either way.
+ */
+static int build_table(const uint8_t *T, int64_t tlen, const or_pattern *p, int nthreads,
+                       or_entry **tab_out, int64_t *nt_out)
 {
-    out->v = NULL;
-    out->n = out->cap = 0;
-    if (tlen < p->span || qlen < p->span)
+    *tab_out = NULL;
+    *nt_out = 0;
+    if (tlen < p->span)
         return OR_OK;
     int64_t nt = tlen - p->span + 1;
     or_entry *tab = (or_entry *)malloc((size_t)nt * sizeof(or_entry));
@@ -214,21 +223,74 @@ static int enumerate_hits(const uint8_t *T, int64_t tlen, const uint8_t *Qs, int
         tab[t].key = seed_key(T, t, p);
         tab[t].pos = t;
     }
-    qsort(tab, (size_t)nt, sizeof(or_entry), cmp_entry);
+    if (nthreads <= 1) {
+        qsort(tab, (size_t)nt, sizeof(or_entry), cmp_entry);
+    } else {
+        int shift = 2 * p->weight > 8 ? 2 * p->weight - 8 : 0; /* 256 parts by the top key bits */
+        int64_t start[257] = {0};
+        for (int64_t t = 0; t < nt; t++)
+            start[(tab[t].key >> shift) + 1]++;
+        for (int b = 0; b < 256; b++)
+            start[b + 1] += start[b];
+        or_entry *tmp = (or_entry *)malloc((size_t)nt * sizeof(or_entry));
+        if (!tmp) {
+            free(tab);
+            return OR_ENOMEM;
+        }
+        int64_t fill[256];
+        memcpy(fill, start, sizeof(fill));
+        for (int64_t t = 0; t < nt; t++)
+            tmp[fill[tab[t].key >> shift]++] = tab[t];
+        free(tab);
+        tab = tmp;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+        for (int b = 0; b < 256; b++)
+            qsort(tab + start[b], (size_t)(start[b + 1] - start[b]), sizeof(or_entry), cmp_entry);
+    }
+    *tab_out = tab;
+    *nt_out = nt;
+    return OR_OK;
+}
+
+/*
+ * Hits of query positions q0 <= q < q1 (and q <= qlen - span) against the
+ * table, appended to out in query order: the exact key of Qs at q, then with
+ * transition tolerance the weight keys with one care position's transition
+ * partner (the 2-bit code x^2) in place of the query base.
+ */
+static int probe_range(const or_entry *tab, int64_t nt, const uint8_t *Qs, int64_t qlen,
+                       int64_t q0, int64_t q1, const or_pattern *p, int transition, tq_vec *out)
+{
     int nprobe = transition ? 1 + p->weight : 1;
-    for (int64_t q = 0; q + p->span <= qlen; q++) {
+    for (int64_t q = q0; q + p->span <= qlen && q < q1; q++) {
         uint32_t k = seed_key(Qs, q, p);
         for (int j = 0; j < nprobe; j++) {
             uint32_t pk = j == 0 ? k : k ^ (2u << (2 * (p->weight - j)));
             for (int64_t i = lower_key(tab, nt, pk); i < nt && tab[i].key == pk; i++) {
-                if (tq_push(out, tab[i].pos, q)) {
-                    free(tab);
+                if (tq_push(out, tab[i].pos, q))
                     return OR_ENOMEM;
-                }
             }
         }
     }
+    return OR_OK;
+}
+
+/* Every hit of one strand, sorted by (diagonal t-q, t). */
+static int enumerate_hits(const uint8_t *T, int64_t tlen, const uint8_t *Qs, int64_t qlen,
+                          const or_pattern *p, int transition, tq_vec *out)
+{
+    out->v = NULL;
+    out->n = out->cap = 0;
+    if (tlen < p->span || qlen < p->span)
+        return OR_OK;
+    or_entry *tab;
+    int64_t nt;
+    if (build_table(T, tlen, p, 1, &tab, &nt))
+        return OR_ENOMEM;
+    int e = probe_range(tab, nt, Qs, qlen, 0, qlen, p, transition, out);
     free(tab);
+    if (e)
+        return e;
     qsort(out->v, (size_t)out->n, sizeof(or_tq), cmp_diag_t);
     return OR_OK;
 }
@@ -326,20 +388,23 @@ static int cmp_hsp(const void *a, const void *b)
 }
 
 /*
- * The serial walk over one strand's hits, already grouped by diagonal and
+ * The serial walk over hits of one strand, already grouped by diagonal and
  * ordered by t (Algorithm 1 with X-drop as the extension, restricted to one
- * diagonal's masking state).
+ * diagonal's masking state). With Ecarry == NULL every diagonal starts with
+ * no masking state; otherwise diagonal d starts from Ecarry[d - dbase] and
+ * leaves its final state there, so a diagonal's hits may be walked in several
+ * calls as long as the calls come in increasing t.
  */
 static int walk(const uint8_t *T, int64_t tlen, const uint8_t *Qs, int64_t qlen, int strand,
-                const tq_vec *h, const or_pattern *p, const int32_t *M, int32_t X,
-                int32_t thresh, int flags, or_result *r)
+                const or_tq *v, int64_t nh, int64_t *Ecarry, int64_t dbase, const or_pattern *p,
+                const int32_t *M, int32_t X, int32_t thresh, int flags, or_result *r)
 {
     int64_t i = 0;
-    while (i < h->n) {
-        int64_t d = h->v[i].t - h->v[i].q;
-        int64_t E = INT64_MIN;
-        for (; i < h->n && h->v[i].t - h->v[i].q == d; i++) {
-            int64_t t = h->v[i].t, q = h->v[i].q;
+    while (i < nh) {
+        int64_t d = v[i].t - v[i].q;
+        int64_t E = Ecarry ? Ecarry[d - dbase] : INT64_MIN;
+        for (; i < nh && v[i].t - v[i].q == d; i++) {
+            int64_t t = v[i].t, q = v[i].q;
             r->st.hits++;
             if (t < E)
                 continue; /* inside an HSP already extended on this diagonal */
@@ -365,6 +430,8 @@ static int walk(const uint8_t *T, int64_t tlen, const uint8_t *Qs, int64_t qlen,
                     return OR_ENOMEM;
             }
         }
+        if (Ecarry)
+            Ecarry[d - dbase] = E;
     }
     return OR_OK;
 }
@@ -406,7 +473,7 @@ or_result *or_run(const uint8_t *T, int64_t tlen, const uint8_t *Q, int64_t qlen
         tq_vec h;
         int e = enumerate_hits(T, tlen, Qs, qlen, &p, transition, &h);
         if (!e)
-            e = walk(T, tlen, Qs, qlen, s, &h, &p, M, X, thresh, flags, r);
+            e = walk(T, tlen, Qs, qlen, s, h.v, h.n, NULL, 0, &p, M, X, thresh, flags, r);
         free(h.v);
         if (e) {
             *err = e;
@@ -417,6 +484,172 @@ or_result *or_run(const uint8_t *T, int64_t tlen, const uint8_t *Q, int64_t qlen
     if (*err) {
         free(r->hsp);
         free(r->ext);
+        free(r);
+        return NULL;
+    }
+    qsort(r->hsp, (size_t)r->n, sizeof(or_hsp), cmp_hsp);
+    return r;
+}
+
+/*
+ * The same filter stage computed on several threads (OpenMP), for inputs
+ * too large for the serial form. The arithmetic is the serial form's: the
+ * same table, probes, walk and X-drop. Only the order of independent work
+ * changes, which the method allows (diagonals are independent, and a
+ * diagonal's hits are still walked in increasing t):
+ *  - the query positions of a strand are taken in tiles of qtile positions
+ *    (qtile <= 0: one tile), in increasing q;
+ *  - a tile's hits are found on several threads (contiguous runs of query
+ *    positions), split into blocks of whole diagonals, and each block is
+ *    sorted by (diagonal, t) and walked on one thread;
+ *  - each diagonal's masking state E lives in a per-strand array, so the
+ *    hits of the next tile continue from the state the previous tile left.
+ * Since t - q is fixed on a diagonal, increasing q is increasing t, and every
+ * diagonal sees its hits in the order of the serial walk. No extension log.
+ * nthreads <= 0: all threads OpenMP offers (1 without OpenMP).
+ */
+or_result *or_run_par(const uint8_t *T, int64_t tlen, const uint8_t *Q, int64_t qlen,
+                      const char *pattern, int transition, int strands, const int32_t *M,
+                      int32_t X, int32_t thresh, int flags, int64_t qtile, int nthreads,
+                      int *err)
+{
+    or_pattern p;
+    *err = OR_OK;
+    if (or_parse_pattern(pattern, &p) || X < 0 || tlen < 0 || qlen < 0) {
+        *err = OR_EINVAL;
+        return NULL;
+    }
+    if (nthreads <= 0) {
+#ifdef _OPENMP
+        nthreads = omp_get_max_threads();
+#else
+        nthreads = 1;
+#endif
+    }
+    or_result *r = (or_result *)calloc(1, sizeof(or_result));
+    or_result *part = (or_result *)calloc((size_t)nthreads, sizeof(or_result));
+    uint8_t *rc = (uint8_t *)malloc((size_t)(qlen > 0 ? qlen : 1));
+    or_entry *tab = NULL;
+    int64_t nt = 0;
+    if (!r || !part || !rc) {
+        *err = OR_ENOMEM;
+        goto done;
+    }
+    if (tlen < p.span || qlen < p.span)
+        goto done;
+    if (build_table(T, tlen, &p, nthreads, &tab, &nt)) {
+        *err = OR_ENOMEM;
+        goto done;
+    }
+    or_revcomp(Q, qlen, rc);
+    const int64_t nq = qlen - p.span + 1;
+    if (qtile <= 0 || qtile > nq)
+        qtile = nq;
+    const int64_t dbase = -(qlen - p.span);        /* smallest diagonal t - q */
+    const int64_t ndiag = (tlen - p.span) - dbase + 1;
+    const int64_t nblk = 64 * (int64_t)nthreads;   /* diagonal blocks per tile */
+    const int64_t bw = (ndiag + nblk - 1) / nblk;  /* diagonals per block */
+    for (int s = 0; s < 2 && !*err; s++) {
+        if (!(strands & (1 << s)))
+            continue;
+        const uint8_t *Qs = s ? rc : Q;
+        int64_t *Ecarry = (int64_t *)malloc((size_t)ndiag * sizeof(int64_t));
+        if (!Ecarry) {
+            *err = OR_ENOMEM;
+            break;
+        }
+        for (int64_t d = 0; d < ndiag; d++)
+            Ecarry[d] = INT64_MIN;
+        for (int64_t q0 = 0; q0 < nq && !*err; q0 += qtile) {
+            const int64_t q1 = q0 + qtile < nq ? q0 + qtile : nq;
+            /* about four runs of query positions per thread, each probed by one task */
+            const int64_t nrun = q1 - q0 < 4 * (int64_t)nthreads ? q1 - q0 : 4 * (int64_t)nthreads;
+            const int64_t qrun = (q1 - q0 + nrun - 1) / nrun;
+            tq_vec *runs = (tq_vec *)calloc((size_t)nrun, sizeof(tq_vec));
+            int64_t *cnt = (int64_t *)calloc((size_t)(nrun * nblk + 1), sizeof(int64_t));
+            if (!runs || !cnt) {
+                free(runs);
+                free(cnt);
+                *err = OR_ENOMEM;
+                break;
+            }
+            int fail = 0;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+            for (int64_t k = 0; k < nrun; k++) {
+                const int64_t a = q0 + k * qrun, b = a + qrun < q1 ? a + qrun : q1;
+                if (probe_range(tab, nt, Qs, qlen, a, b, &p, transition, &runs[k])) {
+#pragma omp atomic write
+                    fail = 1;
+                }
+                for (int64_t i = 0; i < runs[k].n; i++) {
+                    const int64_t blk = (runs[k].v[i].t - runs[k].v[i].q - dbase) / bw;
+                    cnt[blk * nrun + k + 1]++;
+                }
+            }
+            /* block-major exclusive offsets: block blk, run k starts at cnt[blk * nrun + k] */
+            for (int64_t i = 0; i < nrun * nblk; i++)
+                cnt[i + 1] += cnt[i];
+            or_tq *grouped = NULL;
+            if (!fail && cnt[nrun * nblk] > 0) {
+                grouped = (or_tq *)malloc((size_t)cnt[nrun * nblk] * sizeof(or_tq));
+                if (!grouped)
+                    fail = 1;
+            }
+            if (!fail && grouped) {
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+                for (int64_t k = 0; k < nrun; k++) {
+                    for (int64_t i = 0; i < runs[k].n; i++) {
+                        const int64_t blk = (runs[k].v[i].t - runs[k].v[i].q - dbase) / bw;
+                        grouped[cnt[blk * nrun + k]++] = runs[k].v[i];
+                    }
+                }
+                /* after the scatter, cnt[blk * nrun + nrun - 1] is the end of block blk */
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+                for (int64_t blk = 0; blk < nblk; blk++) {
+                    const int64_t a = blk ? cnt[blk * nrun - 1] : 0, b = cnt[blk * nrun + nrun - 1];
+                    if (b <= a)
+                        continue;
+                    int tid = 0;
+#ifdef _OPENMP
+                    tid = omp_get_thread_num();
+#endif
+                    qsort(grouped + a, (size_t)(b - a), sizeof(or_tq), cmp_diag_t);
+                    if (walk(T, tlen, Qs, qlen, s, grouped + a, b - a, Ecarry, dbase, &p, M, X,
+                             thresh, flags, &part[tid])) {
+#pragma omp atomic write
+                        fail = 1;
+                    }
+                }
+            }
+            for (int64_t k = 0; k < nrun; k++)
+                free(runs[k].v);
+            free(runs);
+            free(cnt);
+            free(grouped);
+            if (fail)
+                *err = OR_ENOMEM;
+        }
+        free(Ecarry);
+    }
+    for (int i = 0; i < nthreads && !*err; i++) {
+        for (int64_t j = 0; j < part[i].n && !*err; j++)
+            if (push_hsp(r, &part[i].hsp[j]))
+                *err = OR_ENOMEM;
+        r->st.hits += part[i].st.hits;
+        r->st.extended += part[i].st.extended;
+        r->st.cells += part[i].st.cells;
+        r->st.hsps += part[i].st.hsps;
+    }
+done:
+    free(tab);
+    free(rc);
+    if (part)
+        for (int i = 0; i < nthreads; i++)
+            free(part[i].hsp);
+    free(part);
+    if (*err) {
+        if (r)
+            free(r->hsp);
         free(r);
         return NULL;
     }

@@ -11,8 +11,6 @@
 
 using namespace sfe;
 
-unsigned long long sfe::g_launches = 0;
-
 namespace {
 
 thread_local std::string g_err;
@@ -42,7 +40,6 @@ const int32_t kHoxd70[16] = {91,   -114, -31, -123, -114, 100,  -125, -31,
                              -31,  -125, 100, -114, -123, -31,  -114, 91};
 const char *kDefaultPattern = "1110100110010101111";
 
-constexpr int kDefaultLaneCap = 256;
 constexpr long long kDefaultTileHits = 1LL << 30;  // 8 GB per hit buffer
 constexpr unsigned long long kQueueMax = 1ull << 20;
 // A batch pair's split-key tables have about npos / 2 buckets each (1 to 2
@@ -520,7 +517,7 @@ int walk_sorted(sfe_ctx *c, const uint64_t *hits, long long n, const WalkSetup &
     wp.xdrop = ws.p->xdrop;
     wp.thresh = ws.p->hsp_thresh;
     wp.flags = ws.p->flags;
-    wp.lane_cap = ws.p->lane_cap > 0 ? ws.p->lane_cap : kDefaultLaneCap;
+    wp.lane_cap = ws.p->lane_cap > 0 ? ws.p->lane_cap : DEFAULT_LANE_CAP;
     wp.qoff = ws.qlen - ws.span;
     wp.scores = c->small->scores;
     wp.Ecarry = ws.Ecarry;
@@ -1226,7 +1223,7 @@ int batch_pipeline(sfe_ctx *c, const BatchGeom &g, const sfe_params *params, Bat
     wp.xdrop = params->xdrop;
     wp.thresh = params->hsp_thresh;
     wp.flags = params->flags;
-    wp.lane_cap = params->lane_cap > 0 ? params->lane_cap : kDefaultLaneCap;
+    wp.lane_cap = params->lane_cap > 0 ? params->lane_cap : DEFAULT_LANE_CAP;
     wp.scores = sm->scores;
     wp.bhsps = b.hsps;
     wp.hsp_cap = b.hcap;

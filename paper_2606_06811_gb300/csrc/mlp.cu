@@ -542,14 +542,7 @@ unsigned blocks_for(long long threads, int block) {
 // Inference grids: four CTAs per SM at most (the kernels stride over sample
 // groups).
 static long long predict_grid(long long want) {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
-    return max(1LL, min(want, 4LL * sms));
+    return max(1LL, min(want, 4LL * device_sms()));
 }
 
 cudaError_t launch_mlp_predict16(const uint32_t *T, long long tlen, const uint32_t *Q,
@@ -634,16 +627,13 @@ cudaError_t launch_mlp_fwd_bwd(const uint32_t *T, long long tlen, const uint32_t
     if (n <= 0) return cudaSuccess;
     const SampleCtx sc{T, Q, Qrc, tlen, qlen, pairs, span};
     const size_t smem = grad ? (size_t)NPARAM * 4 : 0;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(mlp_fwd_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             NPARAM * 4);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    int sms = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    static std::atomic<unsigned long long> attr;
+    cudaError_t ae = once_per_device(attr, [] {
+        return cudaFuncSetAttribute(mlp_fwd_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    NPARAM * 4);
+    });
+    if (ae != cudaSuccess) return ae;
+    const int sms = device_sms();
     // about 4 samples per warp: each block flushes its whole gradient once
     long long want = (n + 4 * MLP_WARPS - 1) / (4 * MLP_WARPS);
     long long grid = want < 2LL * sms ? want : 2LL * sms;

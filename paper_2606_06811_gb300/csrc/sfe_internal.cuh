@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "sfe.h"
 
 namespace sfe {
@@ -19,6 +21,10 @@ constexpr int SEQ_PAD = 4;          // words of padding on each side
 constexpr int MAX_SPAN = 32;
 constexpr int MAX_WEIGHT = 14;      // 4^14 + 1 offsets = 1 GiB of CSR
 constexpr int BLOCK = 256;
+// Bases per side a lane scores before it hands its diagonal to the warp tier
+// (the default of sfe_params.lane_cap; a sweep on the 10 Mb pair: 128, 256,
+// 512 and 1024 give 10.12, 9.98, 10.40 and 10.41 ms of walk).
+constexpr int DEFAULT_LANE_CAP = 256;
 
 // Device status bits (accumulated with atomicOr into one uint32).
 constexpr uint32_t ST_BAD_SYMBOL = 1u;
@@ -91,9 +97,30 @@ __device__ __forceinline__ uint32_t base_at(const uint32_t *__restrict__ S, long
 // ------------------------------------------------------------ host launchers
 // All launchers queue work on `st` and return cudaGetLastError().
 
-// Kernels launched by this library since it was loaded (host-side count,
-// incremented at every launch site).
-extern unsigned long long g_launches;
+// Kernels launched by this library from the calling host thread since it was
+// loaded (incremented at every launch site). Thread-local: a context is used
+// by one host thread at a time, so a call's launch count is this counter's
+// change across the call, whatever other threads launch meanwhile.
+extern thread_local unsigned long long g_launches;
+
+// Streaming-multiprocessor count of the current device (looked up once per
+// device; grids of persistent and strided kernels are sized from it).
+int device_sms();
+
+// Runs set() (a cudaFuncSetAttribute, which holds per device) the first time
+// it is reached on the current device; `done` keeps one bit per device.
+// Two threads may both run set() once: it is idempotent.
+template <class F>
+cudaError_t once_per_device(std::atomic<unsigned long long> &done, F set) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    e = set();
+    if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
 
 // bytes -> packed words (n bases). codes: 0 = ASCII, 1 = 2-bit codes.
 // dst points at the word of base 0 of a buffer with SEQ_PAD words on each side;

@@ -28,17 +28,7 @@ constexpr int RS_TILE = RS_BLOCK * RS_ITEMS;  // 4096
 constexpr int RS_MAXBITS = 10;
 constexpr int RS_R = 1 << RS_MAXBITS;  // largest bucket count (sizes the count arrays)
 
-int g_num_sms = 0;
-
-int num_sms() {
-    if (g_num_sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (g_num_sms <= 0) g_num_sms = 1;
-    }
-    return g_num_sms;
-}
+int num_sms() { return device_sms(); }
 
 struct RsGeom {
     int G;
@@ -298,17 +288,14 @@ cudaError_t rs_pass(const uint64_t *kin, uint64_t *kout, const uint32_t *vin, ui
                     const RsGeom &g, unsigned *counts, unsigned *totals, cudaStream_t st) {
     const bool vals = vin != nullptr;
     const size_t smem = rs_smem(vals, R);
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[vals]) {
-        cudaError_t e = vals ? cudaFuncSetAttribute(rs_scatter<true, R, DEVN>,
-                                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                    (int)smem)
-                             : cudaFuncSetAttribute(rs_scatter<false, R, DEVN>,
-                                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                    (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set[vals] = true;
-    }
+    static std::atomic<unsigned long long> attr_set[2];
+    cudaError_t ae = once_per_device(attr_set[vals], [&] {
+        return vals ? cudaFuncSetAttribute(rs_scatter<true, R, DEVN>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                    : cudaFuncSetAttribute(rs_scatter<false, R, DEVN>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (ae != cudaSuccess) return ae;
     cudaError_t me = cudaMemsetAsync(totals, 0, R * 4, st);
     if (me != cudaSuccess) return me;
     g_launches += 3;

@@ -47,20 +47,22 @@ constexpr size_t kStaticBytes = kOffTmp + kTmpBytes;
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
 // Host-side device addresses of g_static_scratch, one per device. In host
-// code the symbol itself is only a stand-in, not a device address.
-void *g_scratch_addr[kMaxDevices] = {};
+// code the symbol itself is only a stand-in, not a device address. Atomic:
+// two host threads making their first call on a device at the same time
+// both look the address up and store the same value.
+std::atomic<void *> g_scratch_addr[kMaxDevices];
 
 int scratch_address(int dev, unsigned char **out) {
     if (dev < 0 || dev >= kMaxDevices) return SFE_EINVAL;
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
+    void *p = g_scratch_addr[dev].load(std::memory_order_acquire);
+    if (!p) {
         if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess) {
             cudaGetLastError();
             return SFE_ECUDA;
         }
-        g_scratch_addr[dev] = p;
+        g_scratch_addr[dev].store(p, std::memory_order_release);
     }
-    *out = reinterpret_cast<unsigned char *>(g_scratch_addr[dev]);
+    *out = reinterpret_cast<unsigned char *>(p);
     return SFE_OK;
 }
 
@@ -134,6 +136,10 @@ extern "C" int sfe_ungapped_xdrop_static(const uint8_t *target, int64_t tlen,
     if (tlen < 0 || qlen < 0 || nhits < 0 || cap < 0) return SFE_EINVAL;
     if (tlen > kMaxBases || qlen > kMaxBases || nhits > kMaxHits) return SFE_ELIMIT;
     if (X < 0 || X >= (1 << 30) || (input_codes != 0 && input_codes != 1)) return SFE_EINVAL;
+    // the walk's packed windows hold 64 x score in int32: the same bound as
+    // every other entry point
+    for (int i = 0; i < 16; i++)
+        if (scores[i] < -(1 << 20) || scores[i] > (1 << 20)) return SFE_EINVAL;
     SeedPattern pat;
     if (parse(seed_pattern, &pat) != SFE_OK) return SFE_EINVAL;
     if ((tlen > 0 && !on_device(target)) || (qlen > 0 && !on_device(query)) ||
@@ -195,7 +201,7 @@ extern "C" int sfe_ungapped_xdrop_static(const uint8_t *target, int64_t tlen,
     wp.xdrop = X;
     wp.thresh = hsp_thresh;
     wp.flags = 0;
-    wp.lane_cap = 96;
+    wp.lane_cap = DEFAULT_LANE_CAP;
     wp.qoff = qlen - pat.span;
     wp.scores = small->scores;
     wp.Ecarry = nullptr;

@@ -698,16 +698,7 @@ inline unsigned grid_for(long long n, int block = BLOCK) {
     return (unsigned)((n + block - 1) / block);
 }
 
-int g_sms = 0;
-int sms() {
-    if (!g_sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (g_sms <= 0) g_sms = 1;
-    }
-    return g_sms;
-}
+int sms() { return device_sms(); }
 
 }  // namespace
 

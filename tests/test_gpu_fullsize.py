@@ -1,17 +1,26 @@
 """Parity at full workload sizes, in the launch configuration the benchmark uses.
 
-The oracle cannot run a whole 10 Mb x 10 Mb pair in test time, but it can
-walk single diagonals exactly (hits found by testing every position of the
-diagonal), so sampled diagonals are compared HSP by HSP, and properties that
-hold at any size are checked on every HSP.
+Each workload's whole sorted HSP list and its hit, extension and cell counts
+are compared with the oracle's: the 10 Mb x 10 Mb pair, the batch of 4096
+uneven pairs (eager call and captured-graph replay) and the 100 Mb x 100 Mb
+pair (query-tiled, skip state carried across tiles). The oracle runs in its
+multi-threaded form on every host core (the 100 Mb pair in query tiles of
+2^21 positions, which bounds its memory), the batch pair by pair on a thread
+pool. Before the full comparison, a fast pre-filter walks sampled diagonals
+exactly (hits found by testing every position of the diagonal) and checks
+that every HSP's score is the sum of its substitution scores.
 """
 from __future__ import annotations
+
+import time
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 import pytest
 
 import oracle
 import synth
+from synth.workloads import concat_batch
 from tests import bruteforce as bf
 
 pytestmark = pytest.mark.gpu
@@ -82,15 +91,71 @@ def pick_diagonals(pair, H, n_hsp, n_rand, seed):
     return picks
 
 
-def test_plain_pair_10mb_full_size(pkg):
+def check_full_list(pair, H, st, qtile=0):
+    """The whole sorted HSP list and the counters against the oracle."""
+    t0 = time.perf_counter()
+    ref = oracle.run_par(pair.T, pair.Q, qtile=qtile)
+    secs = time.perf_counter() - t0
+    print(f"oracle: {oracle.host_cores()} host cores, {secs:.1f} s, {ref.hits} hits, "
+          f"{ref.cells} cells, {ref.hsps.size} HSPs")
+    R = ref.hsps.view(np.int32).reshape(-1, 5)
+    assert H.shape == R.shape and np.array_equal(H, R)
+    assert (st["hits"], st["extended"], st["cells"], st["hsps"]) == \
+        (ref.hits, ref.extended, ref.cells, int(ref.hsps.size))
+
+
+def test_plain_pair_10mb_full_list(pkg):
     pair = synth.plain_pair_10mb(2)  # the benchmark's workload and seed
     H, st = run_gpu(pkg, pair)
     assert st["hits"] > 1e8 and H.shape[0] > 1e5
     check_scores(pair, H)
     check_diagonals(pair, H, pick_diagonals(pair, H, 8, 6, 1))
+    check_full_list(pair, H, st)
 
 
-def test_large_pair_100mb_full_size_tiled(pkg):
+def oracle_pairs(pairs):
+    """Each pair of a batch through the serial oracle, on a thread pool (the
+    oracle's C code runs outside the interpreter lock)."""
+    def one(p):
+        r = oracle.run(p.T, p.Q)
+        return r.hsps.view(np.int32).reshape(-1, 5), r.hits, r.extended, r.cells
+    with ThreadPoolExecutor(oracle.host_cores()) as ex:
+        res = list(ex.map(one, pairs))
+    rows = [np.concatenate([np.full((h.shape[0], 1), i, np.int32), h], 1)
+            for i, (h, *_) in enumerate(res)]
+    return (np.concatenate(rows), sum(r[1] for r in res), sum(r[2] for r in res),
+            sum(r[3] for r in res))
+
+
+def test_batch_pairs_4096_full_list(pkg):
+    """The benchmark's batch (4096 pairs of 1-256 kb): the eager call with the
+    defaults, and replays of the captured graph with the walk the autotuner
+    picks on this workload (persistent, 32-hit chunks), pair by pair."""
+    import torch
+    pairs = synth.batch_pairs(seed=3, n_pairs=4096)
+    Tc, toff, Qc, qoff = concat_batch(pairs)
+    dev = torch.device("cuda", 0)
+    T = torch.from_numpy(np.frombuffer(synth.decode(Tc), np.uint8).copy()).to(dev)
+    Q = torch.from_numpy(np.frombuffer(synth.decode(Qc), np.uint8).copy()).to(dev)
+    R, hits, ext, cells = oracle_pairs(pairs)
+    print(f"batch oracle: {R.shape[0]} HSPs, {hits} hits, {cells} cells")
+    with pkg.Context(0) as ctx:
+        h, st = ctx.run_batch(T, toff, Q, qoff, pkg.default_params(), cap=1 << 22)
+        G = np.ascontiguousarray(h).view(np.int32).reshape(-1, 6)
+        assert G.shape == R.shape and np.array_equal(G, R)
+        assert (st["hits"], st["extended"], st["cells"]) == (hits, ext, cells)
+        plan = ctx.batch_plan(toff, qoff, pkg.default_params(walk_chunk=32))
+        try:
+            for _ in range(2):
+                h, st = plan.run(T, Q, cap=1 << 22)
+                G = np.ascontiguousarray(h).view(np.int32).reshape(-1, 6)
+                assert G.shape == R.shape and np.array_equal(G, R)
+                assert (st["hits"], st["extended"], st["cells"]) == (hits, ext, cells)
+        finally:
+            plan.close()
+
+
+def test_large_pair_100mb_full_list(pkg):
     pair = synth.large_pair_100mb(5)
     H, st = run_gpu(pkg, pair)
     assert st["tiles"] > 10  # the query is tiled, with the skip state carried across tiles
@@ -98,3 +163,4 @@ def test_large_pair_100mb_full_size_tiled(pkg):
     sub = H[synth.Stream(9, "sub").integers(0, H.shape[0], 200_000)]
     check_scores(pair, sub)
     check_diagonals(pair, H, pick_diagonals(pair, H, 5, 3, 2))
+    check_full_list(pair, H, st, qtile=1 << 21)

@@ -5,6 +5,11 @@ dropped term, a flipped comparison, a transposed operand, a wrong index or
 sign), compiled on the CPU into a temporary library. The quick battery below
 (the same checks as test_oracle_pins, at smaller sizes) must fail on every
 mutant and pass on the real oracle. No mutant reads outside its buffers.
+
+The battery runs in two forms: the serial oracle, and the multi-threaded
+form (or_run_par) with small query tiles, so that diagonals cross tiles and
+the carried skip state matters. A mutant in code both forms share must be
+rejected in both; a mutant in code only one form runs, in that form.
 """
 from __future__ import annotations
 
@@ -18,13 +23,17 @@ from tests import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(__file__)), "oracle", "sfe_oracle.c")
 
-# (name, old text, new text, occurrences to replace: 0 = all)
+SERIAL, PARALLEL = "serial", "parallel"
+BOTH = (SERIAL, PARALLEL)
+PAR_QTILE, PAR_THREADS = 97, 3  # tiles of 97 query positions on 3 threads
+
+# (name, old text, new text, occurrences to replace: 0 = all[, forms that must reject it])
 MUTANTS = [
     # range edges: the last target or query position, the last base of a side
     ("last_target_position_dropped", "int64_t nt = tlen - p->span + 1;",
      "int64_t nt = tlen - p->span;", 1),
-    ("last_query_position_dropped", "for (int64_t q = 0; q + p->span <= qlen; q++) {",
-     "for (int64_t q = 0; q + p->span < qlen; q++) {", 1),
+    ("last_query_position_dropped", "for (int64_t q = q0; q + p->span <= qlen && q < q1; q++) {",
+     "for (int64_t q = q0; q + p->span < qlen && q < q1; q++) {", 1),
     ("right_side_stops_one_short", "while (t + span + n < tlen && q + span + n < qlen) {",
      "while (t + span + n + 1 < tlen && q + span + n < qlen) {", 1),
     ("left_side_stops_one_short", "while (t - 1 - n >= 0 && q - 1 - n >= 0) {",
@@ -52,11 +61,24 @@ MUTANTS = [
     ("cells_without_span", "r->st.cells += p->span + e.lscored + e.rscored;",
      "r->st.cells += e.lscored + e.rscored;", 1),
     ("left_max_not_reset", "sum = best = bestlen = n = 0;", "sum = bestlen = n = 0;", 0),
-    ("strand_label_swapped", "e = walk(T, tlen, Qs, qlen, s, &h,", "e = walk(T, tlen, Qs, qlen, 1 - s, &h,", 0),
+    ("strand_label_swapped", "walk(T, tlen, Qs, qlen, s, ", "walk(T, tlen, Qs, qlen, 1 - s, ", 0),
     ("two_transitions_in_predicate", "if (transition && (a ^ b) == 2 && !used) {",
      "if (transition && (a ^ b) == 2) {", 0),
-    ("skip_state_not_reset_per_diagonal", "int64_t E = INT64_MIN;\n        for (; i < h->n",
-     "static int64_t E = INT64_MIN;\n        for (; i < h->n", 0),
+    # the serial form starts every diagonal without a masking state; the
+    # parallel form reads each diagonal's state from the carry array instead
+    ("skip_state_not_reset_per_diagonal",
+     "int64_t E = Ecarry ? Ecarry[d - dbase] : INT64_MIN;\n        for (; i < nh",
+     "static int64_t E = INT64_MIN;\n        if (Ecarry) E = Ecarry[d - dbase];\n"
+     "        for (; i < nh", 0, (SERIAL,)),
+    # parallel form only: the masking state is not carried to the next query
+    # tile, the last query position of every tile is lost, or two probe runs
+    # of one tile overlap by a position
+    ("carry_not_written_back", "        if (Ecarry)\n            Ecarry[d - dbase] = E;\n", "\n",
+     1, (PARALLEL,)),
+    ("tile_end_dropped", "const int64_t q1 = q0 + qtile < nq ? q0 + qtile : nq;",
+     "const int64_t q1 = q0 + qtile < nq ? q0 + qtile - 1 : nq;", 1, (PARALLEL,)),
+    ("probe_runs_overlap", "b = a + qrun < q1 ? a + qrun : q1;",
+     "b = a + qrun + 1 < q1 ? a + qrun + 1 : q1;", 1, (PARALLEL,)),
 ]
 
 
@@ -69,7 +91,10 @@ def _safe(fn, *args) -> bool:
         return False
 
 
-def battery() -> dict:
+def battery(form: str = SERIAL) -> dict:
+    if form == PARALLEL:
+        with oracle.use_parallel(PAR_QTILE, PAR_THREADS):
+            return battery(SERIAL)
     return {
         "hand": _safe(lambda: all(pins.check_hand_case(c) for c in pins._hand_cases())),
         "hits": _safe(pins.check_hits_bruteforce, 7, 1200, 1000),
@@ -90,18 +115,22 @@ def _mutant_source(old, new, count):
     return src.replace(old, new) if count == 0 else src.replace(old, new, count)
 
 
-def test_battery_passes_on_the_oracle():
-    res = battery()
+@pytest.mark.parametrize("form", BOTH)
+def test_battery_passes_on_the_oracle(form):
+    res = battery(form)
     assert all(res.values()), res
 
 
-@pytest.mark.parametrize("name,old,new,count", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_pins_reject_mutant(tmp_path, name, old, new, count):
+@pytest.mark.parametrize("mutant", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_reject_mutant(tmp_path, mutant):
+    name, old, new, count = mutant[:4]
+    forms = mutant[4] if len(mutant) > 4 else BOTH
     src = tmp_path / f"{name}.c"
     src.write_text(_mutant_source(old, new, count))
     lib = tmp_path / f"lib{name}.so"
-    subprocess.run(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-w", "-o", str(lib), str(src)],
-                   check=True)
+    subprocess.run(["gcc", "-O1", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-w", "-o",
+                    str(lib), str(src)], check=True)
     with oracle.use_library(str(lib)):
-        res = battery()
-    assert not all(res.values()), f"mutant {name} survived every pin: {res}"
+        for form in forms:
+            res = battery(form)
+            assert not all(res.values()), f"mutant {name} survived every pin ({form}): {res}"

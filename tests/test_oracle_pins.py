@@ -269,3 +269,36 @@ def test_hoxd70_published_symmetries():
     # the four transitions score alike and every transversion scores below them
     assert {M[0, 2], M[2, 0], M[1, 3], M[3, 1]} == {-31}
     assert oracle.XDROP == 10 * M[0, 0]
+
+
+@pytest.mark.parametrize("qtile,threads", [(0, 1), (0, 4), (1, 2), (97, 3), (1000, 8), (4096, 5)])
+def test_parallel_form_equals_serial(qtile, threads):
+    """or_run_par (query tiles with the skip state carried, blocks of diagonals
+    walked on several threads) gives the serial oracle's HSPs and counters."""
+    T, Q = _rand_pair(21, 6000, 5000)
+    ref = oracle.run(T, Q, thresh=800)
+    got = oracle.run_par(T, Q, thresh=800, qtile=qtile, threads=threads)
+    assert np.array_equal(got.hsps, ref.hsps) and ref.hsps.size > 0
+    assert (got.hits, got.extended, got.cells) == (ref.hits, ref.extended, ref.cells)
+
+
+@pytest.mark.parametrize("n,m", [(0, 0), (0, 50), (50, 0), (18, 18), (19, 19), (19, 40),
+                                 (40, 19), (33, 4097)])
+def test_parallel_form_ragged_and_empty(n, m):
+    T, Q = _rand_pair(22, n, m, homology=False)
+    ref = oracle.run(T, Q, thresh=0)
+    for qtile, threads in ((0, 3), (7, 2)):
+        got = oracle.run_par(T, Q, thresh=0, qtile=qtile, threads=threads)
+        assert np.array_equal(got.hsps, ref.hsps)
+        assert (got.hits, got.extended, got.cells) == (ref.hits, ref.extended, ref.cells)
+
+
+def test_parallel_form_dense_diagonals_across_tiles():
+    """Identical sequences and a period-19 repeat: long diagonals full of
+    skipped hits, cut by query tiles of 13 positions."""
+    for kind in ("polyA", "period19", "identical"):
+        T, Q = _adversarial_pair(kind)
+        ref = oracle.run(T, Q, thresh=0)
+        got = oracle.run_par(T, Q, thresh=0, qtile=13, threads=4)
+        assert np.array_equal(got.hsps, ref.hsps)
+        assert (got.hits, got.extended, got.cells) == (ref.hits, ref.extended, ref.cells)

@@ -120,3 +120,67 @@ def test_rejects_sizes_beyond_the_fixed_scratch(env):
     assert fn(*args(big, big.numel(), small, small.numel(), hits, 0)) == ELIMIT
     assert fn(*args(small, small.numel(), big, big.numel(), hits, 0)) == ELIMIT
     assert fn(*args(small, small.numel(), small, small.numel(), hits, hits.shape[0])) == ELIMIT
+
+
+def _raw(env, T, Q, H, cap, scores=None, stream=None, out_none=False):
+    """One call with explicit scores and stream; returns (code, HSPs, needed count)."""
+    torch, P, fn, _ = env
+    dev = torch.device("cuda", 0)
+    Td = torch.from_numpy(T.copy()).to(dev)
+    Qd = torch.from_numpy(Q.copy()).to(dev)
+    Hd = torch.from_numpy(H).to(dev)
+    out = torch.full((max(cap, 1), 5), -7, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+    nh = C.c_int64(-1)
+    M = oracle.HOXD70.reshape(16) if scores is None else np.asarray(scores).reshape(16)
+    sc = (C.c_int32 * 16)(*[int(x) for x in M])
+    code = fn(Td.data_ptr(), T.size, Qd.data_ptr(), Q.size, None, 1, Hd.data_ptr(), H.shape[0],
+              C.byref(sc), 910, 3000, None if out_none else out.data_ptr(), cap, C.byref(nh),
+              None, stream)
+    return code, out[: max(0, min(nh.value, cap))].cpu().numpy(), nh.value
+
+
+def test_rejects_scores_outside_the_packed_window_range(env):
+    """A score beyond 2^20 would overflow the walk's 64 x score window sums;
+    the call refuses it before any GPU work, like every other entry point."""
+    T, Q = _case(44, 20_000, 20_000, 4)
+    H = _hits(T, Q, 4)
+    for bad in ((1 << 20) + 1, -(1 << 20) - 1):
+        M = oracle.HOXD70.reshape(16).copy()
+        M[5] = bad
+        code, _, _ = _raw(env, T, Q, H, cap=1024, scores=M)
+        assert code == -1
+    M = oracle.HOXD70.reshape(16).copy()
+    M[5] = 1 << 20  # the bound itself is accepted
+    code, _, _ = _raw(env, T, Q, H, cap=1 << 16, scores=M)
+    assert code == 0
+
+
+def test_a_hit_outside_the_sequences_is_rejected_and_the_next_call_is_exact(env):
+    T, Q = _case(45, 30_000, 30_000, 6)
+    H = _hits(T, Q, 5)
+    bad = H.copy()
+    bad[len(bad) // 2, 1] = T.size - 10  # the seed span would leave the target
+    code, _, _ = _raw(env, T, Q, bad, cap=4096)
+    assert code == -1
+    ref, _ = _existing(env, T, Q, H)
+    code, got, n = _raw(env, T, Q, H, cap=4096)
+    assert code == 0 and n == ref.shape[0] and np.array_equal(got, ref)
+
+
+def test_zero_capacity_without_a_buffer_reports_the_count(env):
+    T, Q = _case(46, 30_000, 30_000, 6)
+    H = _hits(T, Q, 6)
+    ref, _ = _existing(env, T, Q, H)
+    code, _, n = _raw(env, T, Q, H, cap=0, out_none=True)
+    assert ref.shape[0] > 0 and code == -5 and n == ref.shape[0]
+
+
+def test_runs_on_a_caller_stream(env):
+    torch = env[0]
+    T, Q = _case(47, 40_000, 30_000, 8)
+    H = _hits(T, Q, 7)
+    ref, _ = _existing(env, T, Q, H)
+    s = torch.cuda.Stream(device=torch.device("cuda", 0))
+    code, got, n = _raw(env, T, Q, H, cap=4096, stream=C.c_void_p(s.cuda_stream))
+    assert code == 0 and n == ref.shape[0] and np.array_equal(got, ref)
