@@ -76,11 +76,17 @@ def args_parse():
                          "(a separate line, not the headline)")
     ap.add_argument("--pairs", type=int, default=4096)
     ap.add_argument("--no-tune", action="store_true", help="batch: skip the autotuner")
+    ap.add_argument("--no-sublines", action="store_true",
+                    help="skip the batch and 100 Mb sub-measurements of the default run")
+    ap.add_argument("--sub-steps", type=int, default=3)
+    ap.add_argument("--sub-warmup", type=int, default=3)
     a = ap.parse_args()
     if a.seed is None:
         a.seed = 5 if a.workload == "large_pair_100mb" else 2
     if a.workload == "large_pair_100mb":  # a separate line: no oracle sample, no predictor
         a.no_learned = a.no_cpu_baseline = True
+    if a.scale != 1.0:
+        a.no_sublines = True
     return a
 
 
@@ -191,6 +197,50 @@ def kernel_traffic(kernel: str) -> float | None:
     return float(t.group(1))
 
 
+def radix_passes(nbits: int) -> int:
+    """Passes of the library's LSD radix sort over an nbits-wide key: as few as
+    9-bit digits allow, or 10-bit ones where that saves a pass."""
+    if nbits <= 0:
+        return 0
+    return min((nbits + 8) // 9, (nbits + 9) // 10)
+
+
+def stage_rooflines(st: dict, stage_ms: dict, tlen: int, qlen: int, weight: int, strands: int,
+                    hbm_gbs: float) -> dict:
+    """Achieved HBM bandwidth of the memory-bound stages from their algorithmic
+    bytes per step (the minimum each stage must move; re-reads are not counted):
+      index: per target position, the 8-byte key written, 16 B per radix pass
+        (read + write), 12 B of CSR work (key read, position written), and
+        8 B per merged probe-set entry (1 + weight per position: position read,
+        entry written); plus six 4-byte sweeps of the 4^weight-entry tables;
+      count: per query position and strand, the 4-byte table word read, the
+        count written and its 8-byte scan written;
+      write: per hit, the 4-byte merged-list entry read and the 8-byte hit written;
+      sort: per hit, 16 B per radix pass over the bits_for(tlen + qlen)-bit
+        diagonal word (each 8-byte key read and written once)."""
+    npos = max(0, tlen - (19 - 1))
+    nq = max(0, qlen - (19 - 1)) * strands
+    dbits = max(1, (tlen + qlen).bit_length())
+    hits = st["hits"]
+    algo = {
+        "index": npos * (8 + 16 * radix_passes(2 * weight) + 12 + 8 * (1 + weight))
+        + 6 * 4 * (4 ** weight),
+        "count": nq * 16,
+        "write": hits * 12,
+        "sort": hits * 16 * radix_passes(dbits),
+    }
+    out = {}
+    for k, b in algo.items():
+        ms = stage_ms.get(k, 0.0)
+        if ms <= 0:
+            continue
+        gbs = b / (ms / 1e3) / 1e9
+        out[k] = {"bound": "hbm", "algorithmic_bytes": int(b), "ms": round(ms, 4),
+                  "achieved": round(gbs, 1), "peak": hbm_gbs, "unit": "GB/s",
+                  "frac": round(gbs / hbm_gbs, 4)}
+    return out
+
+
 # ------------------------------------------------------------ workloads
 
 def make_workload(seed: int, scale: float, name: str = WORKLOAD):
@@ -215,28 +265,69 @@ def oracle_sample(pair, seconds: float):
         qlen = int(min(pair.qlen, qlen * grow))
 
 
+def oracle_sample_cores(pair, qlen: int, reps: int = 1):
+    """The oracle's multi-threaded form on every host core, on the same sample
+    (full target x query prefix of qlen). Returns (cells, hsps, hits, secs, cores)."""
+    import oracle
+    cores = oracle.host_cores()
+    secs, r = 0.0, None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        r = oracle.run_par(pair.T, pair.Q[:qlen], threads=cores)
+        secs += time.perf_counter() - t0
+    return r.cells * reps, int(r.hsps.size) * reps, r.hits * reps, secs, cores
+
+
+def cpu_baseline_line(pair, seconds: float) -> dict:
+    """The oracle on the machine's host cores: one thread, and every core, on the
+    same query prefix of the same pair."""
+    c1, h1, ht1, dt1, qlen = oracle_sample(pair, seconds)
+    reps = 3
+    cn, hn, htn, dtn, cores = oracle_sample_cores(pair, qlen, reps)
+    sample = (f"full {pair.tlen:,} bp target x {qlen:,} bp query prefix, both strands")
+    return {"value": cn / dtn / 1e9, "unit": "GCUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{sample}; multi-threaded form on {cores} cores, {reps} runs, "
+                      f"{dtn:.1f} s",
+            "single_core": {"value": c1 / dt1 / 1e9, "unit": "GCUPS", "cores": 1,
+                            "sample": f"{sample}; serial form, {dt1:.1f} s"},
+            "hsps_per_s": hn / dtn, "hits_per_s": htn / dtn}
+
+
 # ------------------------------------------------------------------ arms
 
 def run_reference(a, rank, world):
     if rank != 0:
         return 0
+    import oracle
     pair, _, _ = make_workload(a.seed, a.scale)
-    # at least 6 s per step: each sample indexes the full target once, and a
-    # query prefix of a few hundred kb keeps that cost from dominating
-    per = max(6.0, a.cpu_seconds / max(1, a.steps + a.warmup))
+    cores = oracle.host_cores()
+    # each step times the oracle's multi-threaded form on every host core over
+    # the full target and a query prefix, sized so the whole run (warm-up and
+    # timed steps) takes about 10 x --cpu-seconds (150 s by default)
+    a_total = 10.0 * a.cpu_seconds
+    per = max(1.0, a_total / max(1, a.steps + a.warmup))
+    qlen = min(pair.qlen, 200_000)
+    while True:
+        t0 = time.perf_counter()
+        oracle.run_par(pair.T, pair.Q[:qlen], threads=cores)
+        dt = time.perf_counter() - t0
+        if dt >= 0.6 * per or qlen >= pair.qlen:
+            break
+        qlen = int(min(pair.qlen, qlen * max(1.5, 0.9 * per / max(dt, 1e-3))))
     cells = hsps = hits = 0
     secs = 0.0
-    qlen = 0
     for i in range(a.warmup + a.steps):
-        c, h, ht, dt, qlen = oracle_sample(pair, per)
+        t0 = time.perf_counter()
+        r = oracle.run_par(pair.T, pair.Q[:qlen], threads=cores)
+        dt = time.perf_counter() - t0
         if i >= a.warmup:
-            cells += c
-            hsps += h
-            hits += ht
+            cells += r.cells
+            hsps += int(r.hsps.size)
+            hits += r.hits
             secs += dt
     gcups = cells / secs / 1e9
     sample = (f"full {pair.tlen:,} bp target x {qlen:,} bp query prefix of {WORKLOAD}, "
-              "both strands, per step")
+              f"both strands, per step; the oracle's multi-threaded form on {cores} cores")
     line = {
         "impl": "reference", "metric": METRIC, "value": gcups, "unit": "GCUPS",
         "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
@@ -246,7 +337,7 @@ def run_reference(a, rank, world):
                    "seed_pattern": "1110100110010101111", "transition": 1, "strands": 2,
                    "xdrop": 910, "hsp_thresh": 3000},
         "hsps_per_s": hsps / secs, "hits_per_s": hits / secs,
-        "cpu_baseline": {"value": gcups, "unit": "GCUPS", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": gcups, "unit": "GCUPS", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": gcups, "unit": "GCUPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -371,8 +462,9 @@ def run_sfe(a, rank, world, local):
     # dominant kernel: the lane walk (skip + X-drop), integer-ALU bound
     peaks = measured_peaks()
     lane_ms = stage_ms["walk_lanes"] / max(1.0, stage_launch["walk_lanes"])
-    # the persistent walk scores the warp tier's cells in the same launch
-    persistent = stage_launch["walk_warps"] == 0
+    # the persistent walk scores the warp tier's cells in the same launch (its
+    # follow-up warp launch only walks entries left by consumers that gave up)
+    persistent = a.walk_mode in (None, 1)
     lane_cells = (s0["cells"] - (0 if persistent else s0["warp_cells"])) / \
         max(1.0, stage_launch["walk_lanes"])
     achieved = lane_cells * OPS_PER_CELL / (lane_ms / 1e3) / 1e12
@@ -385,6 +477,7 @@ def run_sfe(a, rank, world, local):
                 "ops_per_cell": OPS_PER_CELL,
                 "ms_per_launch": lane_ms, "launches_per_step": stage_launch["walk_lanes"]}
     dom = max(stage_ms, key=stage_ms.get)
+    stages_hbm = stage_rooflines(s0, stage_ms, pair.tlen, pair.qlen, 12, 2, peaks["hbm_gbs"])
 
     line = {
         "metric": METRIC, "value": gcups, "unit": "GCUPS", "n_gpus": world,
@@ -408,6 +501,7 @@ def run_sfe(a, rank, world, local):
         "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "dominant_stage": dom,
         "roofline": roofline,
+        "stage_roofline": stages_hbm,
         "gpu_launches": int(launches),
         "clocks": clk,
         "wall_s": wall,
@@ -463,20 +557,27 @@ def run_sfe(a, rank, world, local):
                        "path": "sfe_run with pinned host buffers (host wall clock)"}
 
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        c, h, ht, dt, qlen = oracle_sample(pair, a.cpu_seconds)
-        line["cpu_baseline"] = {
-            "value": c / dt / 1e9, "unit": "GCUPS", "cores": 1, "kind": "oracle",
-            "sample": f"full {pair.tlen:,} bp target x {qlen:,} bp query prefix, both strands, "
-                      f"{dt:.1f} s single-threaded"}
+        line["cpu_baseline"] = cpu_baseline_line(pair, a.cpu_seconds)
+    ctx.close()
+    if a.workload == WORKLOAD and not a.no_sublines:
+        # the other configurations, each in its own sub-object (fewer steps)
+        del out, flush
+        torch.cuda.empty_cache()
+        sub = argparse.Namespace(**vars(a))
+        sub.steps, sub.warmup = a.sub_steps, max(3, a.sub_warmup)
+        line["batch_pairs"] = run_batch_bench(sub, rank, world, local, emit=False)
+        torch.cuda.empty_cache()
+        sub.seed = 5
+        line["large_pair_100mb"] = run_large(sub, local)
+        torch.cuda.empty_cache()
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     if dist:
         dist.destroy_process_group()
     return 0
 
 
-def run_batch_bench(a, rank, world, local):
+def run_batch_bench(a, rank, world, local, emit: bool = True):
     """The batch of uneven pairs: autotuned walk parameters, then eager calls
     (sfe_run_batch) and replays of the captured graph (sfe_batch_plan_run)."""
     import torch
@@ -572,11 +673,88 @@ def run_batch_bench(a, rank, world, local):
         "gpu_launches": int(sum(r[1]["launches"] for r in res["graph"])),
         "clocks": clk, "generate_s": round(gen_s, 2),
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     plan.close()
     ctx.close()
+    if not emit:
+        return line
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     return 0
+
+
+def run_large(a, local) -> dict:
+    """The 100 Mb x 100 Mb pair (query-tiled, skip state carried across
+    tiles): the plain path and the learned-binned persistent path, GCUPS of
+    each and whether their HSP lists are byte-identical."""
+    import torch
+    import paper_2606_06811_gb300 as pkg
+    dev = torch.device("cuda", local)
+    t0 = time.perf_counter()
+    pair, Ta, Qa = make_workload(a.seed, 1.0, "large_pair_100mb")
+    gen_s = time.perf_counter() - t0
+    T = torch.from_numpy(Ta.copy()).to(dev)
+    Q = torch.from_numpy(Qa.copy()).to(dev)
+    del Ta, Qa
+    stream = torch.cuda.Stream(device=dev)
+    ctx = pkg.Context(local, stream=stream)
+    cap = 1 << 23
+    out = torch.zeros((cap, 5), dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def step(prm):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hs, st = ctx.run(T, Q, prm, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), st, int(hs.shape[0])
+
+    def arm(prm):
+        for _ in range(a.warmup):
+            step(prm)
+        rows = [step(prm) for _ in range(a.steps)]
+        ms = sum(r[0] for r in rows)
+        st = rows[0][1]
+        return {"value": sum(r[1]["cells"] for r in rows) / (ms / 1e3) / 1e9, "unit": "GCUPS",
+                "ms_per_step": ms / len(rows), "hsps_per_s": rows[0][2] * len(rows) / (ms / 1e3),
+                "per_step": {"cells": st["cells"], "hits": st["hits"], "hsps": rows[0][2],
+                             "tiles": st["tiles"], "warp_tasks": st["warp_tasks"]},
+                "stage_ms": {k: round(v, 2) for k, v in st["stage_ms"].items()}}
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    plain = arm(pkg.default_params(flags=pkg.TIME_STAGES))
+    plain_out = out[: plain["per_step"]["hsps"]].clone()
+    res = {"workload": "large_pair_100mb", "seed": a.seed, "tlen": pair.tlen, "qlen": pair.qlen,
+           "steps": a.steps, "warmup": a.warmup, "generate_s": round(gen_s, 1),
+           "plain": plain}
+    if not a.no_learned:
+        from paper_2606_06811_gb300 import predictor
+        t1 = time.perf_counter()
+        tr = make_workload(a.train_seed, 0.2, "large_pair_100mb")[0]
+        recs, _ = predictor.collect(ctx, tr.T, tr.Q, a.log_every, cap=1 << 25,
+                                    params=pkg.default_params(input_codes=1))
+        data = predictor.training_data(ctx, [(tr.T, tr.Q, recs)])
+        pred = predictor.train(ctx, data, epochs=2, batch=8192, lr=2e-3, seed=3)
+        data.close()
+        train_s = time.perf_counter() - t1
+        lp = pkg.default_params(flags=pkg.TIME_STAGES, walk_mode=pkg.WALK_PERSISTENT,
+                                walk_schedule=pkg.SCHED_PREDICTED, walk_chunk=256,
+                                model=pred.model.data_ptr())
+        learned = arm(lp)
+        n = learned["per_step"]["hsps"]
+        learned["bit_exact_vs_plain"] = bool(n == plain_out.shape[0] and
+                                             torch.equal(out[:n], plain_out))
+        learned["walk"] = "persistent, chunks of 256 hits ordered by predicted work"
+        learned["predictor"] = {"train_workload": f"large_pair_100mb seed {a.train_seed} "
+                                                  f"at scale 0.2", "train_s": round(train_s, 1)}
+        res["learned_binned"] = learned
+    res["clocks"] = clocks.stop()
+    ctx.close()
+    return res
 
 
 def main():

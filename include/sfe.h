@@ -54,7 +54,8 @@ extern "C" {
 #define SFE_EINVAL (-1)    /* bad argument or symbol */
 #define SFE_ENOMEM (-2)    /* device allocation failed */
 #define SFE_ECUDA (-3)     /* a CUDA call failed */
-#define SFE_ETIMEOUT (-4)  /* a bounded device wait ran out */
+#define SFE_ETIMEOUT (-4)  /* a bounded device wait ran out (kept for the ABI; the persistent
+                              walk now hands late entries to a follow-up launch instead) */
 #define SFE_EOVERFLOW (-5) /* output capacity too small (needed count returned), or a score left int32 */
 #define SFE_ELIMIT (-6)    /* input larger than the fixed scratch of sfe_ungapped_xdrop_static */
 
@@ -126,18 +127,21 @@ typedef struct {
                                  (pair, strand, t, q), so it does not depend on the schedule */
     int64_t ext_log_cap;      /* records the buffer holds (further ones are counted, not written) */
     const void *model;        /* device weights of the work predictor (SFE_SCHED_PREDICTED) */
-    int32_t wait_limit;       /* polls of a bounded device wait (the persistent walk's hand-off
-                                 queue, at most about 1 us each) before the call fails with
-                                 SFE_ETIMEOUT; 0 = default (2^23) */
+    int32_t wait_limit;       /* polls (at most about 1 us each) a warp of the persistent walk
+                                 waits for a hand-off entry to be published before it leaves
+                                 that entry and the rest of the queue to a follow-up warp
+                                 launch on the same stream (the output is the same either way;
+                                 see stats.deferred_tasks); 0 = default (2^20) */
     int32_t test_hooks;       /* SFE_TEST_* bits; 0 in normal use */
 } sfe_params;
 
 /* sfe_params.test_hooks (no counterpart in the paper: they let tests drive the
- * library's error paths without faulting a GPU). SFE_TEST_UNPUBLISHED_QUEUE_ENTRY
+ * library's recovery paths without faulting a GPU). SFE_TEST_UNPUBLISHED_QUEUE_ENTRY
  * reserves one slot of the persistent walk's hand-off queue that is never
- * written, so the warp that takes it waits until wait_limit runs out and the
- * call returns SFE_ETIMEOUT (all other work completes; the context stays
- * usable). */
+ * written, as if its producer had not run yet: the warp that takes it waits
+ * until wait_limit runs out and leaves the queue to the follow-up launch, which
+ * skips the slot (it holds no task); the output is the oracle's all the same
+ * and stats.deferred_tasks counts the warps that gave up. */
 #define SFE_TEST_UNPUBLISHED_QUEUE_ENTRY 1
 
 /* sfe_params.walk_schedule: the order of work never changes the output, only
@@ -170,6 +174,8 @@ typedef struct {
                              cells) */
     double stage_ms[SFE_NSTAGES];        /* device time per stage (with SFE_TIME_STAGES) */
     int64_t stage_launches[SFE_NSTAGES]; /* kernels launched per stage (with SFE_TIME_STAGES) */
+    int64_t deferred_tasks; /* persistent walk: warps that stopped waiting for a hand-off entry
+                               and left the rest of the queue to the follow-up warp launch */
 } sfe_stats;
 
 /* Fill *p with the defaults: 12of19 with one transition, both strands,

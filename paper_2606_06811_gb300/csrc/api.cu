@@ -481,7 +481,7 @@ int walk_tiers(sfe_ctx *c, const uint64_t *hits, long long n, WalkParams &wp, ui
     wp.queue_take = &sm->queue_take;
     wp.chunk = p->walk_chunk > 0 ? (uint32_t)p->walk_chunk : walk_auto_chunk(n);
     wp.order = nullptr;
-    wp.spin_limit = p->wait_limit > 0 ? p->wait_limit : (1LL << 23);
+    wp.spin_limit = p->wait_limit > 0 ? p->wait_limit : (1LL << 20);
     wp.phantom = (p->test_hooks & SFE_TEST_UNPUBLISHED_QUEUE_ENTRY) ? 1 : 0;
     if (p->walk_schedule != SFE_SCHED_NATURAL) {
         Span sp(c, SFE_STAGE_SCHEDULE);
@@ -492,10 +492,19 @@ int walk_tiers(sfe_ctx *c, const uint64_t *hits, long long n, WalkParams &wp, ui
                                 &sm->status, c->st));
         wp.order = order;
     }
-    Span sp(c, SFE_STAGE_WALK_LANES);
-    CK(cudaMemsetAsync(&sm->work_next, 0, 12, c->st));
-    CK(cudaMemsetAsync(queue, 0, (size_t)qcap * sizeof(uint4), c->st));
-    CK(launch_walk_persistent(hits, n, wp, c->st));
+    {
+        Span sp(c, SFE_STAGE_WALK_LANES);
+        CK(cudaMemsetAsync(&sm->work_next, 0, 12, c->st));
+        CK(cudaMemsetAsync(queue, 0, (size_t)qcap * sizeof(uint4), c->st));
+        CK(launch_walk_persistent(hits, n, wp, c->st));
+    }
+    // entries whose consumers gave up waiting (the persistent grid does not
+    // fit on the device at once, e.g. next to another kernel) are walked here,
+    // after every producer has finished; normally nothing is left
+    Span sp(c, SFE_STAGE_WALK_WARPS);
+    WalkParams fu = wp;
+    fu.deferred_only = 1;
+    CK(launch_walk_warps(hits, n, fu, 2 * device_sms() * (BLOCK / 32), c->st));
     return SFE_OK;
 }
 
@@ -555,6 +564,7 @@ void fill_stats(const Small &s, sfe_stats *st, long long hits, long long tiles) 
     st->warp_cells = (int64_t)s.ctr.warp_cells;
     st->ext_logged = (int64_t)s.ctr.ext_logged;
     st->shadow_cells = (int64_t)s.ctr.shadow;
+    st->deferred_tasks = (int64_t)s.ctr.deferred;
     st->tiles = tiles;
 }
 

@@ -50,6 +50,7 @@ struct DevCounters {
     unsigned long long warp_cells; // cells scored by the warp tier
     unsigned long long ext_logged; // extensions selected for the extension log
     unsigned long long shadow;     // lane cells of extensions handed to the warp tier
+    unsigned long long deferred;   // hand-off entries left to the follow-up warp launch
     unsigned int status;
     unsigned int pad;
 };
@@ -230,8 +231,12 @@ struct WalkParams {
     // hit count in device memory (at most the launch's n), for launches that
     // must not wait for the host (graph replay); null: the launch's n
     const unsigned long long *nd;
-    long long spin_limit;  // polls of the hand-off queue before ST_TIMEOUT
+    long long spin_limit;  // polls of a hand-off entry before its consumer leaves it (and the
+                           // rest of the queue) to the follow-up warp launch
     int phantom;           // test hook: reserve one queue slot that is never written
+    // follow-up warp launch after a persistent walk: only entries published by
+    // this call (z == epoch) that no consumer finished (w != epoch)
+    int deferred_only;
     // sampled log of extensions (elog == nullptr: none)
     sfe_ext_record *elog;
     unsigned long long elog_cap;

@@ -509,13 +509,13 @@ __global__ void __launch_bounds__(W_BLOCK, PERSIST ? 1 : 0) walk_lanes_kernel(co
         __threadfence();
         if (lane == 0) atomicAdd(wp.warps_done, 1u);
         const unsigned total_warps = gridDim.x * (W_BLOCK / 32);
-        unsigned long long wext = 0, wcells = 0, wtasks = 0;
+        unsigned long long wext = 0, wcells = 0, wtasks = 0, wdeferred = 0;
         while (true) {
             unsigned e = 0;
             if (lane == 0) e = atomicAdd(wp.queue_take, 1u);
             e = __shfl_sync(0xffffffffu, e, 0);
             if (e >= wp.queue_cap) break;
-            int state = 0;  // 1: entry ready, 2: no entry will come
+            int state = 0;  // 1: entry ready, 2: no entry will come, 3: waited too long
             long long spins = 0;
             unsigned backoff = 32;  // ns: a waiting warp leaves the issue slots to working ones
             while (state == 0) {
@@ -527,10 +527,8 @@ __global__ void __launch_bounds__(W_BLOCK, PERSIST ? 1 : 0) walk_lanes_kernel(co
                         const unsigned wd = *(volatile unsigned *)wp.warps_done;
                         const unsigned ql = *(volatile unsigned *)wp.queue_len;
                         if (wd >= total_warps && e >= min(ql, (unsigned)wp.queue_cap)) state = 2;
-                        else if (++spins > wp.spin_limit) {
-                            status |= ST_TIMEOUT;
-                            state = 2;
-                        } else {
+                        else if (++spins > wp.spin_limit) state = 3;
+                        else {
                             __nanosleep(backoff);
                             backoff = min(backoff * 2u, 1024u);
                         }
@@ -538,13 +536,19 @@ __global__ void __launch_bounds__(W_BLOCK, PERSIST ? 1 : 0) walk_lanes_kernel(co
                 }
                 state = __shfl_sync(0xffffffffu, state, 0);
             }
-            if (state == 2) break;
+            // An entry whose producer has not published it in time (its CTA
+            // may not be resident yet while this one waits) is left, with the
+            // rest of the queue, to the follow-up warp launch on the same
+            // stream, which runs after every producer has finished.
+            if (state == 3) wdeferred++;
+            if (state != 1) break;
             __threadfence();
             volatile uint4 *qe = wp.queue + e;
             const uint32_t hi_idx = qe->x;
             const int hi_E = (int)qe->y;
             wtasks++;
             warp_walk_diagonal<BATCH>(hits, n, hi_idx, hi_E, wp, lut, lane, wext, wcells, status);
+            if (lane == 0) qe->w = wp.epoch;  // done: the follow-up launch skips it
         }
         if (lane == 0) {
             if (wext) atomicAdd(&wp.ctr->extended, wext);
@@ -553,6 +557,7 @@ __global__ void __launch_bounds__(W_BLOCK, PERSIST ? 1 : 0) walk_lanes_kernel(co
                 atomicAdd(&wp.ctr->warp_cells, wcells);
             }
             if (wtasks) atomicAdd(&wp.ctr->warp_tasks, wtasks);
+            if (wdeferred) atomicAdd(&wp.ctr->deferred, wdeferred);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) status |= __shfl_down_sync(0xffffffffu, status, o);
@@ -678,6 +683,9 @@ __global__ void __launch_bounds__(W_BLOCK) walk_warps_kernel(const uint64_t *__r
     uint32_t status = 0;
     for (long long e = warp; e < (long long)nq; e += nwarps) {
         const uint4 it = wp.queue[e];
+        // after a persistent walk: only the entries its consumers left (a slot
+        // reserved but never published is skipped: it holds no task)
+        if (wp.deferred_only && (it.z != wp.epoch || it.w == wp.epoch)) continue;
         tasks++;
         warp_walk_diagonal<BATCH>(hits, nhits, it.x, (int)it.y, wp, lut, lane, ext, cells, status);
     }

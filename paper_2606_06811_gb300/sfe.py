@@ -57,12 +57,14 @@ class Stats(C.Structure):
                 ("warp_cells", C.c_int64), ("tiles", C.c_int64), ("launches", C.c_int64),
                 ("ext_logged", C.c_int64), ("shadow_cells", C.c_int64),
                 ("stage_ms", C.c_double * len(STAGES)),
-                ("stage_launches", C.c_int64 * len(STAGES))]
+                ("stage_launches", C.c_int64 * len(STAGES)),
+                ("deferred_tasks", C.c_int64)]
 
     def as_dict(self) -> dict:
         d = {k: int(getattr(self, k)) for k, _ in self._fields_[:11]}
         d["stage_ms"] = {n: float(self.stage_ms[i]) for i, n in enumerate(STAGES)}
         d["stage_launches"] = {n: int(self.stage_launches[i]) for i, n in enumerate(STAGES)}
+        d["deferred_tasks"] = int(self.deferred_tasks)
         return d
 
 
