@@ -316,6 +316,70 @@ __device__ void warp_walk_diagonal(const uint64_t *__restrict__ hits, uint32_t n
                                    unsigned long long &ext, unsigned long long &cells,
                                    uint32_t &status);
 
+// The warp tier of the persistent walk: a warp whose lanes are out of lane
+// work takes hand-off entries in order and finishes each entry's diagonal.
+// An entry whose producer has not published it in time (its CTA may not be
+// resident yet while this one waits) is left, with the rest of the queue, to
+// the follow-up warp launch on the same stream, which runs after every
+// producer has finished.
+template <bool BATCH>
+__device__ __forceinline__ void drain_queue(const uint64_t *__restrict__ hits, uint32_t n,
+                                            const WalkParams &wp, const int *lut, int lane,
+                                            uint32_t &status) {
+    // this warp's lanes are out of work: consume the hand-off queue
+    __threadfence();
+    if (lane == 0) atomicAdd(wp.warps_done, 1u);
+    const unsigned total_warps = gridDim.x * (W_BLOCK / 32);
+    unsigned long long wext = 0, wcells = 0, wtasks = 0, wdeferred = 0;
+    while (true) {
+        unsigned e = 0;
+        if (lane == 0) e = atomicAdd(wp.queue_take, 1u);
+        e = __shfl_sync(0xffffffffu, e, 0);
+        if (e >= wp.queue_cap) break;
+        int state = 0;  // 1: entry ready, 2: no entry will come, 3: waited too long
+        long long spins = 0;
+        unsigned backoff = 32;  // ns: a waiting warp leaves the issue slots to working ones
+        while (state == 0) {
+            if (lane == 0) {
+                volatile uint4 *qe = wp.queue + e;
+                if (qe->z == wp.epoch) {
+                    state = 1;
+                } else {
+                    const unsigned wd = *(volatile unsigned *)wp.warps_done;
+                    const unsigned ql = *(volatile unsigned *)wp.queue_len;
+                    if (wd >= total_warps && e >= min(ql, (unsigned)wp.queue_cap)) state = 2;
+                    else if (++spins > wp.spin_limit) state = 3;
+                    else {
+                        __nanosleep(backoff);
+                        backoff = min(backoff * 2u, 1024u);
+                    }
+                }
+            }
+            state = __shfl_sync(0xffffffffu, state, 0);
+        }
+        if (state == 3) wdeferred++;
+        if (state != 1) break;
+        __threadfence();
+        volatile uint4 *qe = wp.queue + e;
+        const uint32_t hi_idx = qe->x;
+        const int hi_E = (int)qe->y;
+        wtasks++;
+        warp_walk_diagonal<BATCH>(hits, n, hi_idx, hi_E, wp, lut, lane, wext, wcells, status);
+        if (lane == 0) qe->w = wp.epoch;  // done: the follow-up launch skips it
+    }
+    if (lane == 0) {
+        if (wext) atomicAdd(&wp.ctr->extended, wext);
+        if (wcells) {
+            atomicAdd(&wp.ctr->cells, wcells);
+            atomicAdd(&wp.ctr->warp_cells, wcells);
+        }
+        if (wtasks) atomicAdd(&wp.ctr->warp_tasks, wtasks);
+        if (wdeferred) atomicAdd(&wp.ctr->deferred, wdeferred);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) status |= __shfl_down_sync(0xffffffffu, status, o);
+}
+
 // Lane tier. Lane k owns the diagonals that start in hit range
 // [k*chunk, (k+1)*chunk) and streams through its hits in order, with the next
 // hit prefetched. The lanes of a warp advance in lock step, one iteration at
@@ -504,64 +568,7 @@ __global__ void __launch_bounds__(W_BLOCK, PERSIST ? 1 : 0) walk_lanes_kernel(co
         if (tasks) atomicAdd(&wp.ctr->lane_tasks, tasks);
         if (shadow) atomicAdd(&wp.ctr->shadow, shadow);
     }
-    if (PERSIST) {
-        // this warp's lanes are out of work: consume the hand-off queue
-        __threadfence();
-        if (lane == 0) atomicAdd(wp.warps_done, 1u);
-        const unsigned total_warps = gridDim.x * (W_BLOCK / 32);
-        unsigned long long wext = 0, wcells = 0, wtasks = 0, wdeferred = 0;
-        while (true) {
-            unsigned e = 0;
-            if (lane == 0) e = atomicAdd(wp.queue_take, 1u);
-            e = __shfl_sync(0xffffffffu, e, 0);
-            if (e >= wp.queue_cap) break;
-            int state = 0;  // 1: entry ready, 2: no entry will come, 3: waited too long
-            long long spins = 0;
-            unsigned backoff = 32;  // ns: a waiting warp leaves the issue slots to working ones
-            while (state == 0) {
-                if (lane == 0) {
-                    volatile uint4 *qe = wp.queue + e;
-                    if (qe->z == wp.epoch) {
-                        state = 1;
-                    } else {
-                        const unsigned wd = *(volatile unsigned *)wp.warps_done;
-                        const unsigned ql = *(volatile unsigned *)wp.queue_len;
-                        if (wd >= total_warps && e >= min(ql, (unsigned)wp.queue_cap)) state = 2;
-                        else if (++spins > wp.spin_limit) state = 3;
-                        else {
-                            __nanosleep(backoff);
-                            backoff = min(backoff * 2u, 1024u);
-                        }
-                    }
-                }
-                state = __shfl_sync(0xffffffffu, state, 0);
-            }
-            // An entry whose producer has not published it in time (its CTA
-            // may not be resident yet while this one waits) is left, with the
-            // rest of the queue, to the follow-up warp launch on the same
-            // stream, which runs after every producer has finished.
-            if (state == 3) wdeferred++;
-            if (state != 1) break;
-            __threadfence();
-            volatile uint4 *qe = wp.queue + e;
-            const uint32_t hi_idx = qe->x;
-            const int hi_E = (int)qe->y;
-            wtasks++;
-            warp_walk_diagonal<BATCH>(hits, n, hi_idx, hi_E, wp, lut, lane, wext, wcells, status);
-            if (lane == 0) qe->w = wp.epoch;  // done: the follow-up launch skips it
-        }
-        if (lane == 0) {
-            if (wext) atomicAdd(&wp.ctr->extended, wext);
-            if (wcells) {
-                atomicAdd(&wp.ctr->cells, wcells);
-                atomicAdd(&wp.ctr->warp_cells, wcells);
-            }
-            if (wtasks) atomicAdd(&wp.ctr->warp_tasks, wtasks);
-            if (wdeferred) atomicAdd(&wp.ctr->deferred, wdeferred);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) status |= __shfl_down_sync(0xffffffffu, status, o);
-    }
+    if (PERSIST) drain_queue<BATCH>(hits, n, wp, lut, lane, status);
     if (lane == 0 && status) atomicOr(&wp.ctr->status, status);
 }
 

@@ -230,21 +230,39 @@ def test_walk_modes_chunks_and_schedules(pkg, ctx, mode, chunk, sched, cap):
 
 
 @pytest.mark.parametrize("n,m", [(19, 19), (20, 27), (33, 41), (9_001, 7_333), (60_007, 40_003)])
-@pytest.mark.parametrize("planes", [True, False])
-def test_cell_planes_and_two_bit_windows_agree(pkg, ctx, n, m, planes):
-    """The lane windows read either the 4-bit cell planes (forward and
-    reversed copies of T and of each query strand) or the 2-bit words; both
-    give the oracle's output, on lengths with ragged ends of the planes'
-    8-base words and of the 2-bit words' 16-base words."""
+@pytest.mark.parametrize("windows", ["planes", "two_bit"])
+def test_window_sources_agree(pkg, ctx, n, m, windows):
+    """The lane windows of one pair's walk come from the 4-bit cell planes
+    (the default where they fit) or from the 2-bit words; each gives the
+    oracle's output, on lengths with ragged ends of the planes' 8-base words
+    and of the 2-bit words' 16-base words, with hits next to both ends."""
     T, Q = _pair(40 + n % 7, n, m, blocks=6)
     ref = oracle.run(T, Q)
-    flags = 0 if planes else pkg.NO_CELL_PLANES
-    got, st = ctx.run(T, Q, pkg.default_params(input_codes=1, flags=flags, lane_cap=16))
-    assert_same(got, st, ref)
+    flags = {"planes": 0, "two_bit": pkg.NO_CELL_PLANES}[windows]
+    for cap in (16, 0):
+        got, st = ctx.run(T, Q, pkg.default_params(input_codes=1, flags=flags, lane_cap=cap))
+        assert_same(got, st, ref)
     # the same with the skip advanced only by passing HSPs
     ref = oracle.run(T, Q, flags=1)
     got, st = ctx.run(T, Q, pkg.default_params(input_codes=1, flags=flags | 1))
     assert_same(got, st, ref)
+
+
+@pytest.mark.parametrize("chunk", [1, 2, 7, 64])
+def test_persistent_walk_chunk_starts_and_skips(pkg, ctx, chunk):
+    """Persistent walk with tiny chunks (a chunk boundary at almost every hit,
+    diagonals that start before their chunk) and on nearly identical
+    sequences (long runs of skipped hits)."""
+    st = synth.Stream(33, "ident3")
+    T = synth.iid_bases(st, 20_000, 0.5)
+    Q = T.copy()
+    Q[5000:5400] = synth.iid_bases(st.child("q"), 400, 0.5)
+    got, stt, ref = run_both(pkg, ctx, T, Q, walk_mode=pkg.WALK_PERSISTENT, walk_chunk=chunk,
+                             lane_cap=64)
+    assert_same(got, stt, ref)
+    p = synth.tiny_pair(3, length=50_000, n_blocks=12)
+    got, stt, ref = run_both(pkg, ctx, p.T, p.Q, walk_mode=pkg.WALK_PERSISTENT, walk_chunk=chunk)
+    assert_same(got, stt, ref)
 
 
 def test_persistent_walk_on_identical_sequences(pkg, ctx):
