@@ -70,18 +70,18 @@ def _bind(path: str):
     L.or_encode.restype = C.c_int
     L.or_revcomp.argtypes = [u8p, C.c_int64, u8p]
     L.or_revcomp.restype = None
-    L.or_run.argtypes = [u8p, C.c_int64, u8p, C.c_int64, C.c_char_p, C.c_int, C.c_int,
+    L.or_run.argtypes = [u8p, C.c_int64, u8p, C.c_int64, C.c_char_p, C.c_int, C.c_int, C.c_int,
                          i32p, C.c_int32, C.c_int32, C.c_int, C.c_int, C.POINTER(C.c_int)]
     L.or_run.restype = C.c_void_p
     L.or_run_par.argtypes = [u8p, C.c_int64, u8p, C.c_int64, C.c_char_p, C.c_int, C.c_int,
-                             i32p, C.c_int32, C.c_int32, C.c_int, C.c_int64, C.c_int,
+                             C.c_int, i32p, C.c_int32, C.c_int32, C.c_int, C.c_int64, C.c_int,
                              C.POINTER(C.c_int)]
     L.or_run_par.restype = C.c_void_p
     L.or_run_diagonal.argtypes = [u8p, C.c_int64, u8p, C.c_int64, C.c_int, C.c_int64,
-                                  C.c_int64, C.c_char_p, C.c_int, i32p, C.c_int32,
+                                  C.c_int64, C.c_char_p, C.c_int, C.c_int, i32p, C.c_int32,
                                   C.c_int32, C.c_int, C.c_int, C.POINTER(C.c_int)]
     L.or_run_diagonal.restype = C.c_void_p
-    L.or_seed_hits.argtypes = [u8p, C.c_int64, u8p, C.c_int64, C.c_char_p, C.c_int,
+    L.or_seed_hits.argtypes = [u8p, C.c_int64, u8p, C.c_int64, C.c_char_p, C.c_int, C.c_int,
                                i64p, i64p, C.c_int64, C.POINTER(C.c_int)]
     L.or_seed_hits.restype = C.c_int64
     L.or_xdrop.argtypes = [u8p, C.c_int64, u8p, C.c_int64, C.c_int64, C.c_int64, C.c_int,
@@ -215,23 +215,24 @@ def _collect(h, err, keep_log) -> Result:
 
 def run(T, Q, pattern: str = DEFAULT_PATTERN, transition: bool = True, strands: int = 3,
         scores=HOXD70, X: int = XDROP, thresh: int = HSP_THRESH, flags: int = 0,
-        keep_log: bool = False) -> Result:
-    """The filter stage on one pair: hits -> per-diagonal skip -> X-drop -> sorted HSPs."""
+        keep_log: bool = False, step: int = 1) -> Result:
+    """The filter stage on one pair: hits -> per-diagonal skip -> X-drop -> sorted HSPs.
+    step: index stride (only target positions t % step == 0 are seeds)."""
     if _parallel is not None and not keep_log:
         return run_par(T, Q, pattern, transition, strands, scores, X, thresh, flags,
-                       qtile=_parallel[0], threads=_parallel[1])
+                       qtile=_parallel[0], threads=_parallel[1], step=step)
     T, Q = _u8(T), _u8(Q)
     M = _scores(scores)
     err = C.c_int(0)
     h = lib().or_run(_ptr(T, C.c_uint8), T.size, _ptr(Q, C.c_uint8), Q.size, pattern.encode(),
-                     int(transition), int(strands), _ptr(M, C.c_int32), int(X), int(thresh),
-                     int(flags), int(keep_log), C.byref(err))
+                     int(step), int(transition), int(strands), _ptr(M, C.c_int32), int(X),
+                     int(thresh), int(flags), int(keep_log), C.byref(err))
     return _collect(h, err, keep_log)
 
 
 def run_par(T, Q, pattern: str = DEFAULT_PATTERN, transition: bool = True, strands: int = 3,
             scores=HOXD70, X: int = XDROP, thresh: int = HSP_THRESH, flags: int = 0,
-            qtile: int = 0, threads: int = 0) -> Result:
+            qtile: int = 0, threads: int = 0, step: int = 1) -> Result:
     """run() on several threads (or_run_par): query tiles of qtile positions
     (0: one tile), the skip state carried across tiles, blocks of diagonals
     walked in parallel; threads 0 = every core OpenMP offers. Same result as
@@ -240,7 +241,8 @@ def run_par(T, Q, pattern: str = DEFAULT_PATTERN, transition: bool = True, stran
     M = _scores(scores)
     err = C.c_int(0)
     h = lib().or_run_par(_ptr(T, C.c_uint8), T.size, _ptr(Q, C.c_uint8), Q.size,
-                         pattern.encode(), int(transition), int(strands), _ptr(M, C.c_int32),
+                         pattern.encode(), int(step), int(transition), int(strands),
+                         _ptr(M, C.c_int32),
                          int(X), int(thresh), int(flags), int(qtile), int(threads),
                          C.byref(err))
     return _collect(h, err, False)
@@ -257,33 +259,36 @@ def host_cores() -> int:
 
 def run_diagonal(T, Qs, strand: int, d: int, E0: int = -(1 << 62), pattern: str = DEFAULT_PATTERN,
                  transition: bool = True, scores=HOXD70, X: int = XDROP,
-                 thresh: int = HSP_THRESH, flags: int = 0, keep_log: bool = False) -> Result:
+                 thresh: int = HSP_THRESH, flags: int = 0, keep_log: bool = False,
+                 step: int = 1) -> Result:
     """The walk restricted to diagonal d = t - q of Qs (Qs already strand-oriented)."""
     T, Qs = _u8(T), _u8(Qs)
     M = _scores(scores)
     err = C.c_int(0)
     h = lib().or_run_diagonal(_ptr(T, C.c_uint8), T.size, _ptr(Qs, C.c_uint8), Qs.size,
-                              int(strand), int(d), int(E0), pattern.encode(), int(transition),
+                              int(strand), int(d), int(E0), pattern.encode(), int(step),
+                              int(transition),
                               _ptr(M, C.c_int32), int(X), int(thresh), int(flags),
                               int(keep_log), C.byref(err))
     return _collect(h, err, keep_log)
 
 
-def seed_hits(T, Qs, pattern: str = DEFAULT_PATTERN, transition: bool = True):
+def seed_hits(T, Qs, pattern: str = DEFAULT_PATTERN, transition: bool = True, step: int = 1):
     """All hits (t, q) of T against the strand-oriented Qs, sorted by (t - q, t)."""
     T, Qs = _u8(T), _u8(Qs)
     err = C.c_int(0)
     L = lib()
     empty = np.zeros(1, dtype=np.int64)
     n = L.or_seed_hits(_ptr(T, C.c_uint8), T.size, _ptr(Qs, C.c_uint8), Qs.size,
-                       pattern.encode(), int(transition), _ptr(empty, C.c_int64),
+                       pattern.encode(), int(step), int(transition), _ptr(empty, C.c_int64),
                        _ptr(empty, C.c_int64), 0, C.byref(err))
     if n < 0:
         raise RuntimeError(f"oracle error {err.value}")
     t = np.zeros(max(n, 1), dtype=np.int64)
     q = np.zeros(max(n, 1), dtype=np.int64)
     L.or_seed_hits(_ptr(T, C.c_uint8), T.size, _ptr(Qs, C.c_uint8), Qs.size, pattern.encode(),
-                   int(transition), _ptr(t, C.c_int64), _ptr(q, C.c_int64), n, C.byref(err))
+                   int(step), int(transition), _ptr(t, C.c_int64), _ptr(q, C.c_int64), n,
+                   C.byref(err))
     return t[:n], q[:n]
 
 

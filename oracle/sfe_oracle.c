@@ -19,7 +19,9 @@
  *  every care offset c, T[t+c] equals Qs[q+c], except that with transition
  *  tolerance (Section 2) at most one care offset may hold a transition
  *  (T[t+c] == Qs[q+c]^2). Q+ = Q; Q- = reverse complement of Q, and minus-strand
- *  coordinates index Q-.
+ *  coordinates index Q-. With a step s > 1 (Section 7: the spacing between
+ *  seeds), only target positions t with t % s == 0 are in the position table,
+ *  so only they start hits.
  *
  *  Skip (Algorithm 1, the IsContained test; the masking-list update): hits are
  *  processed per (strand, diagonal d = t - q) in increasing t. A hit with
@@ -70,6 +72,7 @@ typedef struct {
 typedef struct {
     int span, weight;
     int care[32];
+    int step; /* index stride: only target positions t with t % step == 0 are seeds */
 } or_pattern;
 
 /* ---------------------------------------------------------------- basics */
@@ -101,6 +104,7 @@ int or_parse_pattern(const char *s, or_pattern *p)
         return OR_EINVAL;
     p->span = n;
     p->weight = 0;
+    p->step = 1;
     for (int i = 0; i < n; i++) {
         if (s[i] == '1')
             p->care[p->weight++] = i;
@@ -203,7 +207,8 @@ static int cmp_diag_t(const void *a, const void *b)
 
 /*
  * The position table of the target: (seed key, position) for every position
- * t in [0, tlen - span], sorted by key and then position. With nthreads > 1
+ * t in [0, tlen - span] with t % step == 0, sorted by key and then position.
+ * With nthreads > 1
  * the entries are first split by the top bits of their key (a stable
  * counting pass) and each part is sorted on its own thread; the order of
  * (key, position) pairs is total, so the table is the same either way.
@@ -215,13 +220,14 @@ static int build_table(const uint8_t *T, int64_t tlen, const or_pattern *p, int 
     *nt_out = 0;
     if (tlen < p->span)
         return OR_OK;
-    int64_t nt = tlen - p->span + 1;
+    int64_t npos = tlen - p->span + 1;
+    int64_t nt = (npos + p->step - 1) / p->step;
     or_entry *tab = (or_entry *)malloc((size_t)nt * sizeof(or_entry));
     if (!tab)
         return OR_ENOMEM;
-    for (int64_t t = 0; t < nt; t++) {
-        tab[t].key = seed_key(T, t, p);
-        tab[t].pos = t;
+    for (int64_t j = 0; j < nt; j++) {
+        tab[j].key = seed_key(T, j * p->step, p);
+        tab[j].pos = j * p->step;
     }
     if (nthreads <= 1) {
         qsort(tab, (size_t)nt, sizeof(or_entry), cmp_entry);
@@ -441,15 +447,16 @@ static int walk(const uint8_t *T, int64_t tlen, const uint8_t *Qs, int64_t qlen,
  * bit 1 = minus strand. Returns a result handle (NULL on error, with *err set).
  */
 or_result *or_run(const uint8_t *T, int64_t tlen, const uint8_t *Q, int64_t qlen,
-                  const char *pattern, int transition, int strands, const int32_t *M,
+                  const char *pattern, int step, int transition, int strands, const int32_t *M,
                   int32_t X, int32_t thresh, int flags, int keep_log, int *err)
 {
     or_pattern p;
     *err = OR_OK;
-    if (or_parse_pattern(pattern, &p) || X < 0 || tlen < 0 || qlen < 0) {
+    if (or_parse_pattern(pattern, &p) || step < 1 || X < 0 || tlen < 0 || qlen < 0) {
         *err = OR_EINVAL;
         return NULL;
     }
+    p.step = step;
     or_result *r = (or_result *)calloc(1, sizeof(or_result));
     if (!r) {
         *err = OR_ENOMEM;
@@ -509,16 +516,17 @@ or_result *or_run(const uint8_t *T, int64_t tlen, const uint8_t *Q, int64_t qlen
  * nthreads <= 0: all threads OpenMP offers (1 without OpenMP).
  */
 or_result *or_run_par(const uint8_t *T, int64_t tlen, const uint8_t *Q, int64_t qlen,
-                      const char *pattern, int transition, int strands, const int32_t *M,
-                      int32_t X, int32_t thresh, int flags, int64_t qtile, int nthreads,
-                      int *err)
+                      const char *pattern, int step, int transition, int strands,
+                      const int32_t *M, int32_t X, int32_t thresh, int flags, int64_t qtile,
+                      int nthreads, int *err)
 {
     or_pattern p;
     *err = OR_OK;
-    if (or_parse_pattern(pattern, &p) || X < 0 || tlen < 0 || qlen < 0) {
+    if (or_parse_pattern(pattern, &p) || step < 1 || X < 0 || tlen < 0 || qlen < 0) {
         *err = OR_EINVAL;
         return NULL;
     }
+    p.step = step;
     if (nthreads <= 0) {
 #ifdef _OPENMP
         nthreads = omp_get_max_threads();
@@ -664,13 +672,13 @@ done:
  * sampled checks on inputs too large for or_run.
  */
 or_result *or_run_diagonal(const uint8_t *T, int64_t tlen, const uint8_t *Qs, int64_t qlen,
-                           int strand, int64_t d, int64_t E0, const char *pattern,
+                           int strand, int64_t d, int64_t E0, const char *pattern, int step,
                            int transition, const int32_t *M, int32_t X, int32_t thresh,
                            int flags, int keep_log, int *err)
 {
     or_pattern p;
     *err = OR_OK;
-    if (or_parse_pattern(pattern, &p) || X < 0) {
+    if (or_parse_pattern(pattern, &p) || step < 1 || X < 0) {
         *err = OR_EINVAL;
         return NULL;
     }
@@ -684,7 +692,7 @@ or_result *or_run_diagonal(const uint8_t *T, int64_t tlen, const uint8_t *Qs, in
     int64_t t0 = d > 0 ? d : 0;
     for (int64_t t = t0; t + p.span <= tlen && t - d + p.span <= qlen; t++) {
         int64_t q = t - d;
-        if (!or_is_hit(T, Qs, t, q, &p, transition))
+        if (t % step != 0 || !or_is_hit(T, Qs, t, q, &p, transition))
             continue;
         r->st.hits++;
         if (t < E)
@@ -723,15 +731,16 @@ or_result *or_run_diagonal(const uint8_t *T, int64_t tlen, const uint8_t *Qs, in
 
 /* Seed hits of one strand, sorted by (diagonal, t): writes up to cap pairs. */
 int64_t or_seed_hits(const uint8_t *T, int64_t tlen, const uint8_t *Qs, int64_t qlen,
-                     const char *pattern, int transition, int64_t *t_out, int64_t *q_out,
-                     int64_t cap, int *err)
+                     const char *pattern, int step, int transition, int64_t *t_out,
+                     int64_t *q_out, int64_t cap, int *err)
 {
     or_pattern p;
     *err = OR_OK;
-    if (or_parse_pattern(pattern, &p)) {
+    if (or_parse_pattern(pattern, &p) || step < 1) {
         *err = OR_EINVAL;
         return -1;
     }
+    p.step = step;
     tq_vec h;
     int e = enumerate_hits(T, tlen, Qs, qlen, &p, transition, &h);
     if (e) {

@@ -19,8 +19,9 @@ def revcomp(x: np.ndarray) -> np.ndarray:
     return comp[np.asarray(x, dtype=np.uint8)][::-1].copy()
 
 
-def hits_by_diagonal(T, Qs, pattern: str, transition: bool):
-    """Every (t, q) hit by testing every window of every diagonal. O(|T||Q|)."""
+def hits_by_diagonal(T, Qs, pattern: str, transition: bool, step: int = 1):
+    """Every (t, q) hit by testing every window of every diagonal. O(|T||Q|).
+    With a step, only windows that start at a target position divisible by it."""
     T = np.asarray(T, dtype=np.int16)
     Qs = np.asarray(Qs, dtype=np.int16)
     span = len(pattern)
@@ -55,6 +56,8 @@ def hits_by_diagonal(T, Qs, pattern: str, transition: bool):
         return np.zeros(0, np.int64), np.zeros(0, np.int64)
     t = np.concatenate(ts).astype(np.int64)
     q = np.concatenate(qs).astype(np.int64)
+    keep = t % step == 0
+    t, q = t[keep], q[keep]
     order = np.lexsort((t, t - q))
     return t[order], q[order]
 
@@ -95,7 +98,8 @@ def extend(T, Qs, t: int, q: int, span: int, M, X: int) -> dict:
             "end": t + span + rl, "cells": span + rs + ls}
 
 
-def serial_query_order(T, Q, pattern, transition, strands, M, X, thresh, skip_passing_only=False):
+def serial_query_order(T, Q, pattern, transition, strands, M, X, thresh, skip_passing_only=False,
+                       step=1):
     """Algorithm 1's shape: one pass over the hits in query order, with a masking
     state kept per (strand, diagonal). Hits from `hits_by_diagonal`, extensions
     from `extend` above."""
@@ -106,7 +110,7 @@ def serial_query_order(T, Q, pattern, transition, strands, M, X, thresh, skip_pa
         if not strands & (1 << s):
             continue
         Qs = Q if s == 0 else revcomp(Q)
-        t, q = hits_by_diagonal(T, Qs, pattern, transition)
+        t, q = hits_by_diagonal(T, Qs, pattern, transition, step)
         order = np.lexsort((t, q))
         E = {}
         for i in order:

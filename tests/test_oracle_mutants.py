@@ -30,8 +30,8 @@ PAR_QTILE, PAR_THREADS = 97, 3  # tiles of 97 query positions on 3 threads
 # (name, old text, new text, occurrences to replace: 0 = all[, forms that must reject it])
 MUTANTS = [
     # range edges: the last target or query position, the last base of a side
-    ("last_target_position_dropped", "int64_t nt = tlen - p->span + 1;",
-     "int64_t nt = tlen - p->span;", 1),
+    ("last_target_position_dropped", "int64_t npos = tlen - p->span + 1;",
+     "int64_t npos = tlen - p->span;", 1),
     ("last_query_position_dropped", "for (int64_t q = q0; q + p->span <= qlen && q < q1; q++) {",
      "for (int64_t q = q0; q + p->span < qlen && q < q1; q++) {", 1),
     ("right_side_stops_one_short", "while (t + span + n < tlen && q + span + n < qlen) {",
@@ -79,6 +79,12 @@ MUTANTS = [
      "const int64_t q1 = q0 + qtile < nq ? q0 + qtile - 1 : nq;", 1, (PARALLEL,)),
     ("probe_runs_overlap", "b = a + qrun < q1 ? a + qrun : q1;",
      "b = a + qrun + 1 < q1 ? a + qrun + 1 : q1;", 1, (PARALLEL,)),
+    # the index stride: every position's key at a sampled slot, or no stride
+    # test when a diagonal is walked position by position
+    ("step_key_from_wrong_position", "tab[j].key = seed_key(T, j * p->step, p);",
+     "tab[j].key = seed_key(T, j, p);", 1),
+    ("step_ignored_on_one_diagonal", "if (t % step != 0 || !or_is_hit(",
+     "if (!or_is_hit(", 1, (SERIAL,)),
 ]
 
 
@@ -105,6 +111,8 @@ def battery(form: str = SERIAL) -> dict:
         "strand": _safe(pins.check_strand_symmetry, 6),
         "swap": _safe(pins.check_swap_symmetry, 8, pins._rand_asym_scores(8)),
         "diagonal": _safe(pins.test_run_diagonal_agrees_with_run),
+        "hits_step": _safe(pins.check_hits_bruteforce, 13, 1500, 1300, pins.P19, True, 0.5, 3),
+        "diagonal_step": _safe(pins.test_run_diagonal_with_step_agrees_with_run),
     }
 
 

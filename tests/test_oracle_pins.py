@@ -63,11 +63,11 @@ def _rand_asym_scores(seed):
     return M
 
 
-def check_hits_bruteforce(seed=11, n=2500, m=1800, pattern=P19, transition=True, gc=0.5):
+def check_hits_bruteforce(seed=11, n=2500, m=1800, pattern=P19, transition=True, gc=0.5, step=1):
     T, Q = _rand_pair(seed, n, m, gc)
     for Qs in (Q, bf.revcomp(Q)):
-        t1, q1 = oracle.seed_hits(T, Qs, pattern, transition)
-        t2, q2 = bf.hits_by_diagonal(T, Qs, pattern, transition)
+        t1, q1 = oracle.seed_hits(T, Qs, pattern, transition, step)
+        t2, q2 = bf.hits_by_diagonal(T, Qs, pattern, transition, step)
         if not (np.array_equal(t1, t2) and np.array_equal(q1, q2)):
             return False
     return True
@@ -148,12 +148,12 @@ def test_xdrop_matches_exhaustive_asymmetric(seed):
 
 
 def check_serial_loop(seed=4, n=2200, m=2000, flags=0, scores=None, X=910, thresh=1500,
-                      pattern=P19, transition=True):
+                      pattern=P19, transition=True, step=1):
     T, Q = _rand_pair(seed, n, m)
     M = oracle.HOXD70 if scores is None else scores
-    r = oracle.run(T, Q, pattern, transition, 3, M, X, thresh, flags)
+    r = oracle.run(T, Q, pattern, transition, 3, M, X, thresh, flags, step=step)
     ref, st = bf.serial_query_order(T, Q, pattern, transition, 3, M, X, thresh,
-                                    bool(flags & oracle.SKIP_PASSING_ONLY))
+                                    bool(flags & oracle.SKIP_PASSING_ONLY), step)
     got = [tuple(map(int, x)) for x in r.hsps.tolist()]
     return (got == ref and r.hits == st["hits"] and r.extended == st["extended"]
             and r.cells == st["cells"])
@@ -302,3 +302,63 @@ def test_parallel_form_dense_diagonals_across_tiles():
         got = oracle.run_par(T, Q, thresh=0, qtile=13, threads=4)
         assert np.array_equal(got.hsps, ref.hsps)
         assert (got.hits, got.extended, got.cells) == (ref.hits, ref.extended, ref.cells)
+
+
+# ------------------------------------------------------------------ heavier seeds and step
+# Section 7 raises the seed weight (14 of 22) and the spacing between indexed
+# target positions (the step). The oracle's reading: with step s only target
+# positions t with t % s == 0 are in the position table.
+
+P22 = "1110111000011101011011"  # the 14-of-22 mask of this build (weight 14, span 22)
+
+
+def test_heavier_mask_shape():
+    assert len(P22) == 22 and P22.count("1") == 14 and P22[0] == P22[-1] == "1"
+
+
+@pytest.mark.parametrize("pattern,transition,step", [
+    (P19, True, 2), (P19, True, 3), (P19, False, 5), (P22, True, 1), (P22, True, 4),
+    ("1101011", True, 7),
+])
+def test_hits_with_step_match_bruteforce(pattern, transition, step):
+    assert check_hits_bruteforce(13, 2500, 2200, pattern, transition, 0.5, step)
+
+
+@pytest.mark.parametrize("pattern,step", [(P19, 3), (P22, 1), (P22, 2)])
+def test_skip_with_step_matches_serial_query_order(pattern, step):
+    assert check_serial_loop(14, 2600, 2400, thresh=1200, pattern=pattern, step=step)
+
+
+def test_step_one_is_the_default_and_steps_only_thin_the_hits():
+    T, Q = _rand_pair(15, 4000, 3500)
+    base = oracle.run(T, Q, thresh=800)
+    assert np.array_equal(oracle.run(T, Q, thresh=800, step=1).hsps, base.hsps)
+    t1, q1 = oracle.seed_hits(T, Q)
+    for s in (2, 3, 8):
+        t, q = oracle.seed_hits(T, Q, step=s)
+        keep = t1 % s == 0
+        assert np.array_equal(t, t1[keep]) and np.array_equal(q, q1[keep])
+
+
+@pytest.mark.parametrize("step", [2, 5])
+def test_parallel_form_with_step(step):
+    T, Q = _rand_pair(16, 5000, 4500)
+    ref = oracle.run(T, Q, P22, thresh=600, step=step)
+    got = oracle.run_par(T, Q, P22, thresh=600, step=step, qtile=333, threads=3)
+    assert np.array_equal(got.hsps, ref.hsps)
+    assert (got.hits, got.extended, got.cells) == (ref.hits, ref.extended, ref.cells)
+
+
+def test_run_diagonal_with_step_agrees_with_run():
+    """The one-diagonal walk with a step: its HSPs equal the whole run's on that
+    diagonal, and its hit count equals the brute force's hits there."""
+    T, Q = _rand_pair(17, 2500, 2500)
+    full = oracle.run(T, Q, strands=1, thresh=0, keep_log=True, step=3)
+    bt, bq = bf.hits_by_diagonal(T, Q, P19, True, 3)
+    diags = np.unique(full.ext["t"] - full.ext["q"])
+    st = synth.Stream(2, "diag")
+    for d in diags[st.integers(0, diags.size, 20)]:
+        one = oracle.run_diagonal(T, Q, 0, int(d), thresh=0, step=3)
+        mine = full.hsps[full.hsps["tpos"] - full.hsps["qpos"] == d]
+        assert np.array_equal(one.hsps, mine)
+        assert one.hits == int(np.count_nonzero(bt - bq == d))
