@@ -556,6 +556,9 @@ def run_sfe(a, rank, world, local):
                        "d2h_bytes_per_step": int(nh * 20 + 8 * 24),
                        "path": "sfe_run with pinned host buffers (host wall clock)"}
 
+    if a.workload == WORKLOAD and not a.no_sublines:
+        torch.cuda.synchronize()
+        line["seeds"] = run_seed_sweep(a, ctx, T, Q, pair, out, step)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_line(pair, a.cpu_seconds)
     ctx.close()
@@ -680,6 +683,75 @@ def run_batch_bench(a, rank, world, local, emit: bool = True):
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+P22 = "1110111000011101011011"  # this build's 14-of-22 mask (Section 7 names the weight)
+SEED_SWEEP = [("1110100110010101111", 1), ("1110100110010101111", 2), (P22, 1), (P22, 2),
+              (P22, 4)]
+
+
+def block_recovery(pair, H) -> dict:
+    """Planted homologous blocks found by an HSP: on the block's strand, overlapping
+    its target range, on a diagonal within 50 + 3% of its length of the block's
+    (indels drift the diagonal). Returns the fraction of blocks with such an HSP
+    and the fraction of the blocks' target bases such HSPs cover."""
+    if not pair.blocks or H.shape[0] == 0:
+        return {"blocks": len(pair.blocks), "blocks_found": 0.0, "block_bases_covered": 0.0}
+    s, t0, q0, ln = (H[:, k].astype(np.int64) for k in range(4))
+    found, covered, total = 0, 0, 0
+    maxlen = int(ln.max())
+    for b in pair.blocks:
+        strand = 1 if b.rc else 0
+        qb = (pair.qlen - b.qstart - b.qlen) if b.rc else b.qstart
+        d0, tol = b.tstart - qb, 50 + 0.03 * b.tlen
+        lo = np.searchsorted(s * (1 << 40) + t0, strand * (1 << 40) + b.tstart - maxlen)
+        hi = np.searchsorted(s * (1 << 40) + t0, strand * (1 << 40) + b.tstart + b.tlen)
+        sel = np.arange(lo, hi)
+        sel = sel[(t0[sel] + ln[sel] > b.tstart) & (np.abs(t0[sel] - q0[sel] - d0) <= tol)]
+        total += b.tlen
+        if sel.size == 0:
+            continue
+        found += 1
+        a = np.maximum(t0[sel], b.tstart)
+        e = np.minimum(t0[sel] + ln[sel], b.tstart + b.tlen)
+        order = np.argsort(a)
+        a, e = a[order], e[order]
+        run_end, cov = -1, 0
+        for x, y in zip(a.tolist(), e.tolist()):
+            if y <= run_end:
+                continue
+            cov += y - max(x, run_end)
+            run_end = y
+        covered += cov
+    return {"blocks": len(pair.blocks), "blocks_found": found / len(pair.blocks),
+            "block_bases_covered": covered / max(1, total)}
+
+
+def run_seed_sweep(a, ctx, T, Q, pair, out, step_fn) -> list:
+    """Section 7: heavier seeds and a larger step against 12of19 with step 1, on
+    the same pair: hits, cells, HSPs, time per step and planted-block recovery."""
+    import paper_2606_06811_gb300 as pkg
+    rows = []
+    for pattern, step in SEED_SWEEP:
+        prm = pkg.default_params(flags=pkg.TIME_STAGES, seed_pattern=pattern, step=step)
+        for _ in range(a.sub_warmup):
+            step_fn(prm)
+        recs = [step_fn(prm) for _ in range(a.sub_steps)]
+        ms = sum(e0.elapsed_time(e1) for e0, e1, _, _ in recs) / len(recs)
+        st, n = recs[-1][2], recs[-1][3]
+        H = out[:n].cpu().numpy()
+        rows.append({"seed": pattern, "weight": pattern.count("1"), "span": len(pattern),
+                     "step": step, "ms_per_step": round(ms, 3),
+                     "gcups": st["cells"] / (ms / 1e3) / 1e9, "hits": st["hits"],
+                     "extended": st["extended"], "cells": st["cells"], "hsps": n,
+                     "stage_ms": {k: round(v, 3) for k, v in st["stage_ms"].items()},
+                     **block_recovery(pair, H)})
+    base = rows[0]
+    for r in rows:
+        r["speedup_vs_12of19_step1"] = round(base["ms_per_step"] / r["ms_per_step"], 3)
+        r["block_bases_vs_12of19_step1"] = round(
+            r["block_bases_covered"] / max(1e-12, base["block_bases_covered"]), 4)
+    return rows
 
 
 def run_large(a, local) -> dict:

@@ -133,6 +133,9 @@ typedef struct {
                                  launch on the same stream (the output is the same either way;
                                  see stats.deferred_tasks); 0 = default (2^20) */
     int32_t test_hooks;       /* SFE_TEST_* bits; 0 in normal use */
+    int32_t step;             /* index stride (Section 7's spacing between seeds): only target
+                                 positions t with t % step == 0 are indexed, so only they start
+                                 hits; 0 or 1 = every position */
 } sfe_params;
 
 /* sfe_params.test_hooks (no counterpart in the paper: they let tests drive the
@@ -143,6 +146,11 @@ typedef struct {
  * skips the slot (it holds no task); the output is the oracle's all the same
  * and stats.deferred_tasks counts the warps that gave up. */
 #define SFE_TEST_UNPUBLISHED_QUEUE_ENTRY 1
+/* SFE_TEST_DENSE_INDEX builds the position table over all 4^weight keys (with
+ * the per-key probe-set tables) even for a target that fills few of them,
+ * where the library otherwise indexes the keys' top bits (a sparse index);
+ * both give the same hits. */
+#define SFE_TEST_DENSE_INDEX 2
 
 /* sfe_params.walk_schedule: the order of work never changes the output, only
  * how evenly it spreads over the warps */

@@ -53,7 +53,8 @@ constexpr size_t kPlanesMaxBytes = 64ull << 20;
 enum Slot {
     SL_TIN, SL_QIN, SL_TP, SL_QP, SL_QM, SL_KEYS_A, SL_KEYS_B, SL_BCOUNT, SL_OFFS, SL_POS,
     SL_COUNTS, SL_STARTS, SL_HITS_A, SL_HITS_B, SL_QUEUE, SL_PAIRS, SL_BENTRIES, SL_SCHED,
-    SL_HSPS, SL_TMP, SL_ECARRY, SL_PUB, SL_BOUNDS, SL_BSLOTS, SL_OFF2, SL_POS2, SL_PLANES, NSLOT
+    SL_HSPS, SL_TMP, SL_ECARRY, SL_PUB, SL_BOUNDS, SL_BSLOTS, SL_OFF2, SL_POS2, SL_PLANES, SL_LOW,
+    NSLOT
 };
 
 // Small device block: scores, counters and flags of one call.
@@ -118,6 +119,8 @@ struct sfe_index {
     uint32_t *ncount = nullptr;    // 4^weight: hits of each key's probe set
     uint32_t *off2 = nullptr;      // merged probe-set lists (optional): 4^weight + 1
     uint32_t *pos2 = nullptr;      //   and (1 + weight) x positions
+    int shift = 0;                 // sparse index: CSR over key >> shift ...
+    uint16_t *low = nullptr;       //   and each entry's key & (2^shift - 1)
 };
 
 namespace {
@@ -204,6 +207,7 @@ int parse_pattern(const char *s, SeedPattern *p) {
     if (n < 1 || n > MAX_SPAN) return fail(SFE_EINVAL, "seed pattern span must be 1..32");
     memset(p, 0, sizeof(*p));
     p->span = n;
+    p->step = 1;
     for (int i = 0; i < n; i++) {
         if (s[i] == '1')
             p->care[p->weight++] = i;
@@ -235,6 +239,7 @@ int check_params(const sfe_params *p) {
         return fail(SFE_EINVAL, "ext_log must be device memory");
     if (p->tile_hits < 0) return fail(SFE_EINVAL, "tile_hits must be >= 0");
     if (p->input_codes != 0 && p->input_codes != 1) return fail(SFE_EINVAL, "input_codes must be 0 or 1");
+    if (p->step < 0) return fail(SFE_EINVAL, "step must be >= 0");
     for (int i = 0; i < 16; i++)
         if (p->scores[i] < -(1 << 20) || p->scores[i] > (1 << 20))
             return fail(SFE_EINVAL, "scores must lie in [-2^20, 2^20]");
@@ -319,18 +324,47 @@ struct IndexView {
     const uint32_t *pos;
     const uint32_t *ncount;
     const uint32_t *off2, *pos2;  // merged probe-set lists, or null
+    int shift;                    // sparse index (low != null): buckets are key >> shift
+    const uint16_t *low;
 };
+
+HitParams hit_params(const IndexView &v, long long qlen) {
+    HitParams hp;
+    hp.pat = v.pat;
+    hp.transition = v.transition;
+    hp.qlen = qlen;
+    hp.qoff = qlen - v.pat.span;
+    hp.shift = v.shift;
+    hp.low = v.low;
+    return hp;
+}
 
 // Entries of the merged probe-set lists: every position is read by the probe
 // sets of 1 + weight keys (the relation "is a probe of" is symmetric). They
 // are kept while they fit u32 offsets and a memory budget.
 long long merged_entries(const SeedPattern &pat, int transition, long long tlen) {
-    const long long npos = std::max(0LL, tlen - pat.span + 1);
-    return (transition ? pat.weight + 1 : 1) * npos;
+    return (transition ? pat.weight + 1 : 1) * indexed_positions(pat, tlen);
 }
-bool use_merged(const SeedPattern &pat, int transition, long long tlen) {
+// The per-key tables (probe-set sizes, merged lists) are built over all
+// 4^weight keys; they pay only while the target fills them: with at most one
+// indexed position per four keys (a weight-14 seed on a 10 Mb target) the
+// count and write passes probe the CSR offsets of the 1 + weight keys instead.
+bool dense_tables(const SeedPattern &pat, long long tlen) {
+    return (1LL << (2 * pat.weight)) <= 4 * indexed_positions(pat, tlen);
+}
+// Sparse index: buckets are the top 2 * weight - shift key bits, about one
+// indexed position per bucket (and at least 2^(2 * weight - 16) buckets, so
+// the remaining bits fit the 16-bit low column). 0 for a dense index.
+int index_shift(const SeedPattern &pat, long long tlen, bool force_dense = false) {
+    if (force_dense || dense_tables(pat, tlen)) return 0;
+    int cb = 1;
+    while (cb < 2 * pat.weight && (1LL << cb) < indexed_positions(pat, tlen)) cb++;
+    cb = std::max(cb, 2 * pat.weight - 16);
+    return 2 * pat.weight - cb;
+}
+bool use_merged(const SeedPattern &pat, int transition, long long tlen, int shift) {
     const long long m = merged_entries(pat, transition, tlen);
-    return m < (1LL << 32) - 1 && m * 4 <= (16LL << 30);
+    return shift == 0 && m < (1LL << 32) - 1 && m * 4 <= (16LL << 30);
 }
 
 // Spaced keys -> stable radix sort -> CSR (offsets, positions).
@@ -338,10 +372,10 @@ bool use_merged(const SeedPattern &pat, int transition, long long tlen) {
 // done) receives the hits of every key's probe set under `transition`.
 // off2 / pos2 (optional) receive the merged probe-set lists.
 int build_index(sfe_ctx *c, const uint32_t *T, long long tlen, const SeedPattern &pat,
-                int transition, uint32_t *offs, uint32_t *pos, uint32_t **ncount_io,
-                uint32_t *off2 = nullptr, uint32_t *pos2 = nullptr) {
-    const long long npos = std::max(0LL, tlen - pat.span + 1);
-    const long long nbuckets = 1LL << (2 * pat.weight);
+                int transition, int shift, uint32_t *offs, uint32_t *pos, uint32_t **ncount_io,
+                uint32_t *off2 = nullptr, uint32_t *pos2 = nullptr, uint16_t *low = nullptr) {
+    const long long npos = indexed_positions(pat, tlen);
+    const long long nbuckets = 1LL << (2 * pat.weight - shift);
     uint32_t *counts = nullptr;
     TRY(ensure_t(c, SL_BCOUNT, (size_t)nbuckets, &counts));
     CK(cudaMemsetAsync(counts, 0, (size_t)nbuckets * 4, c->st));
@@ -354,9 +388,14 @@ int build_index(sfe_ctx *c, const uint32_t *T, long long tlen, const SeedPattern
         CK(launch_seed_keys(T, tlen, pat, ka, c->st));
         bool in_b = false;
         CK(radix_sort(ka, kb, nullptr, nullptr, npos, 32, 32 + 2 * pat.weight, tmp, &in_b, &c->small->status, c->st));
-        CK(launch_csr_counts(in_b ? kb : ka, npos, counts, pos, c->st));
+        CK(launch_csr_counts(in_b ? kb : ka, npos, counts, pos, shift, shift ? low : nullptr,
+                             c->st));
     }
     CK(scan_u32_to_u32(counts, offs, nbuckets, tmp, c->st));
+    if (shift) {  // sparse: the hit passes probe the buckets
+        *ncount_io = nullptr;
+        return SFE_OK;
+    }
     if (!*ncount_io) *ncount_io = counts;  // the per-key counts are no longer needed
     CK(launch_neighbor_counts(offs, pat, transition, *ncount_io, c->st));
     if (off2 && pos2) {
@@ -376,11 +415,7 @@ int count_hits(sfe_ctx *c, const IndexView &ix, const uint32_t *Qs, long long ql
         *nq_out = 0;
         return SFE_OK;
     }
-    HitParams hp;
-    hp.pat = ix.pat;
-    hp.transition = ix.transition;
-    hp.qlen = qlen;
-    hp.qoff = qlen - ix.pat.span;
+    const HitParams hp = hit_params(ix, qlen);
     uint32_t *counts = nullptr;
     unsigned long long *starts = nullptr;
     void *tmp = nullptr;
@@ -709,6 +744,8 @@ int sfe_index_build(sfe_ctx *c, const uint8_t *target, int64_t tlen, const sfe_p
     TRY(check_len(tlen, "target"));
     SeedPattern pat;
     TRY(parse_pattern(params ? params->seed_pattern : nullptr, &pat));
+    if (params && params->step < 0) return fail(SFE_EINVAL, "step must be >= 0");
+    pat.step = params && params->step > 1 ? params->step : 1;
     const int codes = params ? params->input_codes : 0;
     TRY(begin(c));
     const void *tdev = nullptr;
@@ -719,13 +756,16 @@ int sfe_index_build(sfe_ctx *c, const uint8_t *target, int64_t tlen, const sfe_p
     ix->pat = pat;
     ix->transition = params ? params->transition : 1;
     ix->codes = codes;
-    const long long npos = std::max(0LL, (long long)tlen - pat.span + 1);
-    const long long nbuckets = 1LL << (2 * pat.weight);
+    const long long npos = indexed_positions(pat, tlen);
+    ix->shift = index_shift(pat, tlen, params && (params->test_hooks & SFE_TEST_DENSE_INDEX));
+    const long long nbuckets = 1LL << (2 * pat.weight - ix->shift);
     cudaError_t e = cudaMalloc(&ix->tp_alloc, packed_words(tlen) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&ix->offs, (size_t)(nbuckets + 1) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&ix->pos, (size_t)std::max(1LL, npos) * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&ix->ncount, (size_t)nbuckets * 4);
-    if (e == cudaSuccess && use_merged(pat, ix->transition, tlen)) {
+    if (e == cudaSuccess && ix->shift)
+        e = cudaMalloc(&ix->low, (size_t)std::max(1LL, npos) * 2);
+    if (e == cudaSuccess && !ix->shift) e = cudaMalloc(&ix->ncount, (size_t)nbuckets * 4);
+    if (e == cudaSuccess && use_merged(pat, ix->transition, tlen, ix->shift)) {
         e = cudaMalloc(&ix->off2, (size_t)(nbuckets + 1) * 4);
         if (e == cudaSuccess)
             e = cudaMalloc(&ix->pos2,
@@ -739,8 +779,8 @@ int sfe_index_build(sfe_ctx *c, const uint8_t *target, int64_t tlen, const sfe_p
     uint32_t *T = nullptr;
     int r = pack_into(c, reinterpret_cast<const uint8_t *>(tdev), tlen, codes, ix->tp_alloc, &T);
     if (r == SFE_OK)
-        r = build_index(c, T, tlen, pat, ix->transition, ix->offs, ix->pos, &ix->ncount,
-                        ix->off2, ix->pos2);
+        r = build_index(c, T, tlen, pat, ix->transition, ix->shift, ix->offs, ix->pos,
+                        &ix->ncount, ix->off2, ix->pos2, ix->low);
     if (r == SFE_OK) r = sync_small(c);
     if (r == SFE_OK) r = check_status(c->host_small->status);
     if (r != SFE_OK) {
@@ -760,6 +800,7 @@ void sfe_index_free(sfe_index *ix) {
     if (ix->ncount) cudaFree(ix->ncount);
     if (ix->off2) cudaFree(ix->off2);
     if (ix->pos2) cudaFree(ix->pos2);
+    if (ix->low) cudaFree(ix->low);
     delete ix;
 }
 
@@ -774,6 +815,8 @@ static IndexView view_of(const sfe_index *ix) {
     v.ncount = ix->ncount;
     v.off2 = ix->off2;
     v.pos2 = ix->pos2;
+    v.shift = ix->shift;
+    v.low = ix->low;
     return v;
 }
 
@@ -817,11 +860,7 @@ int sfe_seed_hits(sfe_ctx *c, const sfe_index *ix, const uint8_t *query, int64_t
         TRY(ensure_t(c, SL_HITS_A, (size_t)t2, &ha));
         TRY(ensure_t(c, SL_HITS_B, (size_t)t2, &hb));
         TRY(ensure(c, SL_TMP, radix_sort_temp_bytes((long long)t2), &tmp));
-        HitParams hp;
-        hp.pat = v.pat;
-        hp.transition = v.transition;
-        hp.qlen = qlen;
-        hp.qoff = qlen - v.pat.span;
+        const HitParams hp = hit_params(v, qlen);
         CK(launch_hit_write(s ? Qm : Qp, hp, v.offs, v.pos, v.off2, v.pos2, 0, nq, starts, 0, t2, ha,
                             c->st));
         bool in_b = false;
@@ -916,6 +955,7 @@ int sfe_run(sfe_ctx *c, const uint8_t *target, int64_t tlen, const uint8_t *quer
     TRY(check_len(qlen, "query"));
     SeedPattern pat;
     TRY(parse_pattern(params->seed_pattern, &pat));
+    pat.step = params->step > 1 ? params->step : 1;
     TRY(begin(c, params->flags));
     TRY(upload_scores(c, params->scores));
     uint32_t *Tp = nullptr, *Qp = nullptr, *Qm = nullptr;
@@ -951,21 +991,25 @@ int sfe_run(sfe_ctx *c, const uint8_t *target, int64_t tlen, const uint8_t *quer
             }
         }
     }
-    const long long npos = std::max(0LL, (long long)tlen - pat.span + 1);
+    const long long npos = indexed_positions(pat, tlen);
+    const int shift = index_shift(pat, tlen, (params->test_hooks & SFE_TEST_DENSE_INDEX) != 0);
     uint32_t *offs = nullptr, *pos = nullptr;
-    TRY(ensure_t(c, SL_OFFS, (size_t)(1LL << (2 * pat.weight)) + 1, &offs));
+    uint16_t *low = nullptr;
+    TRY(ensure_t(c, SL_OFFS, (size_t)(1LL << (2 * pat.weight - shift)) + 1, &offs));
     TRY(ensure_t(c, SL_POS, (size_t)std::max(1LL, npos), &pos));
+    if (shift) TRY(ensure_t(c, SL_LOW, (size_t)std::max(1LL, npos), &low));
     uint32_t *ncount = nullptr, *off2 = nullptr, *pos2 = nullptr;
-    if (use_merged(pat, params->transition, tlen)) {
+    if (use_merged(pat, params->transition, tlen, shift)) {
         TRY(ensure_t(c, SL_OFF2, (size_t)(1LL << (2 * pat.weight)) + 1, &off2));
         TRY(ensure_t(c, SL_POS2,
                      (size_t)std::max(1LL, merged_entries(pat, params->transition, tlen)), &pos2));
     }
     {
         Span sp(c, SFE_STAGE_INDEX);
-        TRY(build_index(c, Tp, tlen, pat, params->transition, offs, pos, &ncount, off2, pos2));
+        TRY(build_index(c, Tp, tlen, pat, params->transition, shift, offs, pos, &ncount, off2,
+                        pos2, low));
     }
-    IndexView v{Tp, tlen, pat, params->transition, offs, pos, ncount, off2, pos2};
+    IndexView v{Tp, tlen, pat, params->transition, offs, pos, ncount, off2, pos2, shift, low};
 
     const long long tile_hits = params->tile_hits > 0 ? params->tile_hits : kDefaultTileHits;
     const int DB = bits_for(tlen + qlen);
@@ -1023,11 +1067,7 @@ int sfe_run(sfe_ctx *c, const uint8_t *target, int64_t tlen, const uint8_t *quer
             TRY(ensure_t(c, SL_HITS_A, (size_t)maxtile, &ha));
             TRY(ensure_t(c, SL_HITS_B, (size_t)maxtile, &hbuf));
             TRY(ensure(c, SL_TMP, radix_sort_temp_bytes((long long)maxtile), &tmp));
-            HitParams hp;
-            hp.pat = pat;
-            hp.transition = params->transition;
-            hp.qlen = qlen;
-            hp.qoff = qlen - pat.span;
+            const HitParams hp = hit_params(v, qlen);
             for (long long k = 0; k < ntiles; k++) {
                 const long long nh = (long long)(hb[k + 1] - hb[k]);
                 if (nh == 0) continue;
@@ -1107,6 +1147,7 @@ int batch_geometry(const int64_t *toff, const int64_t *qoff, int npairs, const s
     if (npairs < 1 || npairs > (1 << 16)) return fail(SFE_EINVAL, "npairs must be 1..65536");
     TRY(check_params(params));
     TRY(parse_pattern(params->seed_pattern, &g.pat));
+    g.pat.step = params->step > 1 ? params->step : 1;
     if (toff[0] != 0 || qoff[0] != 0) return fail(SFE_EINVAL, "offsets must start at 0");
     long long maxsum = 1;
     g.maxlen = 1;
@@ -1136,7 +1177,7 @@ int batch_geometry(const int64_t *toff, const int64_t *qoff, int npairs, const s
         x.qoff_rc = g.qtot - qoff[p + 1];
         x.tlen = (int)(toff[p + 1] - toff[p]);
         x.qlen = (int)(qoff[p + 1] - qoff[p]);
-        const long long npos = std::max(1LL, (long long)x.tlen - g.pat.span + 1);
+        const long long npos = std::max(1LL, indexed_positions(g.pat, x.tlen));
         x.bbits = std::min(kbits, std::max(4, bits_for(npos - 1) - kBatchBucketShift));
         x.boff = g.nbuckets;
         x.pad = 0;

@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(BLOCK) bidx_count(const uint32_t *__restrict__
     const long long i0 = (blockIdx.x - tprefix[p]) * (long long)ITEM;
     const Split q = split_of(pat.weight);
     for (long long i = i0 + threadIdx.x; i < min(npos, i0 + ITEM); i += BLOCK) {
+        if (i % pat.step) continue;  // the index stride: only every step-th position
         const uint32_t k = spaced_key(T, P.toff + i, pat);
         uint2 sl;
         sl.x = atomicAdd(cnt + P.boff + (table1_key(k, q) >> (q.ik - P.bbits)), 1u);
@@ -132,6 +133,7 @@ __global__ void __launch_bounds__(BLOCK) bidx_fill(const uint32_t *__restrict__ 
     const long long i0 = (blockIdx.x - tprefix[p]) * (long long)ITEM;
     const Split q = split_of(pat.weight);
     for (long long i = i0 + threadIdx.x; i < min(npos, i0 + ITEM); i += BLOCK) {
+        if (i % pat.step) continue;
         const uint32_t k = spaced_key(T, P.toff + i, pat);
         const uint64_t ent = ((uint64_t)k << 32) | (uint32_t)i;
         const uint2 sl = slots[P.toff + i];

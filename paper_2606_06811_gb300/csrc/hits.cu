@@ -83,6 +83,67 @@ __global__ void __launch_bounds__(BLOCK) hit_count_kernel(const uint32_t *__rest
     counts[q - q0] = c;
 }
 
+// Sparse index (a heavy seed on a target that fills few of its 4^weight
+// keys): the CSR is over each key's top bits, about one entry per bucket, so
+// its offsets stay in L2; entry j keeps the rest of its key in low[j]. A
+// probe reads its bucket's bounds and counts (or writes) the entries whose
+// low bits are its own. Entries of one key are contiguous and in position
+// order (the index is sorted by key, then position).
+__global__ void __launch_bounds__(BLOCK) hit_count_sparse_kernel(
+    const uint32_t *__restrict__ Qs, HitParams hp, const uint32_t *__restrict__ off,
+    long long q0, long long q1, uint32_t *__restrict__ counts) {
+    long long q = q0 + blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= q1) return;
+    const uint32_t k = spaced_key(Qs, q, hp.pat);
+    const int nprobe = hp.transition ? hp.pat.weight + 1 : 1;
+    const uint32_t lmask = (1u << hp.shift) - 1u;
+    uint32_t a[MAX_PROBES], b[MAX_PROBES];
+#pragma unroll
+    for (int i = 0; i < MAX_PROBES; i++) {
+        const uint32_t pk = i == 0 ? k : k ^ (2u << (2 * (i - 1)));
+        a[i] = i < nprobe ? __ldg(off + (pk >> hp.shift)) : 0u;
+        b[i] = i < nprobe ? __ldg(off + (pk >> hp.shift) + 1) : 0u;
+    }
+    uint32_t c = 0;
+#pragma unroll
+    for (int i = 0; i < MAX_PROBES; i++) {
+        const uint32_t lo = (i == 0 ? k : k ^ (2u << (2 * (i - 1)))) & lmask;
+        for (uint32_t j = a[i]; j < b[i]; j++) c += __ldg(hp.low + j) == lo;
+    }
+    counts[q - q0] = c;
+}
+
+__global__ void __launch_bounds__(BLOCK) hit_write_sparse_kernel(
+    const uint32_t *__restrict__ Qs, HitParams hp, const uint32_t *__restrict__ off,
+    const uint32_t *__restrict__ pos, long long q0, long long q1,
+    const unsigned long long *__restrict__ starts, unsigned long long base,
+    uint64_t *__restrict__ hits) {
+    long long q = q0 + blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= q1) return;
+    const uint32_t k = spaced_key(Qs, q, hp.pat);
+    const int nprobe = hp.transition ? hp.pat.weight + 1 : 1;
+    const uint32_t lmask = (1u << hp.shift) - 1u;
+    uint32_t a[MAX_PROBES], b[MAX_PROBES];
+#pragma unroll
+    for (int i = 0; i < MAX_PROBES; i++) {
+        const uint32_t pk = i == 0 ? k : k ^ (2u << (2 * (i - 1)));
+        a[i] = i < nprobe ? __ldg(off + (pk >> hp.shift)) : 0u;
+        b[i] = i < nprobe ? __ldg(off + (pk >> hp.shift) + 1) : 0u;
+    }
+    unsigned long long o = starts[q - q0] - base;
+    const long long dq = hp.qoff - q;  // D = t + dq
+#pragma unroll
+    for (int i = 0; i < MAX_PROBES; i++) {
+        const uint32_t lo = (i == 0 ? k : k ^ (2u << (2 * (i - 1)))) & lmask;
+        for (uint32_t j = a[i]; j < b[i]; j++) {
+            if (__ldg(hp.low + j) != lo) continue;
+            const uint32_t t = __ldg(pos + j);
+            __stcs(reinterpret_cast<unsigned long long *>(hits) + o++,
+                   (unsigned long long)make_hit((uint32_t)(t + dq), t));
+        }
+    }
+}
+
 // Hits go out with evict-first stores: the stream of hit records must not push
 // the CSR table out of L2. Each thread writes the hits of its query position.
 __global__ void __launch_bounds__(BLOCK) hit_write_kernel(
@@ -248,7 +309,10 @@ cudaError_t launch_hit_count(const uint32_t *Qs, HitParams hp, const uint32_t *o
                              cudaStream_t st) {
     if (q1 <= q0) return cudaSuccess;
     g_launches++;
-    if (ncount)
+    if (hp.low)
+        hit_count_sparse_kernel<<<grid_for(q1 - q0), BLOCK, 0, st>>>(Qs, hp, offsets, q0, q1,
+                                                                     counts);
+    else if (ncount)
         hit_count_table_kernel<<<grid_for(q1 - q0), BLOCK, 0, st>>>(Qs, hp, ncount, q0, q1,
                                                                     counts);
     else
@@ -272,6 +336,11 @@ cudaError_t launch_hit_write(const uint32_t *Qs, HitParams hp, const uint32_t *o
                              unsigned long long nhits, uint64_t *hits, cudaStream_t st) {
     if (q1 <= q0) return cudaSuccess;
     g_launches++;
+    if (hp.low) {
+        hit_write_sparse_kernel<<<grid_for(q1 - q0), BLOCK, 0, st>>>(Qs, hp, offsets, positions,
+                                                                     q0, q1, starts, base, hits);
+        return cudaGetLastError();
+    }
     if (off2) {
         // with one range per position the per-warp writer wins even at a few
         // hits per position (10 Mb pair: 0.95 against 2.05 ms per step)

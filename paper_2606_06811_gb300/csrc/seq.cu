@@ -100,25 +100,29 @@ __global__ void plane_kernel(const uint32_t *__restrict__ S, long long n, int sh
     dst[j] = f;
 }
 
-__global__ void seed_keys_kernel(const uint32_t *__restrict__ S, long long npos, SeedPattern pat,
+__global__ void seed_keys_kernel(const uint32_t *__restrict__ S, long long nidx, SeedPattern pat,
                                  uint64_t *__restrict__ keys) {
-    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (p >= npos) return;
+    long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (j >= nidx) return;
+    const long long p = j * pat.step;
     uint64_t v = (uint64_t)win16(S, p) | ((uint64_t)win16(S, p + 16) << 32);
     uint32_t k = 0;
     for (int i = 0; i < pat.weight; i++) k = (k << 2) | (uint32_t)((v >> (2 * pat.care[i])) & 3u);
-    keys[p] = ((uint64_t)k << 32) | (uint32_t)p;
+    keys[j] = ((uint64_t)k << 32) | (uint32_t)p;
 }
 
 // Bucket sizes of the CSR table (counts must be zeroed) and the positions
 // column: counts[key(i)] += 1, positions[i] = low word of sorted[i].
 __global__ void csr_count_kernel(const uint64_t *__restrict__ sorted, long long m,
-                                 uint32_t *__restrict__ counts, uint32_t *__restrict__ positions) {
+                                 uint32_t *__restrict__ counts, uint32_t *__restrict__ positions,
+                                 int shift, uint16_t *__restrict__ low) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= m) return;
     uint64_t v = sorted[i];
     positions[i] = (uint32_t)v;
-    atomicAdd(counts + (v >> 32), 1u);
+    const uint32_t key = (uint32_t)(v >> 32);
+    if (low) low[i] = (uint16_t)(key & ((1u << shift) - 1u));
+    atomicAdd(counts + (key >> shift), 1u);
 }
 
 __global__ void hits_to_public_kernel(const uint64_t *__restrict__ hits, long long n, int strand,
@@ -188,18 +192,18 @@ cudaError_t launch_plane(const uint32_t *S, long long n, int shift, uint32_t *ds
 
 cudaError_t launch_seed_keys(const uint32_t *S, long long n, SeedPattern pat, uint64_t *keys,
                              cudaStream_t st) {
-    long long npos = n - pat.span + 1;
-    if (npos <= 0) return cudaSuccess;
+    const long long nidx = indexed_positions(pat, n);
+    if (nidx <= 0) return cudaSuccess;
     g_launches++;
-    seed_keys_kernel<<<grid_for(npos), BLOCK, 0, st>>>(S, npos, pat, keys);
+    seed_keys_kernel<<<grid_for(nidx), BLOCK, 0, st>>>(S, nidx, pat, keys);
     return cudaGetLastError();
 }
 
 cudaError_t launch_csr_counts(const uint64_t *sorted, long long m, uint32_t *counts,
-                             uint32_t *positions, cudaStream_t st) {
+                             uint32_t *positions, int shift, uint16_t *low, cudaStream_t st) {
     if (m <= 0) return cudaSuccess;
     g_launches++;
-    csr_count_kernel<<<grid_for(m), BLOCK, 0, st>>>(sorted, m, counts, positions);
+    csr_count_kernel<<<grid_for(m), BLOCK, 0, st>>>(sorted, m, counts, positions, shift, low);
     return cudaGetLastError();
 }
 

@@ -38,7 +38,15 @@ struct SeedPattern {
     int span;
     int weight;
     int care[MAX_SPAN];
+    int step;  // index stride: only target positions t with t % step == 0 are seeds
 };
+
+// Target positions a pattern indexes in a sequence of n bases: every step-th
+// of the n - span + 1 positions, from 0.
+__host__ __device__ inline long long indexed_positions(const SeedPattern &pat, long long n) {
+    const long long npos = n - pat.span + 1;
+    return npos > 0 ? (npos + pat.step - 1) / pat.step : 0;
+}
 
 // Counters written by the walkers (one struct in device memory).
 struct DevCounters {
@@ -135,13 +143,15 @@ cudaError_t launch_revcomp(const uint32_t *src, long long n, uint32_t *dst, cuda
 constexpr int PLANE_PAD = 4;
 size_t plane_words(long long n);
 cudaError_t launch_plane(const uint32_t *S, long long n, int shift, uint32_t *dst, cudaStream_t st);
-// keys[p] = (seed key of p) << 32 | p, for p in [0, n - span].
+// keys[j] = (seed key of p) << 32 | p for p = j * step, j < indexed_positions(pat, n).
 cudaError_t launch_seed_keys(const uint32_t *S, long long n, SeedPattern pat, uint64_t *keys,
                              cudaStream_t st);
 // CSR bucket sizes (counts zeroed by the caller) and the positions column from
-// keys sorted by their high word; offsets = exclusive scan of counts.
+// keys sorted by their high word; offsets = exclusive scan of counts. With
+// shift > 0 (a sparse index) the buckets are the keys' top bits (key >> shift)
+// and low[i] receives the remaining bits of entry i's key.
 cudaError_t launch_csr_counts(const uint64_t *sorted, long long m, uint32_t *counts,
-                              uint32_t *positions, cudaStream_t st);
+                              uint32_t *positions, int shift, uint16_t *low, cudaStream_t st);
 
 // Stable LSD radix sort of n (< 2^32) uint64 keys by bits [lo, hi), optional
 // uint32 values carried along. Uses (a, b) ping-pong and returns in
@@ -171,6 +181,10 @@ struct HitParams {
     int transition;
     long long qlen;
     long long qoff;  // qlen - span, so D = t - q + qoff >= 0
+    // sparse index (low != nullptr): CSR over key >> shift, low[j] = the
+    // entry's key & (2^shift - 1); a probe scans its bucket for its low bits
+    int shift;
+    const uint16_t *low;
 };
 // ncount[k]: hits of key k's probe set (launch_neighbor_counts), or null to
 // count by probing the offsets.

@@ -81,6 +81,7 @@ int parse(const char *s, SeedPattern *p) {
     if (n < 1 || n > MAX_SPAN) return SFE_EINVAL;
     memset(p, 0, sizeof(*p));
     p->span = n;
+    p->step = 1;
     for (int i = 0; i < n; i++) {
         if (s[i] == '1')
             p->care[p->weight++] = i;

@@ -23,6 +23,7 @@ NO_CELL_PLANES = 4
 WALK_TWO_LAUNCHES, WALK_PERSISTENT = 0, 1
 SCHED_NATURAL, SCHED_LARGEST_FIRST, SCHED_PREDICTED, SCHED_RANDOM = 0, 1, 2, 3
 TEST_UNPUBLISHED_QUEUE_ENTRY = 1
+TEST_DENSE_INDEX = 2
 EXT_DTYPE = np.dtype([("pair", "<i4"), ("strand", "<i4"), ("t", "<i4"), ("q", "<i4"),
                       ("right", "<i4"), ("left", "<i4")])
 STAGES = ("pack", "index", "count", "write", "sort", "schedule", "walk_lanes", "walk_warps",
@@ -48,7 +49,8 @@ class Params(C.Structure):
                 ("lane_cap", C.c_int32), ("lanes_per_sm", C.c_int32), ("tile_hits", C.c_int64),
                 ("walk_chunk", C.c_int32), ("walk_mode", C.c_int32), ("walk_schedule", C.c_int32),
                 ("ext_log_every", C.c_int32), ("ext_log", C.c_void_p), ("ext_log_cap", C.c_int64),
-                ("model", C.c_void_p), ("wait_limit", C.c_int32), ("test_hooks", C.c_int32)]
+                ("model", C.c_void_p), ("wait_limit", C.c_int32), ("test_hooks", C.c_int32),
+                ("step", C.c_int32)]
 
 
 class Stats(C.Structure):

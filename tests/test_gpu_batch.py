@@ -43,7 +43,8 @@ def gpu_batch(P, pairs, **kw):
 
 
 def check(P, pairs, **kw):
-    okw = {("thresh" if k == "hsp_thresh" else k): v for k, v in kw.items()
+    names = {"hsp_thresh": "thresh", "seed_pattern": "pattern"}
+    okw = {names.get(k, k): v for k, v in kw.items()
            if k not in ("lane_cap", "lanes_per_sm", "tile_hits", "walk_mode", "walk_chunk",
                         "walk_schedule")}
     H, hits, ext, cells = oracle_batch(pairs, **okw)
@@ -154,3 +155,12 @@ def test_autotuner_keeps_the_output_and_caches_its_choice(pkg, tmp_path):
         best2, _ = autotune.tune(never, sig, space=space, reps=1, cache=cache)
         assert best2 == best
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("pattern,step", [("1110111000011101011011", 1),
+                                          ("1110111000011101011011", 3),
+                                          ("1110100110010101111", 2)])
+def test_batch_heavier_seed_and_step(pkg, pattern, step):
+    pairs = synth.batch_pairs(seed=6, n_pairs=48, len_lo=2000, len_hi=30_000)
+    G = check(pkg, pairs, seed_pattern=pattern, step=step)
+    assert G.shape[0] > 0

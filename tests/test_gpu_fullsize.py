@@ -91,10 +91,10 @@ def pick_diagonals(pair, H, n_hsp, n_rand, seed):
     return picks
 
 
-def check_full_list(pair, H, st, qtile=0):
+def check_full_list(pair, H, st, qtile=0, **kw):
     """The whole sorted HSP list and the counters against the oracle."""
     t0 = time.perf_counter()
-    ref = oracle.run_par(pair.T, pair.Q, qtile=qtile)
+    ref = oracle.run_par(pair.T, pair.Q, qtile=qtile, **kw)
     secs = time.perf_counter() - t0
     print(f"oracle: {oracle.host_cores()} host cores, {secs:.1f} s, {ref.hits} hits, "
           f"{ref.cells} cells, {ref.hsps.size} HSPs")
@@ -111,6 +111,17 @@ def test_plain_pair_10mb_full_list(pkg):
     check_scores(pair, H)
     check_diagonals(pair, H, pick_diagonals(pair, H, 8, 6, 1))
     check_full_list(pair, H, st)
+
+
+@pytest.mark.parametrize("step", [1, 2])
+def test_plain_pair_10mb_heavier_seed_full_list(pkg, step):
+    """Section 7's heavier seed (14 of 22, this build's mask) with and without
+    an index stride, on the benchmark's 10 Mb pair: the whole list."""
+    p22 = "1110111000011101011011"
+    pair = synth.plain_pair_10mb(2)
+    H, st = run_gpu(pkg, pair, seed_pattern=p22, step=step)
+    assert H.shape[0] > 1e4
+    check_full_list(pair, H, st, pattern=p22, step=step)
 
 
 def oracle_pairs(pairs):

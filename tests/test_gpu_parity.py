@@ -47,7 +47,7 @@ def assert_same(got, st, ref):
 
 def run_both(pkg, ctx, T, Q, **kw):
     okw = {k: v for k, v in kw.items() if k in ("pattern", "transition", "strands", "scores",
-                                                 "X", "thresh", "flags")}
+                                                 "X", "thresh", "flags", "step")}
     ref = oracle.run(T, Q, **okw)
     pmap = {"pattern": "seed_pattern", "X": "xdrop", "thresh": "hsp_thresh"}
     pkw = {pmap.get(k, k): v for k, v in kw.items()}
@@ -272,3 +272,62 @@ def test_persistent_walk_on_identical_sequences(pkg, ctx):
                              walk_schedule=1, lane_cap=16)
     assert_same(got, stt, ref)
     assert stt["warp_tasks"] > 0
+
+
+# ------------------------------------------------------------------ heavier seeds and step
+P22 = "1110111000011101011011"  # the 14-of-22 mask (Section 7 names the weight, not the mask)
+
+
+@pytest.mark.parametrize("pattern,step,transition", [
+    (P22, 1, True), (P22, 2, True), (P22, 5, False), (oracle.DEFAULT_PATTERN, 3, True),
+    (oracle.DEFAULT_PATTERN, 2, False), ("1101011", 4, True),
+])
+def test_heavier_seed_and_step(pkg, ctx, pattern, step, transition):
+    """Section 7's heavier seed and the index stride (only target positions
+    divisible by the step are seeds), against the oracle, on the plain
+    generator at 200 kb and on ragged lengths."""
+    p = synth.plain_pair_10mb(9, scale=0.02 if pattern.count("1") > 8 else 0.003)
+    got, st, ref = run_both(pkg, ctx, p.T, p.Q, pattern=pattern, step=step, transition=transition)
+    assert_same(got, st, ref)
+    T, Q = _pair(71, 4099, 3001, blocks=4)
+    got, st, ref = run_both(pkg, ctx, T, Q, pattern=pattern, step=step, transition=transition,
+                            lane_cap=16)
+    assert_same(got, st, ref)
+
+
+def test_seed_hits_api_with_step(pkg, ctx):
+    p = synth.tiny_pair(6, length=80_000, n_blocks=12)
+    ix = ctx.index_build(p.T, pkg.default_params(input_codes=1, seed_pattern=P22, step=3))
+    try:
+        h = ctx.seed_hits(ix, p.Q)
+    finally:
+        ix.close()
+    for s, Qs in ((0, p.Q), (1, oracle.revcomp(p.Q))):
+        t, q = oracle.seed_hits(p.T, Qs, P22, True, 3)
+        mine = h[h["strand"] == s]
+        assert np.array_equal(mine["tpos"], t) and np.array_equal(mine["qpos"], q)
+
+
+@pytest.mark.parametrize("pattern,step", [(oracle.DEFAULT_PATTERN, 1), (oracle.DEFAULT_PATTERN, 3),
+                                          (P22, 1), (P22, 2), ("1101011", 1)])
+@pytest.mark.parametrize("dense", [False, True])
+def test_sparse_and_dense_index_agree(pkg, ctx, pattern, step, dense):
+    """The position table over the keys' top bits (the default where the
+    target fills few of the 4^weight keys) and the dense table over every key
+    (forced by a test hook) give the oracle's hits and HSPs, through sfe_run
+    and through sfe_index_build + sfe_seed_hits."""
+    hooks = pkg.sfe.TEST_DENSE_INDEX if dense else 0
+    # a weight-5 seed hits about every 4^5 / 13 positions per diagonal: a smaller pair
+    p = synth.tiny_pair(12, length=120_000 if pattern.count("1") > 8 else 15_000, n_blocks=15)
+    got, st, ref = run_both(pkg, ctx, p.T, p.Q, pattern=pattern, step=step, test_hooks=hooks)
+    assert_same(got, st, ref)
+    ix = ctx.index_build(p.T, pkg.default_params(input_codes=1, seed_pattern=pattern, step=step,
+                                                 test_hooks=hooks))
+    try:
+        h = ctx.seed_hits(ix, p.Q)
+    finally:
+        ix.close()
+    for s, Qs in ((0, p.Q), (1, oracle.revcomp(p.Q))):
+        t, q = oracle.seed_hits(p.T, Qs, pattern, True, step)
+        mine = h[h["strand"] == s]
+        assert np.array_equal(mine["tpos"], t) and np.array_equal(mine["qpos"], q)
