@@ -559,6 +559,7 @@ def run_sfe(a, rank, world, local):
     if a.workload == WORKLOAD and not a.no_sublines:
         torch.cuda.synchronize()
         line["seeds"] = run_seed_sweep(a, ctx, T, Q, pair, out, step)
+        line["speculative_window"] = run_spec_study(a, ctx, T, Q, pair)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_line(pair, a.cpu_seconds)
     ctx.close()
@@ -752,6 +753,109 @@ def run_seed_sweep(a, ctx, T, Q, pair, out, step_fn) -> list:
         r["block_bases_vs_12of19_step1"] = round(
             r["block_bases_covered"] / max(1e-12, base["block_bases_covered"]), 4)
     return rows
+
+
+SPEC_WINDOWS = [1, 2, 4, 8, 16, 32]
+
+
+def block_diagonal_hits(hits, pair):
+    """The hits (device int32 tensor (n, 3): strand, tpos, qpos) that lie on a
+    planted block's diagonal band (the block's diagonal on its strand within
+    50 + 3% of its length, as in block_recovery)."""
+    import torch
+    out = []
+    for strand in (0, 1):
+        iv = []
+        for b in pair.blocks:
+            if int(b.rc) != strand:
+                continue
+            qb = (pair.qlen - b.qstart - b.qlen) if b.rc else b.qstart
+            d0, tol = b.tstart - qb, int(50 + 0.03 * b.tlen)
+            iv.append((d0 - tol, d0 + tol))
+        if not iv:
+            continue
+        iv.sort()
+        merged = [list(iv[0])]
+        for lo, hi in iv[1:]:
+            if lo <= merged[-1][1]:
+                merged[-1][1] = max(merged[-1][1], hi)
+            else:
+                merged.append([lo, hi])
+        dev = hits.device
+        lo = torch.tensor([m[0] for m in merged], dtype=torch.int64, device=dev)
+        hi = torch.tensor([m[1] for m in merged], dtype=torch.int64, device=dev)
+        h = hits[hits[:, 0] == strand]
+        d = h[:, 1].long() - h[:, 2].long()
+        k = torch.searchsorted(lo, d, right=True) - 1
+        ok = (k >= 0) & (d <= hi[k.clamp(min=0)])
+        out.append(h[ok])
+    return torch.cat(out).contiguous() if out else hits[:0]
+
+
+def run_spec_study(a, ctx, T, Q, pair) -> dict:
+    """Algorithm 3's speculative window on the per-diagonal skip: walk time and
+    shadow fraction (speculative work on hits a commit then covered, over the
+    useful cells) against the window, on the whole pair and on the hits of the
+    planted blocks' diagonals alone; the default lane walk for reference."""
+    import torch
+    import paper_2606_06811_gb300 as pkg
+    res = {"windows": SPEC_WINDOWS, "whole_pair": [], "block_diagonals": []}
+
+    def timed(fn, reps):
+        for _ in range(a.sub_warmup):
+            fn()
+        rows = [fn() for _ in range(reps)]
+        return rows[-1][1], sum(r[0] for r in rows) / reps
+
+    for k in SPEC_WINDOWS:
+        prm = pkg.default_params(flags=pkg.TIME_STAGES, walk_mode=pkg.WALK_SPECULATIVE,
+                                 spec_window=k)
+
+        def one():
+            hs, st = ctx.run(T, Q, prm, cap=1 << 22)
+            return st["stage_ms"]["walk_warps"], st
+        st, ms = timed(one, a.sub_steps)
+        res["whole_pair"].append({"window": k, "walk_ms": round(ms, 3), "cells": st["cells"],
+                                  "shadow_cells": st["shadow_cells"],
+                                  "shadow_fraction": st["shadow_cells"] / max(1, st["cells"])})
+    ix = ctx.index_build(T, pkg.default_params())
+    try:
+        cap = 1 << 28
+        while True:  # device buffer for every hit of both strands
+            buf = torch.zeros((cap, 3), dtype=torch.int32, device=T.device)
+            try:
+                _, n = ctx.seed_hits(ix, Q, out=buf)
+                break
+            except pkg.SfeError:
+                del buf
+                cap *= 2
+        sub = block_diagonal_hits(buf[:n], pair)
+        del buf
+        res["block_diagonal_hits"] = int(sub.shape[0])
+        for k in [0] + SPEC_WINDOWS:
+            walk = (pkg.default_params(flags=pkg.TIME_STAGES) if k == 0 else
+                    pkg.default_params(flags=pkg.TIME_STAGES, walk_mode=pkg.WALK_SPECULATIVE,
+                                       spec_window=k))
+            ctx.set_walk(walk)
+
+            def one():
+                hs, st = ctx.ungapped_xdrop(ix, Q, sub, oracle_scores(), 910, 3000)
+                return st["stage_ms"]["walk_lanes"] + st["stage_ms"]["walk_warps"], st
+            st, ms = timed(one, a.sub_steps)
+            row = {"window": k if k else "lane walk (default)", "walk_ms": round(ms, 3),
+                   "cells": st["cells"], "shadow_cells": st["shadow_cells"],
+                   "shadow_fraction": st["shadow_cells"] / max(1, st["cells"])}
+            res["block_diagonals"].append(row)
+        ctx.set_walk(None)
+    finally:
+        ix.close()
+    return res
+
+
+def oracle_scores():
+    """HOXD70 as the library's default parameters hold it (4 x 4, target-major)."""
+    import paper_2606_06811_gb300 as pkg
+    return np.array(list(pkg.default_params().scores), dtype=np.int32).reshape(4, 4)
 
 
 def run_large(a, local) -> dict:

@@ -136,6 +136,8 @@ typedef struct {
     int32_t step;             /* index stride (Section 7's spacing between seeds): only target
                                  positions t with t % step == 0 are indexed, so only they start
                                  hits; 0 or 1 = every position */
+    int32_t spec_window;      /* SFE_WALK_SPECULATIVE: hits extended at once per diagonal, 1, 2,
+                                 4, 8, 16 or 32; 0 = 8 */
 } sfe_params;
 
 /* sfe_params.test_hooks (no counterpart in the paper: they let tests drive the
@@ -163,6 +165,13 @@ typedef struct {
 #define SFE_WALK_TWO_LAUNCHES 0 /* lanes own fixed hit ranges; a second launch drains the queue */
 #define SFE_WALK_PERSISTENT 1   /* one launch: lanes pull chunks from a device counter, then
                                    the same warps drain the hand-off queue */
+#define SFE_WALK_SPECULATIVE 2  /* Algorithm 3's speculative batch on the per-diagonal skip: a
+                                   warp per diagonal extends the next spec_window hits not yet
+                                   covered at once (32 / spec_window lanes each) and commits
+                                   them in t order; hits an earlier commit covers are skipped
+                                   and their work is counted in stats.shadow_cells. Same output
+                                   as the other modes; one pair or hit list at a time (not
+                                   sfe_run_batch) */
 
 /* Statistics of one call. cells is the work measure of the method: seed span
  * plus the bases scored on both sides, summed over hits that were extended. */
@@ -177,9 +186,10 @@ typedef struct {
     int64_t tiles;      /* query tiles processed */
     int64_t launches;   /* kernels this call launched */
     int64_t ext_logged; /* extensions selected for the log (may exceed ext_log_cap) */
-    int64_t shadow_cells; /* work done twice: the cells a lane scored on an extension before it
-                             handed the diagonal to the warp tier, which scores it again (not in
-                             cells) */
+    int64_t shadow_cells; /* work not in cells: the cells a lane scored on an extension before it
+                             handed the diagonal to the warp tier, which scores it again, or
+                             (SFE_WALK_SPECULATIVE) the work on hits extended speculatively and
+                             then found covered */
     double stage_ms[SFE_NSTAGES];        /* device time per stage (with SFE_TIME_STAGES) */
     int64_t stage_launches[SFE_NSTAGES]; /* kernels launched per stage (with SFE_TIME_STAGES) */
     int64_t deferred_tasks; /* persistent walk: warps that stopped waiting for a hand-off entry
@@ -199,6 +209,12 @@ int sfe_ctx_create(int device, sfe_ctx **out);
 /* Queue later work on `stream` (a cudaStream_t, e.g. a PyTorch stream); NULL
  * restores the context's own stream. The caller keeps the stream alive. */
 int sfe_ctx_set_stream(sfe_ctx *ctx, void *stream);
+/* Walk settings for later sfe_ungapped_xdrop calls on this context (that call
+ * takes the method's parameters explicitly and no sfe_params): walk_mode,
+ * lane_cap, walk_chunk, spec_window and the SFE_TIME_STAGES bit of flags are
+ * copied from *params; NULL restores the defaults of sfe_params_default. The
+ * output never depends on them. SFE_EINVAL on settings check_params rejects. */
+int sfe_ctx_set_walk(sfe_ctx *ctx, const sfe_params *params);
 /* Test hook (no counterpart in the paper): the next n device allocations of
  * the context's scratch arena fail as if the device were out of memory, so
  * the calls that need them return SFE_ENOMEM. n = 0 clears it. */

@@ -105,6 +105,8 @@ struct sfe_ctx {
     StageTimer tm;
     unsigned long long launches0 = 0;
     int fail_allocs = 0;  // test hook: allocations still to fail
+    sfe_params walk{};    // walk settings of sfe_ungapped_xdrop (sfe_ctx_set_walk)
+    bool walk_set = false;
 };
 
 struct sfe_index {
@@ -226,8 +228,12 @@ int check_params(const sfe_params *p) {
     if (p->lane_cap < 0) return fail(SFE_EINVAL, "lane_cap must be >= 0");
     if (p->lanes_per_sm < 0) return fail(SFE_EINVAL, "lanes_per_sm must be >= 0");
     if (p->walk_chunk < 0) return fail(SFE_EINVAL, "walk_chunk must be >= 0");
-    if (p->walk_mode != SFE_WALK_PERSISTENT && p->walk_mode != SFE_WALK_TWO_LAUNCHES)
-        return fail(SFE_EINVAL, "walk_mode must be SFE_WALK_PERSISTENT or SFE_WALK_TWO_LAUNCHES");
+    if (p->walk_mode != SFE_WALK_PERSISTENT && p->walk_mode != SFE_WALK_TWO_LAUNCHES &&
+        p->walk_mode != SFE_WALK_SPECULATIVE)
+        return fail(SFE_EINVAL, "walk_mode must be SFE_WALK_PERSISTENT, SFE_WALK_TWO_LAUNCHES or "
+                                "SFE_WALK_SPECULATIVE");
+    if (p->spec_window < 0 || p->spec_window > 32 || (p->spec_window & (p->spec_window - 1)))
+        return fail(SFE_EINVAL, "spec_window must be 0 or a power of two up to 32");
     if (p->walk_schedule < SFE_SCHED_NATURAL || p->walk_schedule > SFE_SCHED_RANDOM)
         return fail(SFE_EINVAL, "unknown walk_schedule");
     if (p->walk_schedule != SFE_SCHED_NATURAL && p->walk_mode != SFE_WALK_PERSISTENT)
@@ -500,6 +506,15 @@ int walk_tiers(sfe_ctx *c, const uint64_t *hits, long long n, WalkParams &wp, ui
     wp.queue_cap = qcap;
     wp.queue_len = &sm->queue_len;
     CK(cudaMemsetAsync(&sm->queue_len, 0, 4, c->st));
+    if (p->walk_mode == SFE_WALK_SPECULATIVE) {
+        if (wp.pairs) return fail(SFE_EINVAL, "SFE_WALK_SPECULATIVE walks one pair at a time");
+        Span sp(c, SFE_STAGE_WALK_WARPS);
+        wp.work_next = &sm->work_next;
+        wp.chunk = p->walk_chunk > 0 ? (uint32_t)p->walk_chunk : walk_auto_chunk(n);
+        CK(cudaMemsetAsync(&sm->work_next, 0, 4, c->st));
+        CK(launch_walk_speculative(hits, n, wp, p->spec_window > 0 ? p->spec_window : 8, c->st));
+        return SFE_OK;
+    }
     if (p->walk_mode == SFE_WALK_TWO_LAUNCHES) {
         {
             Span sp(c, SFE_STAGE_WALK_LANES);
@@ -709,6 +724,25 @@ int sfe_test_radix_sort(sfe_ctx *c, uint64_t *keys, int64_t n, int32_t lo, int32
     return SFE_OK;
 }
 
+int sfe_ctx_set_walk(sfe_ctx *c, const sfe_params *params) {
+    if (!c) return fail(SFE_EINVAL, "context is NULL");
+    if (!params) {
+        c->walk_set = false;
+        return SFE_OK;
+    }
+    sfe_params p;
+    sfe_params_default(&p);
+    p.walk_mode = params->walk_mode;
+    p.lane_cap = params->lane_cap;
+    p.walk_chunk = params->walk_chunk;
+    p.spec_window = params->spec_window;
+    p.flags = params->flags & SFE_TIME_STAGES;
+    TRY(check_params(&p));
+    c->walk = p;
+    c->walk_set = true;
+    return SFE_OK;
+}
+
 int sfe_ctx_fail_next_allocs(sfe_ctx *c, int32_t n) {
     if (!c || n < 0) return fail(SFE_EINVAL, "bad context or count");
     c->fail_allocs = n;
@@ -881,13 +915,21 @@ int sfe_ungapped_xdrop(sfe_ctx *c, const sfe_index *ix, const uint8_t *query, in
     if (!ix || !nhsps || !scores) return fail(SFE_EINVAL, "index, scores or nhsps is NULL");
     if (nhits < 0 || nhits >= (1LL << 32)) return fail(SFE_EINVAL, "nhits out of range");
     TRY(check_len(qlen, "query"));
+    if (!c) return fail(SFE_EINVAL, "context is NULL");
     sfe_params p;
     sfe_params_default(&p);
+    if (c->walk_set) {
+        p.walk_mode = c->walk.walk_mode;
+        p.lane_cap = c->walk.lane_cap;
+        p.walk_chunk = c->walk.walk_chunk;
+        p.spec_window = c->walk.spec_window;
+        p.flags = c->walk.flags;
+    }
     memcpy(p.scores, scores, 64);
     p.xdrop = X;
     p.hsp_thresh = hsp_thresh;
     TRY(check_params(&p));
-    TRY(begin(c));
+    TRY(begin(c, p.flags));
     const IndexView v = view_of(ix);
     const int span = v.pat.span;
     TRY(upload_scores(c, p.scores));

@@ -315,6 +315,11 @@ cudaError_t launch_perm(long long n, unsigned long long seed, int epoch, uint64_
 cudaError_t launch_chunk_predict(const uint64_t *hits, long long n, uint32_t chunk,
                                  uint32_t nchunks, const WalkParams &wp, const void *model,
                                  uint64_t *keys, cudaStream_t st);
+// The speculative window walk (one warp per diagonal, `window` hits of it
+// extended at once and committed in t order; window = 1, 2, 4, ..., 32):
+// wp.work_next zeroed by the caller; one pair or hit list (no wp.pairs).
+cudaError_t launch_walk_speculative(const uint64_t *hits, long long n, WalkParams wp, int window,
+                                    cudaStream_t st);
 // Both tiers in one persistent launch fed by the work counter and the queue
 // (wp.work_next, warps_done, queue_take, queue_len zeroed by the caller).
 cudaError_t launch_walk_persistent(const uint64_t *hits, long long n, WalkParams wp,

@@ -675,6 +675,178 @@ __device__ void warp_walk_diagonal(const uint64_t *__restrict__ hits, uint32_t n
     if (wp.Ecarry && lane == 0) wp.Ecarry[D] = E;
 }
 
+// ---------------------------------------------------- speculative window
+//
+// The speculative batch of Algorithm 3, applied to the per-diagonal skip: a
+// warp walks whole diagonals; on each, it takes the next K hits that the
+// current skip state E does not already cover, extends them at once (group
+// g of W = 32 / K lanes extends hit g in W-base chunks with group-wide
+// shuffle scans), then commits the K results one by one in t order: a hit
+// that an earlier committed extension now covers (t < E) is skipped and its
+// work was shadow work (stats.shadow_cells); every other result is exactly
+// the serial one, since an extension does not depend on E. K = 1 is the
+// serial walk with one warp per hit.
+
+template <int W>
+__device__ __forceinline__ int grp_incl_sum(int v, int gl) {
+#pragma unroll
+    for (int o = 1; o < W; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, v, o, W);
+        if (gl >= o) v += y;
+    }
+    return v;
+}
+
+template <int W>
+__device__ __forceinline__ int grp_incl_max(int v, int gl) {
+#pragma unroll
+    for (int o = 1; o < W; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, v, o, W);
+        if (gl >= o) v = max(v, y);
+    }
+    return v;
+}
+
+// One side of each group's hit (bases p0 + dir * k, k < avail) in chunks of W
+// bases; every lane of a group returns its group's result. The loop runs
+// until every group is done, so the shuffles always see the whole warp.
+template <int W>
+__device__ __forceinline__ Side group_side(const uint32_t *__restrict__ T,
+                                           const uint32_t *__restrict__ Q, long long pt0,
+                                           long long pq0, int dir, int avail, bool active, int X,
+                                           const int *lut, int lane, uint32_t &status) {
+    const int gl = lane & (W - 1), gbase = lane & ~(W - 1);
+    const unsigned gmask = W == 32 ? 0xffffffffu : (((1u << W) - 1u) << gbase);
+    int carry = 0, best = 0, blen = 0, scored = active ? avail : 0;
+    bool done = !active || avail <= 0;
+    for (int k0 = 0; __any_sync(0xffffffffu, !done); k0 += W) {
+        const int k = k0 + gl;
+        const bool valid = !done && k < avail;
+        int s = 0;
+        if (valid)
+            s = lut[base_at(T, pt0 + dir * (long long)k) * 4u + base_at(Q, pq0 + dir * (long long)k)];
+        const int P = grp_incl_sum<W>(s, gl) + carry;
+        const int Mx = max(grp_incl_max<W>(P, gl), best);
+        const unsigned stopm = __ballot_sync(0xffffffffu, valid && (Mx - P > X)) & gmask;
+        const unsigned validm = __ballot_sync(0xffffffffu, valid) & gmask;
+        const int nvalid = __popc(validm);
+        const int last = stopm ? __ffs(stopm) - 1 - gbase : nvalid - 1;
+        const int bl = __shfl_sync(0xffffffffu, Mx, gbase + max(0, last));
+        const unsigned m =
+            __ballot_sync(0xffffffffu, valid && gl <= last && P == bl) & gmask;
+        const int cend = __shfl_sync(0xffffffffu, P, gbase + W - 1);
+        if (!done) {
+            if (bl > best) {
+                blen = k0 + (__ffs(m) - 1 - gbase) + 1;
+                best = bl;
+            }
+            if (best > SCORE_LIMIT) status |= ST_SCORE_OVERFLOW;
+            if (stopm) {
+                scored = k0 + last + 1;
+                done = true;
+            } else if (k0 + W >= avail) {
+                done = true;
+            }
+            carry = cend;
+        }
+    }
+    return {best, blen, scored};
+}
+
+template <int W>
+__global__ void __launch_bounds__(W_BLOCK) walk_spec_kernel(const uint64_t *__restrict__ hits,
+                                                            uint32_t n, WalkParams wp) {
+    constexpr int K = 32 / W;
+    __shared__ int lut[16];
+    if (threadIdx.x < 16) lut[threadIdx.x] = wp.scores[threadIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane / W, gl = lane & (W - 1);
+    const int span = wp.span, X = wp.xdrop;
+    const long long qoff = wp.qlen - span;
+    unsigned long long ext = 0, cells = 0, shadow = 0, tasks = 0;
+    uint32_t status = 0;
+    SegCtx c;
+    seg_ctx<false>(wp, 0u, c);
+    while (true) {
+        uint32_t w = 0;
+        if (lane == 0) w = atomicAdd(wp.work_next, 1u);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= wp.nchunks) break;
+        uint32_t i = w * wp.chunk;
+        const uint32_t end = (uint32_t)min((long long)n, (long long)i + wp.chunk);
+        // a diagonal that started before this chunk belongs to the previous one
+        if (i > 0 && i < end && diag_of(hits[i]) == diag_of(hits[i - 1]))
+            i = segment_end(hits, i, n, diag_of(hits[i]));
+        while (i < end) {
+            const uint32_t D = diag_of(hits[i]);
+            const uint32_t se = segment_end(hits, i, n, D);
+            const long long Dl = (long long)(D & 0x7FFFFFFFu);
+            int E = wp.Ecarry ? wp.Ecarry[Dl] : INT_MIN;
+            tasks++;
+            uint32_t j = i;
+            while (true) {
+                while (j < se && (long long)(uint32_t)hits[j] < E) j++;  // covered: skipped
+                if (j >= se) break;
+                // the window: hits j .. j + K - 1 of this diagonal, group g takes j + g
+                const uint32_t my = j + g;
+                const bool active = my < se;
+                const long long t = active ? (long long)(uint32_t)hits[my] : 0;
+                const long long q = t - Dl + qoff;
+                int s = 0;
+                if (active)
+                    for (int k = gl; k < span; k += W)
+                        s += lut[base_at(wp.T, t + k) * 4u + base_at(c.Q, q + k)];
+                s = grp_incl_sum<W>(s, gl);
+                const int s0 = __shfl_sync(0xffffffffu, s, (lane & ~(W - 1)) + W - 1);
+                const int ravail = active ? (int)min(wp.tlen - t - span, wp.qlen - q - span) : 0;
+                const int lavail = active ? (int)min(t, q) : 0;
+                const Side r = group_side<W>(wp.T, c.Q, t + span, q + span, +1, ravail, active, X,
+                                             lut, lane, status);
+                const Side l = group_side<W>(wp.T, c.Q, t - 1, q - 1, -1, lavail, active, X, lut,
+                                             lane, status);
+                // commit in t order
+                for (int gg = 0; gg < K && j + gg < se; gg++) {
+                    const int src = gg * W;
+                    const long long tg = __shfl_sync(0xffffffffu, t, src);
+                    const long long qg = __shfl_sync(0xffffffffu, q, src);
+                    const int sg = __shfl_sync(0xffffffffu, s0, src);
+                    const int rb = __shfl_sync(0xffffffffu, r.best, src);
+                    const int rbl = __shfl_sync(0xffffffffu, r.blen, src);
+                    const int rsc = __shfl_sync(0xffffffffu, r.scored, src);
+                    const int lb = __shfl_sync(0xffffffffu, l.best, src);
+                    const int lbl = __shfl_sync(0xffffffffu, l.blen, src);
+                    const int lsc = __shfl_sync(0xffffffffu, l.scored, src);
+                    const unsigned long long work = (unsigned long long)(span + rsc + lsc);
+                    if (tg < E) {  // covered by a hit committed in this window
+                        shadow += work;
+                        continue;
+                    }
+                    const long long score = (long long)sg + rb + lb;
+                    if (score > INT_MAX) status |= ST_SCORE_OVERFLOW;
+                    ext++;
+                    cells += work;
+                    if (lane == 0) log_ext(wp, c, tg, qg, rsc, lsc);
+                    const bool pass = score >= wp.thresh;
+                    if (pass && lane == 0) emit<false>(wp, c, tg, qg, lbl, rbl, score, status);
+                    if (pass || !(wp.flags & SFE_SKIP_PASSING_ONLY)) E = (int)(tg + span + rbl);
+                }
+                j += K;
+            }
+            if (wp.Ecarry && lane == 0) wp.Ecarry[Dl] = E;
+            i = se;
+        }
+    }
+    if (lane == 0) {
+        if (ext) atomicAdd(&wp.ctr->extended, ext);
+        if (cells) atomicAdd(&wp.ctr->cells, cells);
+        if (shadow) atomicAdd(&wp.ctr->shadow, shadow);
+        if (tasks) atomicAdd(&wp.ctr->warp_tasks, tasks);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) status |= __shfl_down_sync(0xffffffffu, status, o);
+    if (lane == 0 && status) atomicOr(&wp.ctr->status, status);
+}
+
 template <bool BATCH>
 __global__ void __launch_bounds__(W_BLOCK) walk_warps_kernel(const uint64_t *__restrict__ hits,
                                                              uint32_t nhits, WalkParams wp) {
@@ -833,6 +1005,26 @@ cudaError_t launch_walk_persistent(const uint64_t *hits, long long n, WalkParams
     if (!packed && !batch) return launch_persistent_t<false, false>(hits, n, wp, st);
     if (packed) return launch_persistent_t<true, true>(hits, n, wp, st);
     return launch_persistent_t<false, true>(hits, n, wp, st);
+}
+
+cudaError_t launch_walk_speculative(const uint64_t *hits, long long n, WalkParams wp, int window,
+                                    cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (wp.pairs) return cudaErrorInvalidValue;  // one pair (or one hit list) at a time
+    if (wp.chunk == 0) wp.chunk = walk_auto_chunk(n);
+    wp.nchunks = (uint32_t)((n + wp.chunk - 1) / wp.chunk);
+    const unsigned grid = (unsigned)(4 * sms());
+    g_launches++;
+    switch (window) {
+    case 1: walk_spec_kernel<32><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, wp); break;
+    case 2: walk_spec_kernel<16><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, wp); break;
+    case 4: walk_spec_kernel<8><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, wp); break;
+    case 8: walk_spec_kernel<4><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, wp); break;
+    case 16: walk_spec_kernel<2><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, wp); break;
+    case 32: walk_spec_kernel<1><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, wp); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 size_t walk_schedule_temp_bytes(long long n, uint32_t chunk) {

@@ -20,7 +20,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW = 0, -1, -2, -3, -4, -5
 SKIP_PASSING_ONLY = 1
 TIME_STAGES = 2
 NO_CELL_PLANES = 4
-WALK_TWO_LAUNCHES, WALK_PERSISTENT = 0, 1
+WALK_TWO_LAUNCHES, WALK_PERSISTENT, WALK_SPECULATIVE = 0, 1, 2
 SCHED_NATURAL, SCHED_LARGEST_FIRST, SCHED_PREDICTED, SCHED_RANDOM = 0, 1, 2, 3
 TEST_UNPUBLISHED_QUEUE_ENTRY = 1
 TEST_DENSE_INDEX = 2
@@ -50,7 +50,7 @@ class Params(C.Structure):
                 ("walk_chunk", C.c_int32), ("walk_mode", C.c_int32), ("walk_schedule", C.c_int32),
                 ("ext_log_every", C.c_int32), ("ext_log", C.c_void_p), ("ext_log_cap", C.c_int64),
                 ("model", C.c_void_p), ("wait_limit", C.c_int32), ("test_hooks", C.c_int32),
-                ("step", C.c_int32)]
+                ("step", C.c_int32), ("spec_window", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -90,6 +90,7 @@ def lib() -> C.CDLL:
         L.sfe_ctx_create.argtypes = [C.c_int, C.POINTER(vp)]
         L.sfe_ctx_set_stream.argtypes = [vp, vp]
         L.sfe_ctx_fail_next_allocs.argtypes = [vp, i32]
+        L.sfe_ctx_set_walk.argtypes = [vp, C.POINTER(Params)]
         L.sfe_test_radix_sort.argtypes = [vp, vp, i64, i32, i32, i32]
         L.sfe_test_radix_sort.restype = C.c_int
         L.sfe_ctx_fail_next_allocs.restype = C.c_int
@@ -203,6 +204,10 @@ class Context:
         ptr, nbytes, keep = _buf(keys)
         _check(lib().sfe_test_radix_sort(self.h, ptr, nbytes // 8, int(lo), int(hi),
                                          int(bool(device_count))))
+
+    def set_walk(self, params: Params | None) -> None:
+        """Walk settings for later ungapped_xdrop calls (sfe_ctx_set_walk); None: defaults."""
+        _check(lib().sfe_ctx_set_walk(self.h, C.byref(params) if params is not None else None))
 
     def fail_next_allocs(self, n: int) -> None:
         """Test hook: the next n scratch allocations fail with SFE_ENOMEM."""

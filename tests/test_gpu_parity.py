@@ -331,3 +331,53 @@ def test_sparse_and_dense_index_agree(pkg, ctx, pattern, step, dense):
         t, q = oracle.seed_hits(p.T, Qs, pattern, True, step)
         mine = h[h["strand"] == s]
         assert np.array_equal(mine["tpos"], t) and np.array_equal(mine["qpos"], q)
+
+
+# ------------------------------------------------------------------ speculative window
+@pytest.mark.parametrize("window", [1, 2, 4, 8, 16, 32])
+def test_speculative_window_keeps_the_output(pkg, ctx, window):
+    """Algorithm 3's speculative batch on the per-diagonal skip: any window of
+    hits extended at once and committed in t order gives the serial output;
+    window 1 does no shadow work, larger windows do on dense diagonals."""
+    kw = dict(walk_mode=pkg.WALK_SPECULATIVE, spec_window=window)
+    p = synth.tiny_pair(2, length=60_000, n_blocks=15)
+    got, st, ref = run_both(pkg, ctx, p.T, p.Q, **kw)
+    assert_same(got, st, ref)
+    st_ = synth.Stream(34, "spec")
+    T = synth.iid_bases(st_, 20_000, 0.5)
+    got, st, ref = run_both(pkg, ctx, T, T.copy(), **kw)  # one long, dense diagonal per strand
+    assert_same(got, st, ref)
+    assert (st["shadow_cells"] == 0) if window == 1 else (st["shadow_cells"] > 0)
+    T, Q = _pair(72, 9001, 7333, blocks=6)
+    got, st, ref = run_both(pkg, ctx, T, Q, thresh=1000, flags=1, **kw)  # skip-passing-only
+    assert_same(got, st, ref)
+    got, st, ref = run_both(pkg, ctx, T, Q, tile_hits=500, walk_chunk=3, **kw)  # E across tiles
+    assert_same(got, st, ref)
+
+
+def test_speculative_window_through_the_hit_list_call(pkg, ctx):
+    p = synth.tiny_pair(7, length=50_000, n_blocks=12)
+    ref = oracle.run(p.T, p.Q)
+    ix = ctx.index_build(p.T, pkg.default_params(input_codes=1))
+    try:
+        hits = ctx.seed_hits(ix, p.Q)
+        ctx.set_walk(pkg.default_params(walk_mode=pkg.WALK_SPECULATIVE, spec_window=4))
+        got, st = ctx.ungapped_xdrop(ix, p.Q, hits, oracle.HOXD70, 910, 3000)
+        ctx.set_walk(None)
+    finally:
+        ix.close()
+    assert_same(got, st, ref)
+
+
+def test_speculative_window_rejects_a_batch_and_bad_windows(pkg, ctx):
+    from synth.workloads import concat_batch
+    pairs = synth.batch_pairs(seed=7, n_pairs=4, len_lo=2000, len_hi=5000)
+    T, toff, Q, qoff = concat_batch(pairs)
+    with pytest.raises(pkg.SfeError):
+        ctx.run_batch(T, toff, Q, qoff, pkg.default_params(input_codes=1,
+                                                           walk_mode=pkg.WALK_SPECULATIVE))
+    p = synth.tiny_pair(2, length=5_000, n_blocks=2)
+    for bad in (3, 64, -1):
+        with pytest.raises(pkg.SfeError):
+            ctx.run(p.T, p.Q, pkg.default_params(input_codes=1, walk_mode=pkg.WALK_SPECULATIVE,
+                                                 spec_window=bad))
