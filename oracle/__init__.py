@@ -47,6 +47,22 @@ EXT_DTYPE = np.dtype({
 })
 
 
+class _Half(C.Structure):
+    _fields_ = [("best", C.c_int64), ("bi", C.c_int32), ("bj", C.c_int32), ("cells", C.c_int64)]
+
+
+class _GStats(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("anchors", "skipped", "extended", "cells", "shadow",
+                                          "shadow_cells", "committed", "batches")]
+
+
+GALIGN_DTYPE = np.dtype([("strand", "<i4"), ("tstart", "<i4"), ("tend", "<i4"),
+                         ("qstart", "<i4"), ("qend", "<i4"), ("score", "<i4")])
+# LASTZ's default gapped scoring with HOXD70: gap open 400, extend 30 (a gap of
+# L bases costs 400 + 30 L), Y = 400 + 300 x 30, gapped threshold 3000.
+GAP_OPEN, GAP_EXTEND, YDROP, GAPPED_THRESH, BAND = 400, 30, 9400, 3000, 256
+
+
 class _Stats(C.Structure):
     _fields_ = [("hits", C.c_int64), ("extended", C.c_int64), ("cells", C.c_int64),
                 ("hsps", C.c_int64)]
@@ -87,6 +103,14 @@ def _bind(path: str):
     L.or_xdrop.argtypes = [u8p, C.c_int64, u8p, C.c_int64, C.c_int64, C.c_int64, C.c_int,
                            i32p, C.c_int32, C.POINTER(_Ext)]
     L.or_xdrop.restype = None
+    L.or_ydrop_half.argtypes = [u8p, C.c_int64, C.c_int64, u8p, C.c_int64, C.c_int64, C.c_int,
+                                i32p, C.c_int32, C.c_int32, C.c_int32, C.c_int,
+                                C.POINTER(_Half)]
+    L.or_ydrop_half.restype = None
+    L.or_gapped.argtypes = [u8p, C.c_int64, u8p, C.c_int64, C.c_void_p, C.c_int64, i32p,
+                            C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int, C.c_int64,
+                            C.c_void_p, C.c_int64, C.POINTER(_GStats)]
+    L.or_gapped.restype = C.c_int64
     L.or_result_count.argtypes = [C.c_void_p]
     L.or_result_count.restype = C.c_int64
     L.or_result_ext_count.argtypes = [C.c_void_p]
@@ -303,3 +327,47 @@ def xdrop(T, Qs, t: int, q: int, span: int = 19, scores=HOXD70, X: int = XDROP) 
             "score": e.score, "tpos": t - e.lext, "qpos": q - e.lext,
             "len": span + e.lext + e.rext, "end": t + span + e.rext,
             "cells": span + e.lscored + e.rscored}
+
+
+def ydrop_half(T, t0: int, Qs, q0: int, direction: int, scores=HOXD70, gap_open: int = GAP_OPEN,
+               gap_extend: int = GAP_EXTEND, Y: int = YDROP, band: int = BAND) -> dict:
+    """One half of a gapped Y-drop extension from anchor (t0, q0): forward
+    (direction +1) over T[t0:], Qs[q0:], backward (-1) over T[:t0], Qs[:q0] reversed.
+    Returns best, (bi, bj) (bases consumed at the best cell) and cells."""
+    T, Qs = _u8(T), _u8(Qs)
+    M = _scores(scores)
+    h = _Half()
+    TL = T.size - t0 if direction > 0 else t0
+    QL = Qs.size - q0 if direction > 0 else q0
+    lib().or_ydrop_half(_ptr(T, C.c_uint8), int(t0), int(TL), _ptr(Qs, C.c_uint8), int(q0),
+                        int(QL), int(direction), _ptr(M, C.c_int32), int(gap_open),
+                        int(gap_extend), int(Y), int(band), C.byref(h))
+    return {"best": h.best, "bi": h.bi, "bj": h.bj, "cells": h.cells}
+
+
+@dataclass
+class Gapped:
+    aligns: np.ndarray   # GALIGN_DTYPE, sorted by (strand, tstart, qstart, tend, qend, score)
+    stats: dict
+
+
+def gapped(T, Q, hsps, scores=HOXD70, gap_open: int = GAP_OPEN, gap_extend: int = GAP_EXTEND,
+           Y: int = YDROP, thresh: int = GAPPED_THRESH, band: int = BAND,
+           batch: int = 0) -> Gapped:
+    """The gapped stage over a pair's HSPs (HSP_DTYPE): anchors at the HSPs'
+    midpoints in decreasing score, skipped when inside a committed alignment,
+    Y-drop extended, committed at >= thresh. batch 0: Algorithm 1 (serial);
+    batch K: Algorithm 3 (speculative batches of K, serial commit)."""
+    T, Q = _u8(T), _u8(Q)
+    H = np.ascontiguousarray(np.asarray(hsps).view(HSP_DTYPE))
+    M = _scores(scores)
+    st = _GStats()
+    L = lib()
+    out = np.zeros(max(1, H.size), dtype=GALIGN_DTYPE)
+    hp = H.ctypes.data if H.size else None
+    n = L.or_gapped(_ptr(T, C.c_uint8), T.size, _ptr(Q, C.c_uint8), Q.size, hp, H.size,
+                    _ptr(M, C.c_int32), int(gap_open), int(gap_extend), int(Y), int(thresh),
+                    int(band), int(batch), out.ctypes.data, out.size, C.byref(st))
+    if n < 0:
+        raise RuntimeError("oracle gapped stage failed")
+    return Gapped(out[:n].copy(), {k: int(getattr(st, k)) for k, _ in _GStats._fields_})

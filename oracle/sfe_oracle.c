@@ -777,3 +777,306 @@ void or_result_free(or_result *r)
     free(r->ext);
     free(r);
 }
+
+/* ======================================================= gapped (Y-drop) stage
+ *
+ * The gapped extension that follows the filter (Algorithm 1: an anchor inside
+ * an alignment already committed is skipped, the others are extended with
+ * Y-drop and committed when they reach the threshold; Algorithm 3: the same
+ * in speculative batches with a serial commit). The paper names Y-drop and
+ * LASTZ's loop; the details below are this build's readings.
+ *
+ *  Scoring: substitutions M[t][q], affine gaps (a gap of L bases costs
+ *  open + L * extend).
+ *
+ *  One half of an extension, from anchor (t0, q0) in direction dir: cell
+ *  (i, j), 0 <= i <= TL, 0 <= j <= QL, has consumed i target and j query
+ *  bases (forward: T[t0 .. t0+i), backward: T[t0-i .. t0)). H[0][0] = 0 and
+ *    E[i][j] = max(E[i][j-1] - ext, H[i][j-1] - open - ext)   (gap in T)
+ *    F[i][j] = max(F[i-1][j] - ext, H[i-1][j] - open - ext)   (gap in Q)
+ *    H[i][j] = max(H[i-1][j-1] + M[T_i][Q_j], E[i][j], F[i][j])
+ *  evaluated by anti-diagonals d = i + j. A cell is live when its H is at
+ *  least best - Y, best being the maximum H of the anti-diagonals before d;
+ *  a cell that is not live has H = E = F = -inf and feeds nothing. Anti-
+ *  diagonal d computes every cell from the lowest to the highest i that has
+ *  a live neighbour on d - 1 or a live diagonal predecessor on d - 2 (a
+ *  contiguous range), at most `band` of them (from the lowest i on). A diagonal step skips an anti-diagonal, so the half stops
+ *  only when two consecutive anti-diagonals hold no live cell. It returns
+ *  best and the first cell (lowest d, then lowest i) where best was reached;
+ *  cells = cells computed beyond the origin.
+ *
+ *  Anchor of an HSP: its midpoint (tpos + len/2, qpos + len/2). Alignment =
+ *  backward half + forward half: score = sum of the two bests, box
+ *  [t0 - bi_b, t0 + bi_f) x [q0 - bj_b, q0 + bj_f).
+ *
+ *  Order and containment: anchors in decreasing HSP score (then strand, tpos,
+ *  qpos, len); an anchor (t, q) is contained when it lies in the box
+ *  [tstart, tend) x [qstart, qend) of an alignment committed on its strand.
+ *  Only alignments with score >= threshold are committed (Algorithm 1's
+ *  CommitAlignment and UpdateMaskingLists).
+ */
+
+#define OR_YNEG (-(1 << 29))
+
+typedef struct {
+    int64_t best;
+    int32_t bi, bj;
+    int64_t cells;
+} or_half;
+
+typedef struct {
+    int32_t strand, tstart, tend, qstart, qend, score;
+} or_galign;
+
+typedef struct {
+    int64_t anchors;        /* anchors in the input */
+    int64_t skipped;        /* contained when reached (never extended) */
+    int64_t extended;       /* extensions whose result counts */
+    int64_t cells;          /* DP cells of those extensions */
+    int64_t shadow;         /* speculative extensions found contained at commit */
+    int64_t shadow_cells;   /* their DP cells */
+    int64_t committed;      /* alignments reported (score >= threshold) */
+    int64_t batches;
+} or_gstats;
+
+static int32_t tbase(const uint8_t *S, int64_t p0, int dir, int64_t i)
+{
+    /* base consumed by step i (1-based) of a half from p0 in direction dir */
+    return dir > 0 ? S[p0 + i - 1] : S[p0 - i];
+}
+
+void or_ydrop_half(const uint8_t *T, int64_t t0, int64_t TL, const uint8_t *Q, int64_t q0,
+                   int64_t QL, int dir, const int32_t *M, int32_t gopen, int32_t gext,
+                   int32_t Y, int band, or_half *out)
+{
+    int32_t *buf = (int32_t *)malloc((size_t)band * 7 * sizeof(int32_t));
+    int32_t *H2 = buf, *H1 = buf + band, *E1 = buf + 2 * band, *F1 = buf + 3 * band;
+    int32_t *H0 = buf + 4 * band, *E0 = buf + 5 * band, *F0 = buf + 6 * band;
+    /* anti-diagonal 0: the origin */
+    int64_t lo1 = 0, hi1 = 0, L1 = 0, R1 = 0;       /* computed range, live range of d - 1 */
+    int64_t lo2 = 1, hi2 = 0, L2 = 1, R2 = 0;       /* d - 2: nothing yet */
+    H1[0] = 0;
+    E1[0] = F1[0] = OR_YNEG;
+    int64_t best = 0;
+    int32_t bi = 0, bj = 0;
+    int64_t cells = 0;
+    for (int64_t d = 1;; d++) {
+        if (L1 > R1 && L2 > R2)
+            break; /* two anti-diagonals without a live cell: nothing can follow */
+        int64_t clo, chi;
+        if (L1 <= R1 && L2 <= R2) {
+            clo = L1 < L2 + 1 ? L1 : L2 + 1;
+            chi = R1 + 1 > R2 + 1 ? R1 + 1 : R2 + 1;
+        } else if (L1 <= R1) {
+            clo = L1;
+            chi = R1 + 1;
+        } else {
+            clo = L2 + 1;
+            chi = R2 + 1;
+        }
+        if (clo < d - QL)
+            clo = d - QL;
+        if (clo < 0)
+            clo = 0;
+        if (chi > TL)
+            chi = TL;
+        if (chi > d)
+            chi = d;
+        if (chi > clo + band - 1)
+            chi = clo + band - 1;
+        int64_t L0 = 1, R0 = 0, dbest = OR_YNEG; /* live range of d (empty: L0 > R0) */
+        int32_t dbi = 0;
+        for (int64_t i = clo; i <= chi; i++) {
+            int64_t j = d - i;
+            int32_t dg = OR_YNEG, e = OR_YNEG, f = OR_YNEG;
+            if (i >= 1 && j >= 1 && i - 1 >= lo2 && i - 1 <= hi2 && H2[i - 1 - lo2] > OR_YNEG)
+                dg = H2[i - 1 - lo2] + M[tbase(T, t0, dir, i) * 4 + tbase(Q, q0, dir, j)];
+            if (j >= 1 && i >= lo1 && i <= hi1 && H1[i - lo1] > OR_YNEG) {
+                int32_t a = E1[i - lo1] - gext, b = H1[i - lo1] - gopen - gext;
+                e = a > b ? a : b;
+            }
+            if (i >= 1 && i - 1 >= lo1 && i - 1 <= hi1 && H1[i - 1 - lo1] > OR_YNEG) {
+                int32_t a = F1[i - 1 - lo1] - gext, b = H1[i - 1 - lo1] - gopen - gext;
+                f = a > b ? a : b;
+            }
+            int32_t h = dg;
+            if (e > h)
+                h = e;
+            if (f > h)
+                h = f;
+            if (h <= OR_YNEG || (int64_t)h < best - Y) {
+                h = e = f = OR_YNEG;
+            } else {
+                if (L0 > R0)
+                    L0 = i;
+                R0 = i;
+                if (h > dbest) {
+                    dbest = h;
+                    dbi = (int32_t)i;
+                }
+            }
+            H0[i - clo] = h;
+            E0[i - clo] = e;
+            F0[i - clo] = f;
+            cells++;
+        }
+        if (dbest > best) {
+            best = dbest;
+            bi = dbi;
+            bj = (int32_t)(d - dbi);
+        }
+        /* rotate: d - 1 becomes d - 2, d becomes d - 1 */
+        int32_t *t;
+        t = H2; H2 = H1; H1 = H0; H0 = t;
+        t = E1; E1 = E0; E0 = t;
+        t = F1; F1 = F0; F0 = t;
+        lo2 = lo1; hi2 = hi1; L2 = L1; R2 = R1;
+        lo1 = clo; hi1 = chi; L1 = L0; R1 = R0;
+        if (clo > chi) { /* no candidate at all: an empty anti-diagonal */
+            lo1 = 1; hi1 = 0;
+        }
+    }
+    free(buf);
+    out->best = best;
+    out->bi = bi;
+    out->bj = bj;
+    out->cells = cells;
+}
+
+/* Both halves from anchor (t0, q0) of Qs. */
+static void ydrop_anchor(const uint8_t *T, int64_t tlen, const uint8_t *Qs, int64_t qlen,
+                         int64_t t0, int64_t q0, const int32_t *M, int32_t gopen, int32_t gext,
+                         int32_t Y, int band, int strand, or_galign *a, int64_t *cells)
+{
+    or_half f, b;
+    or_ydrop_half(T, t0, tlen - t0, Qs, q0, qlen - q0, +1, M, gopen, gext, Y, band, &f);
+    or_ydrop_half(T, t0, t0, Qs, q0, q0, -1, M, gopen, gext, Y, band, &b);
+    a->strand = strand;
+    a->tstart = (int32_t)(t0 - b.bi);
+    a->tend = (int32_t)(t0 + f.bi);
+    a->qstart = (int32_t)(q0 - b.bj);
+    a->qend = (int32_t)(q0 + f.bj);
+    a->score = (int32_t)(f.best + b.best);
+    *cells = f.cells + b.cells;
+}
+
+typedef struct {
+    or_hsp h;
+    int64_t idx;
+} or_anchor;
+
+static int cmp_anchor(const void *x, const void *y)
+{
+    const or_hsp *a = &((const or_anchor *)x)->h, *b = &((const or_anchor *)y)->h;
+    if (a->score != b->score) return a->score > b->score ? -1 : 1;
+    if (a->strand != b->strand) return a->strand < b->strand ? -1 : 1;
+    if (a->tpos != b->tpos) return a->tpos < b->tpos ? -1 : 1;
+    if (a->qpos != b->qpos) return a->qpos < b->qpos ? -1 : 1;
+    if (a->len != b->len) return a->len < b->len ? -1 : 1;
+    return 0;
+}
+
+static int cmp_galign(const void *x, const void *y)
+{
+    const or_galign *a = (const or_galign *)x, *b = (const or_galign *)y;
+    if (a->strand != b->strand) return a->strand < b->strand ? -1 : 1;
+    if (a->tstart != b->tstart) return a->tstart < b->tstart ? -1 : 1;
+    if (a->qstart != b->qstart) return a->qstart < b->qstart ? -1 : 1;
+    if (a->tend != b->tend) return a->tend < b->tend ? -1 : 1;
+    if (a->qend != b->qend) return a->qend < b->qend ? -1 : 1;
+    if (a->score != b->score) return a->score < b->score ? -1 : 1;
+    return 0;
+}
+
+/* Is (strand, t, q) inside the box of one of the n committed alignments? */
+static int contained(const or_galign *c, int64_t n, int strand, int64_t t, int64_t q)
+{
+    for (int64_t k = 0; k < n; k++)
+        if (c[k].strand == strand && c[k].tstart <= t && t < c[k].tend && c[k].qstart <= q &&
+            q < c[k].qend)
+            return 1;
+    return 0;
+}
+
+/*
+ * The gapped stage over the HSPs of a pair (strand 1 coordinates index the
+ * reverse complement of Q). batch <= 0: Algorithm 1 (serial). batch K > 0:
+ * Algorithm 3 (the next K anchors not contained in what is committed so far
+ * are extended, then committed one by one in order unless an alignment
+ * committed before them, in this batch or earlier, now contains them). Writes
+ * at most cap alignments, sorted by (strand, tstart, qstart, tend, qend,
+ * score); returns their number, or -1 on error.
+ */
+int64_t or_gapped(const uint8_t *T, int64_t tlen, const uint8_t *Q, int64_t qlen,
+                  const or_hsp *hsps, int64_t nhsps, const int32_t *M, int32_t gopen,
+                  int32_t gext, int32_t Y, int32_t thresh, int band, int64_t batch,
+                  or_galign *out, int64_t cap, or_gstats *st)
+{
+    memset(st, 0, sizeof(*st));
+    st->anchors = nhsps;
+    if (band < 1 || gopen < 0 || gext < 0 || Y < 0)
+        return -1;
+    uint8_t *rc = (uint8_t *)malloc((size_t)(qlen > 0 ? qlen : 1));
+    or_anchor *an = (or_anchor *)malloc((size_t)(nhsps > 0 ? nhsps : 1) * sizeof(or_anchor));
+    or_galign *com = (or_galign *)malloc((size_t)(nhsps > 0 ? nhsps : 1) * sizeof(or_galign));
+    or_galign *ext = (or_galign *)malloc((size_t)(nhsps > 0 ? nhsps : 1) * sizeof(or_galign));
+    int64_t *ecells = (int64_t *)malloc((size_t)(nhsps > 0 ? nhsps : 1) * sizeof(int64_t));
+    int64_t *pick = (int64_t *)malloc((size_t)(nhsps > 0 ? nhsps : 1) * sizeof(int64_t));
+    if (!rc || !an || !com || !ext || !ecells || !pick) {
+        free(rc); free(an); free(com); free(ext); free(ecells); free(pick);
+        return -1;
+    }
+    or_revcomp(Q, qlen, rc);
+    for (int64_t k = 0; k < nhsps; k++) {
+        an[k].h = hsps[k];
+        an[k].idx = k;
+    }
+    qsort(an, (size_t)nhsps, sizeof(or_anchor), cmp_anchor);
+    int64_t ncom = 0, j = 0;
+    while (j < nhsps) {
+        /* phase 1: the next anchors not contained in what is committed */
+        int64_t nb = 0;
+        int64_t K = batch > 0 ? batch : 1;
+        while (nb < K && j < nhsps) {
+            const or_hsp *h = &an[j].h;
+            int64_t ta = h->tpos + h->len / 2, qa = h->qpos + h->len / 2;
+            if (contained(com, ncom, h->strand, ta, qa))
+                st->skipped++;
+            else
+                pick[nb++] = j;
+            j++;
+        }
+        if (nb == 0)
+            break;
+        st->batches++;
+        /* phase 2: extend every picked anchor */
+        for (int64_t b = 0; b < nb; b++) {
+            const or_hsp *h = &an[pick[b]].h;
+            int64_t ta = h->tpos + h->len / 2, qa = h->qpos + h->len / 2;
+            const uint8_t *Qs = h->strand ? rc : Q;
+            ydrop_anchor(T, tlen, Qs, qlen, ta, qa, M, gopen, gext, Y, band, h->strand, &ext[b],
+                         &ecells[b]);
+        }
+        /* phase 3: commit in order */
+        for (int64_t b = 0; b < nb; b++) {
+            const or_hsp *h = &an[pick[b]].h;
+            int64_t ta = h->tpos + h->len / 2, qa = h->qpos + h->len / 2;
+            if (b > 0 && contained(com, ncom, h->strand, ta, qa)) {
+                st->shadow++;
+                st->shadow_cells += ecells[b];
+                continue;
+            }
+            st->extended++;
+            st->cells += ecells[b];
+            if (ext[b].score >= thresh)
+                com[ncom++] = ext[b];
+        }
+    }
+    st->committed = ncom;
+    qsort(com, (size_t)ncom, sizeof(or_galign), cmp_galign);
+    for (int64_t k = 0; k < ncom && k < cap; k++)
+        out[k] = com[k];
+    free(rc); free(an); free(ext); free(ecells); free(pick);
+    free(com);
+    return ncom;
+}

@@ -128,3 +128,86 @@ def serial_query_order(T, Q, pattern, transition, strands, M, X, thresh, skip_pa
                 out.append((s, e["tpos"], e["qpos"], e["len"], e["score"]))
     out.sort()
     return out, st
+
+
+def gotoh_half_full(Tseg, Qseg, M, gap_open, gap_extend):
+    """Affine-gap DP of one extension half over whole segments, no pruning:
+    Tseg / Qseg already oriented (step k consumes Tseg[k-1]). Row by row,
+    H[0][0] = 0, a gap of L bases costs open + L * extend. Returns the H matrix."""
+    n, m = len(Tseg), len(Qseg)
+    NEG = -(1 << 40)
+    H = np.full((n + 1, m + 1), NEG, dtype=np.int64)
+    E = np.full((n + 1, m + 1), NEG, dtype=np.int64)
+    F = np.full((n + 1, m + 1), NEG, dtype=np.int64)
+    H[0, 0] = 0
+    M = np.asarray(M, dtype=np.int64).reshape(4, 4)
+    for i in range(n + 1):
+        for j in range(m + 1):
+            if i == 0 and j == 0:
+                continue
+            e = max(E[i, j - 1] - gap_extend, H[i, j - 1] - gap_open - gap_extend) if j else NEG
+            f = max(F[i - 1, j] - gap_extend, H[i - 1, j] - gap_open - gap_extend) if i else NEG
+            dg = H[i - 1, j - 1] + M[Tseg[i - 1], Qseg[j - 1]] if i and j else NEG
+            E[i, j], F[i, j] = e, f
+            H[i, j] = max(dg, e, f)
+    return H
+
+
+def first_max_by_antidiagonal(H):
+    """Maximum of H and its first cell in the order (i + j, then i)."""
+    best = int(H.max())
+    cells = [(i + j, i, j) for i, j in zip(*np.nonzero(H == best))]
+    d, i, j = min(cells)
+    return best, int(i), int(j)
+
+
+def ydrop_half_sets(Tseg, Qseg, M, gap_open, gap_extend, Y, band):
+    """The Y-drop half written with Python sets and dicts: live cells of the last
+    two anti-diagonals; the candidates of anti-diagonal d are every i from the
+    lowest to the highest cell next to a live cell of d - 1 or one diagonal
+    step from a live cell of d - 2 (inside the matrix), the `band` of lowest i
+    kept; stop after two anti-diagonals without a live cell. Returns
+    (best, i, j, cells) with the first best cell by (anti-diagonal, i)."""
+    n, m = len(Tseg), len(Qseg)
+    M = np.asarray(M, dtype=np.int64).reshape(4, 4)
+    prev2, prev1 = {}, {(0, 0): (0, None, None)}  # cell -> (H, E, F) of live cells
+    best, bi, bj, cells = 0, 0, 0, 0
+    d = 0
+    while prev1 or prev2:
+        d += 1
+        cand = {i for (i, j) in prev1} | {i + 1 for (i, j) in prev1} | \
+            {i + 1 for (i, j) in prev2}
+        cand = [i for i in range(min(cand), max(cand) + 1) if 0 <= i <= n and 0 <= d - i <= m]
+        cand = cand[:band]
+        cur, dbest, dcell = {}, None, None
+        for i in cand:
+            j = d - i
+            cells += 1
+            opts = []
+            if (i - 1, j - 1) in prev2 and i >= 1 and j >= 1:
+                opts.append(prev2[(i - 1, j - 1)][0] + M[Tseg[i - 1], Qseg[j - 1]])
+            e = f = None
+            if (i, j - 1) in prev1:
+                h1, e1, _ = prev1[(i, j - 1)]
+                e = h1 - gap_open - gap_extend if e1 is None else max(
+                    e1 - gap_extend, h1 - gap_open - gap_extend)
+                opts.append(e)
+            if (i - 1, j) in prev1:
+                h1, _, f1 = prev1[(i - 1, j)]
+                f = h1 - gap_open - gap_extend if f1 is None else max(
+                    f1 - gap_extend, h1 - gap_open - gap_extend)
+                opts.append(f)
+            if not opts:
+                continue
+            h = max(opts)
+            if h < best - Y:
+                continue
+            cur[(i, j)] = (h, e, f)
+            if dbest is None or h > dbest:
+                dbest, dcell = h, (i, j)
+        if dbest is not None and dbest > best:
+            best, (bi, bj) = dbest, dcell
+        prev2, prev1 = prev1, cur
+        if not prev1 and not prev2:
+            break
+    return best, bi, bj, cells
