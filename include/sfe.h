@@ -401,6 +401,78 @@ int sfe_mlp_train(sfe_ctx *ctx, const sfe_mlp_data *data, float *params, int32_t
                   int32_t batch, float lr, uint64_t seed, double *epoch_loss);
 
 /*
+ * Gapped extension after the filter (the stage Algorithm 1 runs on the
+ * filter's survivors: YDropExtension with containment skipping, and
+ * Algorithm 3's speculative batches with a serial commit).
+ *
+ * Anchors: the midpoint (tpos + len/2, qpos + len/2) of each HSP (hsps:
+ * nhsps records, host or device, as sfe_run writes them; the score orders
+ * them), taken in decreasing HSP score (then strand, tpos, qpos, len). An
+ * anchor that lies inside the box [tstart, tend) x [qstart, qend) of an
+ * alignment committed on its strand is skipped; the others are extended and
+ * committed when their score reaches gapped_thresh.
+ *
+ * Extension: from the anchor forward and backward, the affine-gap dynamic
+ * program (substitutions scores[4 * target_base + query_base], a gap of L
+ * bases costs gap_open + L * gap_extend) by anti-diagonals: a cell is live
+ * while its score is at least best - ydrop (best over the earlier
+ * anti-diagonals); an anti-diagonal computes every cell from the lowest to
+ * the highest that has a live neighbour on the previous one or a live
+ * diagonal predecessor on the one before, at most `band` cells; a half stops
+ * after two anti-diagonals without a live cell. Alignment score = the two
+ * halves' best scores; its box runs from the backward half's best cell to the
+ * forward half's (the first cell, by anti-diagonal then target offset, that
+ * reached the best). One GPU warp per anchor half.
+ *
+ * Batches (Algorithm 3): the host takes the next `batch` anchors not
+ * contained in what is committed (0: every anchor in one batch), the GPU
+ * extends them all, and the host commits them in order, dropping those that
+ * an alignment committed before them in the batch now contains (their work
+ * is stats.shadow / shadow_cells). The output does not depend on the batch
+ * size. Strand 1 coordinates index the reverse complement of the query.
+ *
+ * out: cap records (host or device), sorted by (strand, tstart, qstart,
+ * tend, qend, score); *nout the count (SFE_EOVERFLOW if above cap, or if a
+ * score left the int32 range). Limits: |scores| <= 2^15, gap costs and ydrop
+ * in [0, 2^28], band 1..256.
+ */
+typedef struct {
+    int32_t strand, tstart, tend, qstart, qend, score;
+} sfe_galign;
+
+typedef struct {
+    int32_t scores[16];
+    int32_t gap_open;      /* default 400 */
+    int32_t gap_extend;    /* default 30 */
+    int32_t ydrop;         /* default 9400 */
+    int32_t gapped_thresh; /* default 3000 */
+    int32_t band;          /* cells per anti-diagonal, 1..256; 0 = 256 */
+    int32_t input_codes;   /* 0: ASCII ACGTacgt, 1: codes 0..3 */
+    int64_t batch;         /* anchors per speculative batch; 0 = all in one batch */
+} sfe_ydrop_params;
+
+typedef struct {
+    int64_t anchors;      /* HSPs given */
+    int64_t skipped;      /* anchors contained when the scan reached them (never extended) */
+    int64_t extended;     /* extensions whose result counts */
+    int64_t cells;        /* DP cells of those extensions */
+    int64_t shadow;       /* speculative extensions dropped at the commit */
+    int64_t shadow_cells; /* their DP cells */
+    int64_t committed;    /* alignments reported */
+    int64_t batches;
+    double device_ms;     /* extension kernels (CUDA events on the context's stream) */
+    double total_ms;      /* the whole call, host scan and commit included (host clock) */
+} sfe_ydrop_stats;
+
+/* Fill *p with the defaults (HOXD70, 400/30, Y 9400, threshold 3000, band 256,
+ * one batch). */
+int sfe_ydrop_params_default(sfe_ydrop_params *p);
+int sfe_gapped_extend(sfe_ctx *ctx, const uint8_t *target, int64_t tlen, const uint8_t *query,
+                      int64_t qlen, const sfe_hsp *hsps, int64_t nhsps,
+                      const sfe_ydrop_params *params, sfe_galign *out, int64_t cap,
+                      int64_t *nout, sfe_ydrop_stats *stats);
+
+/*
  * Allocation-free variant of sfe_ungapped_xdrop (the paper has no counterpart:
  * this entry point exists for callers of the library, not for the method).
  *

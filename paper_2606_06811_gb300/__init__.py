@@ -6,7 +6,7 @@ include/sfe.h. `sfe` is the Python binding (argument marshalling only);
 `build` compiles the library in-tree.
 """
 from .sfe import (  # noqa: F401
-    BATCH_HSP_DTYPE, EXT_DTYPE, HIT_DTYPE, HSP_DTYPE, NO_CELL_PLANES, SCHED_LARGEST_FIRST,
+    BATCH_HSP_DTYPE, EXT_DTYPE, GALIGN_DTYPE, YdropParams, ydrop_params, HIT_DTYPE, HSP_DTYPE, NO_CELL_PLANES, SCHED_LARGEST_FIRST,
     SCHED_NATURAL, SCHED_PREDICTED, SCHED_RANDOM, SKIP_PASSING_ONLY, STAGES, TIME_STAGES,
     WALK_PERSISTENT, WALK_SPECULATIVE, WALK_TWO_LAUNCHES,
     BatchPlan, Context, Index, MlpData, Params, SfeError, Stats, default_params, exported_symbols, lib,

@@ -1,6 +1,8 @@
 // C ABI of libsfe (declared in include/sfe.h): context and scratch arena,
 // host/device staging, and the order of the kernels of the filter stage.
 #include <algorithm>
+#include <chrono>
+#include <map>
 #include <climits>
 #include <cstdio>
 #include <cstring>
@@ -54,7 +56,7 @@ enum Slot {
     SL_TIN, SL_QIN, SL_TP, SL_QP, SL_QM, SL_KEYS_A, SL_KEYS_B, SL_BCOUNT, SL_OFFS, SL_POS,
     SL_COUNTS, SL_STARTS, SL_HITS_A, SL_HITS_B, SL_QUEUE, SL_PAIRS, SL_BENTRIES, SL_SCHED,
     SL_HSPS, SL_TMP, SL_ECARRY, SL_PUB, SL_BOUNDS, SL_BSLOTS, SL_OFF2, SL_POS2, SL_PLANES, SL_LOW,
-    NSLOT
+    SL_YANCH, SL_YHALF, NSLOT
 };
 
 // Small device block: scores, counters and flags of one call.
@@ -1541,6 +1543,231 @@ void plan_release(sfe_batch_plan *pl) {
 }
 
 }  // namespace
+
+// ------------------------------------------------------------- gapped stage
+
+namespace {
+
+// Boxes of the committed alignments of one strand, found by target start:
+// an anchor (t, q) can only lie in a box that starts at most the longest box
+// length before t.
+struct CommittedBoxes {
+    std::vector<sfe_galign> boxes;
+    std::multimap<int32_t, int> by_start[2];
+    int32_t longest[2] = {0, 0};
+
+    bool contains(int strand, int32_t t, int32_t q) const {
+        const auto &m = by_start[strand];
+        for (auto it = m.lower_bound(t - longest[strand]); it != m.end() && it->first <= t; ++it) {
+            const sfe_galign &b = boxes[it->second];
+            if (t < b.tend && b.qstart <= q && q < b.qend) return true;
+        }
+        return false;
+    }
+    void add(const sfe_galign &g) {
+        by_start[g.strand].emplace(g.tstart, (int)boxes.size());
+        longest[g.strand] = std::max(longest[g.strand], g.tend - g.tstart);
+        boxes.push_back(g);
+    }
+};
+
+int check_ydrop_params(const sfe_ydrop_params *p) {
+    if (!p) return fail(SFE_EINVAL, "params is NULL");
+    for (int i = 0; i < 16; i++)
+        if (p->scores[i] < -(1 << 15) || p->scores[i] > (1 << 15))
+            return fail(SFE_EINVAL, "gapped scores must lie in [-2^15, 2^15]");
+    if (p->gap_open < 0 || p->gap_extend < 0 || p->ydrop < 0 || p->gap_open > (1 << 28) ||
+        p->gap_extend > (1 << 28) || p->ydrop > (1 << 28))
+        return fail(SFE_EINVAL, "gap costs and ydrop must lie in [0, 2^28]");
+    if (p->band < 0 || p->band > YD_MAX_BAND) return fail(SFE_EINVAL, "band must be 0..256");
+    if (p->batch < 0) return fail(SFE_EINVAL, "batch must be >= 0");
+    if (p->input_codes != 0 && p->input_codes != 1) return fail(SFE_EINVAL, "input_codes must be 0 or 1");
+    return SFE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sfe_ydrop_params_default(sfe_ydrop_params *p) {
+    if (!p) return fail(SFE_EINVAL, "params is NULL");
+    memset(p, 0, sizeof(*p));
+    memcpy(p->scores, kHoxd70, sizeof(kHoxd70));
+    p->gap_open = 400;
+    p->gap_extend = 30;
+    p->ydrop = 9400;
+    p->gapped_thresh = 3000;
+    p->band = YD_MAX_BAND;
+    return SFE_OK;
+}
+
+int sfe_gapped_extend(sfe_ctx *c, const uint8_t *target, int64_t tlen, const uint8_t *query,
+                      int64_t qlen, const sfe_hsp *hsps, int64_t nhsps,
+                      const sfe_ydrop_params *params, sfe_galign *out, int64_t cap,
+                      int64_t *nout, sfe_ydrop_stats *stats) {
+    const auto w0 = std::chrono::steady_clock::now();
+    if (!nout) return fail(SFE_EINVAL, "nout is NULL");
+    TRY(check_ydrop_params(params));
+    TRY(check_len(tlen, "target"));
+    TRY(check_len(qlen, "query"));
+    if (nhsps < 0 || nhsps >= (1LL << 31)) return fail(SFE_EINVAL, "nhsps out of range");
+    if (nhsps > 0 && !hsps) return fail(SFE_EINVAL, "hsps is NULL");
+    TRY(begin(c));
+    // the anchors, on the host: the scan and the commit run there
+    std::vector<sfe_hsp> H((size_t)nhsps);
+    if (nhsps > 0) {
+        if (is_device_ptr(hsps)) {
+            CK(cudaMemcpyAsync(H.data(), hsps, (size_t)nhsps * sizeof(sfe_hsp),
+                               cudaMemcpyDeviceToHost, c->st));
+            CK(cudaStreamSynchronize(c->st));
+        } else {
+            memcpy(H.data(), hsps, (size_t)nhsps * sizeof(sfe_hsp));
+        }
+    }
+    for (const sfe_hsp &h : H)
+        if ((h.strand != 0 && h.strand != 1) || h.len < 0 || h.tpos < 0 || h.qpos < 0 ||
+            (int64_t)h.tpos + h.len / 2 > tlen || (int64_t)h.qpos + h.len / 2 > qlen)
+            return fail(SFE_EINVAL, "an HSP's anchor lies outside the sequences");
+    std::vector<int> order((size_t)nhsps);
+    for (int k = 0; k < (int)nhsps; k++) order[k] = k;
+    std::sort(order.begin(), order.end(), [&](int x, int y) {
+        const sfe_hsp &a = H[x], &b = H[y];
+        if (a.score != b.score) return a.score > b.score;
+        if (a.strand != b.strand) return a.strand < b.strand;
+        if (a.tpos != b.tpos) return a.tpos < b.tpos;
+        if (a.qpos != b.qpos) return a.qpos < b.qpos;
+        return a.len < b.len;
+    });
+    // the sequences, packed on the device
+    uint32_t *Tp = nullptr, *Qp = nullptr, *Qm = nullptr;
+    const void *tdev = nullptr, *qdev = nullptr;
+    TRY(stage(c, SL_TIN, target, (size_t)tlen, &tdev));
+    TRY(stage(c, SL_QIN, query, (size_t)qlen, &qdev));
+    TRY(pack_slot(c, SL_TP, reinterpret_cast<const uint8_t *>(tdev), tlen, params->input_codes,
+                  &Tp));
+    TRY(pack_slot(c, SL_QP, reinterpret_cast<const uint8_t *>(qdev), qlen, params->input_codes,
+                  &Qp));
+    TRY(rc_slot(c, SL_QM, Qp, qlen, &Qm));
+    TRY(sync_small(c));
+    TRY(check_status(c->host_small->status));
+    YdParams yp;
+    memcpy(yp.scores, params->scores, sizeof(yp.scores));
+    yp.gap_open = params->gap_open;
+    yp.gap_extend = params->gap_extend;
+    yp.ydrop = params->ydrop;
+    yp.band = params->band > 0 ? params->band : YD_MAX_BAND;
+    const long long K = params->batch > 0 ? std::min<long long>(params->batch, nhsps) : nhsps;
+    int4 *dan = nullptr;
+    YdHalf *dhalf = nullptr;
+    TRY(ensure_t(c, SL_YANCH, (size_t)std::max(1LL, K), &dan));
+    TRY(ensure_t(c, SL_YHALF, (size_t)std::max(1LL, 2 * K), &dhalf));
+    std::vector<int4> ban;
+    std::vector<int> bidx;
+    std::vector<YdHalf> half;
+    ban.reserve((size_t)K);
+    bidx.reserve((size_t)K);
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    CK(cudaEventCreate(&ev[0]));
+    CK(cudaEventCreate(&ev[1]));
+    CommittedBoxes com;
+    sfe_ydrop_stats st{};
+    st.anchors = nhsps;
+    uint32_t status = 0;
+    int rc = SFE_OK;
+    size_t j = 0;
+    while (j < order.size() && rc == SFE_OK) {
+        // phase 1: the next anchors not contained in what is committed
+        ban.clear();
+        bidx.clear();
+        while ((long long)ban.size() < K && j < order.size()) {
+            const sfe_hsp &h = H[order[j]];
+            const int32_t ta = h.tpos + h.len / 2, qa = h.qpos + h.len / 2;
+            if (com.contains(h.strand, ta, qa))
+                st.skipped++;
+            else {
+                ban.push_back(make_int4(h.strand, ta, qa, 0));
+                bidx.push_back(order[j]);
+            }
+            j++;
+        }
+        if (ban.empty()) break;
+        st.batches++;
+        // phase 2: every anchor of the batch, both halves, on the GPU
+        const int nb = (int)ban.size();
+        half.resize(2 * (size_t)nb);
+        cudaError_t e = cudaMemcpyAsync(dan, ban.data(), nb * sizeof(int4),
+                                        cudaMemcpyHostToDevice, c->st);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[0], c->st);
+        if (e == cudaSuccess) e = launch_ydrop(Tp, tlen, Qp, Qm, qlen, dan, nb, yp, dhalf, c->st);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(half.data(), dhalf, 2 * (size_t)nb * sizeof(YdHalf),
+                                cudaMemcpyDeviceToHost, c->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(SFE_ECUDA, std::string("gapped extension: ") + cudaGetErrorString(e));
+            break;
+        }
+        st.device_ms += ms;
+        // phase 3: commit in order
+        for (int b = 0; b < nb; b++) {
+            const YdHalf &f = half[2 * b], &r = half[2 * b + 1];
+            status |= f.status | r.status;
+            const int4 an = ban[b];
+            const long long work = f.cells + r.cells;
+            if (b > 0 && com.contains(an.x, an.y, an.z)) {
+                st.shadow++;
+                st.shadow_cells += work;
+                continue;
+            }
+            st.extended++;
+            st.cells += work;
+            const long long score = (long long)f.best + r.best;
+            if (score > INT_MAX) status |= ST_SCORE_OVERFLOW;
+            if (score >= params->gapped_thresh) {
+                sfe_galign g;
+                g.strand = an.x;
+                g.tstart = an.y - r.bi;
+                g.tend = an.y + f.bi;
+                g.qstart = an.z - r.bj;
+                g.qend = an.z + f.bj;
+                g.score = (int32_t)score;
+                com.add(g);
+            }
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (rc != SFE_OK) return rc;
+    if (status & ST_SCORE_OVERFLOW) return fail(SFE_EOVERFLOW, "a gapped score left the int32 range");
+    std::vector<sfe_galign> &A = com.boxes;
+    std::sort(A.begin(), A.end(), [](const sfe_galign &x, const sfe_galign &y) {
+        if (x.strand != y.strand) return x.strand < y.strand;
+        if (x.tstart != y.tstart) return x.tstart < y.tstart;
+        if (x.qstart != y.qstart) return x.qstart < y.qstart;
+        if (x.tend != y.tend) return x.tend < y.tend;
+        if (x.qend != y.qend) return x.qend < y.qend;
+        return x.score < y.score;
+    });
+    st.committed = (int64_t)A.size();
+    *nout = st.committed;
+    st.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0)
+                      .count();
+    if (stats) *stats = st;
+    if ((int64_t)A.size() > cap) return fail(SFE_EOVERFLOW, "alignment buffer too small");
+    if (!A.empty()) {
+        CK(cudaMemcpyAsync(out, A.data(), A.size() * sizeof(sfe_galign),
+                           is_device_ptr(out) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost,
+                           c->st));
+        CK(cudaStreamSynchronize(c->st));
+    }
+    return SFE_OK;
+}
+
+}  // extern "C"
 
 extern "C" {
 

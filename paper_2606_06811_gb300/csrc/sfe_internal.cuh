@@ -325,6 +325,26 @@ cudaError_t launch_walk_speculative(const uint64_t *hits, long long n, WalkParam
 cudaError_t launch_walk_persistent(const uint64_t *hits, long long n, WalkParams wp,
                                    cudaStream_t st);
 
+// Gapped Y-drop extension (ydrop.cu): one warp per anchor half. anchors[k] =
+// (strand, t, q, unused); task 2k is anchor k's forward half (T[t..],
+// Qs[q..]), task 2k + 1 its backward half (T[..t), Qs[..q) reversed); Qs is
+// the packed query (strand 0) or its reverse complement (strand 1).
+constexpr int YD_MAX_BAND = 256;
+struct YdParams {
+    int32_t scores[16];
+    int32_t gap_open, gap_extend, ydrop;
+    int32_t band;  // cells per anti-diagonal, 1..YD_MAX_BAND
+};
+struct YdHalf {
+    int32_t best, bi, bj;  // best score, bases of T and Q consumed at the first best cell
+    uint32_t status;       // ST_SCORE_OVERFLOW
+    long long cells;       // DP cells computed beyond the origin
+};
+size_t ydrop_smem_bytes(int band);
+cudaError_t launch_ydrop(const uint32_t *T, long long tlen, const uint32_t *Qp,
+                         const uint32_t *Qm, long long qlen, const int4 *anchors, int nanchors,
+                         const YdParams &prm, YdHalf *out, cudaStream_t st);
+
 // Sort HSPs in place by (strand, tpos, qpos, len, score); tpos < 2^tbits,
 // qpos < 2^qbits, tbits + qbits <= 62. tmp: hsp_sort_temp_bytes(n).
 size_t hsp_sort_temp_bytes(long long n);

@@ -1,0 +1,187 @@
+// Gapped Y-drop extension (the extension stage after the filter: Algorithm 1's
+// YDropExtension, run in Algorithm 3's speculative batches).
+//
+// One warp per anchor half (forward or backward from the anchor), as the
+// paper's systolic kernel maps one anchor-half per block. The affine-gap
+// dynamic program is evaluated by anti-diagonals d = i + j: cell (i, j) has
+// consumed i target and j query bases. The warp keeps the last two
+// anti-diagonals (H, E, F of every computed cell) in shared memory slots of at
+// most `band` cells; lanes take the cells of anti-diagonal d in chunks of 32,
+// each reading its diagonal predecessor from d - 2 and its two gap
+// predecessors from d - 1, and warp ballots and reductions give the live range
+// and the best cell. A cell is live while H >= best - Y (best over the earlier
+// anti-diagonals); anti-diagonal d computes every cell from the lowest to the
+// highest i next to a live cell of d - 1 or one diagonal step from a live cell
+// of d - 2, at most `band` of them, and the half stops after two
+// anti-diagonals without a live cell. Same rule, same cells, same result as
+// the oracle's or_ydrop_half.
+#include <climits>
+
+#include "sfe_internal.cuh"
+
+namespace sfe {
+
+namespace {
+
+constexpr int YD_WARPS = 4;        // warps per CTA (each owns 9 * band ints of shared memory)
+constexpr int YD_NEG = -(1 << 29); // -inf that survives subtracting a gap cost
+constexpr int YD_LIMIT = 1 << 30;  // a score above this flags overflow
+
+struct YdSlot {
+    int *H, *E, *F;
+};
+
+__device__ __forceinline__ int yd_base(const uint32_t *__restrict__ S, long long p0, int dir,
+                                       long long i) {
+    // base consumed by step i (1-based) of a half from p0 in direction dir
+    return (int)base_at(S, dir > 0 ? p0 + i - 1 : p0 - i);
+}
+
+__global__ void __launch_bounds__(YD_WARPS * 32) ydrop_half_kernel(
+    const uint32_t *__restrict__ T, long long tlen, const uint32_t *__restrict__ Qp,
+    const uint32_t *__restrict__ Qm, long long qlen, const int4 *__restrict__ anchors,
+    int ntasks, YdParams prm, YdHalf *__restrict__ out) {
+    extern __shared__ int yd_smem[];
+    __shared__ int lut[16];
+    if (threadIdx.x < 16) lut[threadIdx.x] = prm.scores[threadIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int task = blockIdx.x * YD_WARPS + wib;
+    if (task >= ntasks) return;  // whole warp
+    const int band = prm.band;
+    int *wbuf = yd_smem + wib * 9 * band;
+    auto slot = [&](int s) {  // H, E, F of one anti-diagonal
+        return YdSlot{wbuf + 3 * s * band, wbuf + (3 * s + 1) * band, wbuf + (3 * s + 2) * band};
+    };
+    const int4 a = anchors[task >> 1];
+    const int dir = (task & 1) ? -1 : 1;
+    const uint32_t *Q = a.x ? Qm : Qp;
+    const long long t0 = a.y, q0 = a.z;
+    const long long TL = dir > 0 ? tlen - t0 : t0, QL = dir > 0 ? qlen - q0 : q0;
+    const int go = prm.gap_open, ge = prm.gap_extend, Y = prm.ydrop;
+    // anti-diagonal 0: the origin in slot 1 (d - 1); slot 2 (d - 2) empty
+    int s0 = 0, s1 = 1, s2 = 2;
+    if (lane == 0) {
+        slot(s1).H[0] = 0;
+        slot(s1).E[0] = YD_NEG;
+        slot(s1).F[0] = YD_NEG;
+    }
+    __syncwarp();
+    long long lo1 = 0, hi1 = 0, L1 = 0, R1 = 0, lo2 = 1, hi2 = 0, L2 = 1, R2 = 0;
+    long long best = 0, cells = 0;
+    int bi = 0, bj = 0;
+    uint32_t status = 0;
+    for (long long d = 1;; d++) {
+        if (L1 > R1 && L2 > R2) break;
+        long long clo, chi;
+        if (L1 <= R1 && L2 <= R2) {
+            clo = min(L1, L2 + 1);
+            chi = max(R1 + 1, R2 + 1);
+        } else if (L1 <= R1) {
+            clo = L1;
+            chi = R1 + 1;
+        } else {
+            clo = L2 + 1;
+            chi = R2 + 1;
+        }
+        clo = max(clo, max(0LL, d - QL));
+        chi = min(min(chi, TL), d);
+        chi = min(chi, clo + band - 1);
+        long long L0 = 1, R0 = 0, dbest = YD_NEG, dbi = 0;
+        const YdSlot c0 = slot(s0), c1 = slot(s1), c2 = slot(s2);
+        for (long long base = clo; base <= chi; base += 32) {
+            const long long i = base + lane, j = d - i;
+            const bool in = i <= chi;
+            int h = YD_NEG, e = YD_NEG, f = YD_NEG;
+            if (in) {
+                int dg = YD_NEG;
+                if (i >= 1 && j >= 1 && i - 1 >= lo2 && i - 1 <= hi2) {
+                    const int hp = c2.H[i - 1 - lo2];
+                    if (hp > YD_NEG) dg = hp + lut[yd_base(T, t0, dir, i) * 4 + yd_base(Q, q0, dir, j)];
+                }
+                if (j >= 1 && i >= lo1 && i <= hi1) {
+                    const int hp = c1.H[i - lo1];
+                    if (hp > YD_NEG) e = max(c1.E[i - lo1] - ge, hp - go - ge);
+                }
+                if (i >= 1 && i - 1 >= lo1 && i - 1 <= hi1) {
+                    const int hp = c1.H[i - 1 - lo1];
+                    if (hp > YD_NEG) f = max(c1.F[i - 1 - lo1] - ge, hp - go - ge);
+                }
+                h = max(dg, max(e, f));
+                if (h <= YD_NEG || (long long)h < best - Y) h = e = f = YD_NEG;
+                c0.H[i - clo] = h;
+                c0.E[i - clo] = e;
+                c0.F[i - clo] = f;
+            }
+            const bool live = h > YD_NEG;
+            const unsigned lm = __ballot_sync(0xffffffffu, live);
+            if (lm) {
+                if (L0 > R0) L0 = base + __ffs(lm) - 1;
+                R0 = base + 31 - __clz(lm);
+                const int m = __reduce_max_sync(0xffffffffu, live ? h : YD_NEG);
+                if (m > dbest) {
+                    dbest = m;
+                    dbi = base + __ffs(__ballot_sync(0xffffffffu, live && h == m)) - 1;
+                }
+            }
+        }
+        if (clo <= chi) cells += chi - clo + 1;
+        __syncwarp();  // this anti-diagonal's cells are written before the next reads them
+        if (dbest > best) {
+            best = dbest;
+            bi = (int)dbi;
+            bj = (int)(d - dbi);
+            if (best > YD_LIMIT) status |= ST_SCORE_OVERFLOW;
+        }
+        const int sfree = s2;
+        s2 = s1;
+        s1 = s0;
+        s0 = sfree;
+        lo2 = lo1;
+        hi2 = hi1;
+        L2 = L1;
+        R2 = R1;
+        lo1 = clo;
+        hi1 = chi;
+        L1 = L0;
+        R1 = R0;
+        if (clo > chi) {
+            lo1 = 1;
+            hi1 = 0;
+        }
+    }
+    if (lane == 0) {
+        YdHalf r;
+        r.best = (int)best;
+        r.bi = bi;
+        r.bj = bj;
+        r.status = status;
+        r.cells = cells;
+        out[task] = r;
+    }
+}
+
+}  // namespace
+
+size_t ydrop_smem_bytes(int band) { return (size_t)YD_WARPS * 9 * band * sizeof(int); }
+
+cudaError_t launch_ydrop(const uint32_t *T, long long tlen, const uint32_t *Qp,
+                         const uint32_t *Qm, long long qlen, const int4 *anchors, int nanchors,
+                         const YdParams &prm, YdHalf *out, cudaStream_t st) {
+    if (nanchors <= 0) return cudaSuccess;
+    const size_t smem = ydrop_smem_bytes(prm.band);
+    static std::atomic<unsigned long long> attr;
+    cudaError_t e = once_per_device(attr, [] {
+        return cudaFuncSetAttribute(ydrop_half_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)ydrop_smem_bytes(YD_MAX_BAND));
+    });
+    if (e != cudaSuccess) return e;
+    const int ntasks = 2 * nanchors;
+    const unsigned grid = (unsigned)((ntasks + YD_WARPS - 1) / YD_WARPS);
+    g_launches++;
+    ydrop_half_kernel<<<grid, YD_WARPS * 32, smem, st>>>(T, tlen, Qp, Qm, qlen, anchors, ntasks,
+                                                         prm, out);
+    return cudaGetLastError();
+}
+
+}  // namespace sfe

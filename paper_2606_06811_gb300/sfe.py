@@ -70,6 +70,25 @@ class Stats(C.Structure):
         return d
 
 
+class YdropParams(C.Structure):
+    _fields_ = [("scores", C.c_int32 * 16), ("gap_open", C.c_int32), ("gap_extend", C.c_int32),
+                ("ydrop", C.c_int32), ("gapped_thresh", C.c_int32), ("band", C.c_int32),
+                ("input_codes", C.c_int32), ("batch", C.c_int64)]
+
+
+class YdropStats(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("anchors", "skipped", "extended", "cells", "shadow",
+                                          "shadow_cells", "committed", "batches")] + \
+               [("device_ms", C.c_double), ("total_ms", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: (float if k.endswith("_ms") else int)(getattr(self, k))
+                for k, _ in self._fields_}
+
+
+GALIGN_DTYPE = np.dtype([("strand", "<i4"), ("tstart", "<i4"), ("tend", "<i4"),
+                         ("qstart", "<i4"), ("qend", "<i4"), ("score", "<i4")])
+
 _lib = None
 
 
@@ -91,6 +110,9 @@ def lib() -> C.CDLL:
         L.sfe_ctx_set_stream.argtypes = [vp, vp]
         L.sfe_ctx_fail_next_allocs.argtypes = [vp, i32]
         L.sfe_ctx_set_walk.argtypes = [vp, C.POINTER(Params)]
+        L.sfe_ydrop_params_default.argtypes = [C.POINTER(YdropParams)]
+        L.sfe_gapped_extend.argtypes = [vp, vp, i64, vp, i64, vp, i64, C.POINTER(YdropParams), vp,
+                                        i64, C.POINTER(i64), C.POINTER(YdropStats)]
         L.sfe_test_radix_sort.argtypes = [vp, vp, i64, i32, i32, i32]
         L.sfe_test_radix_sort.restype = C.c_int
         L.sfe_ctx_fail_next_allocs.restype = C.c_int
@@ -140,6 +162,18 @@ def _check(code: int) -> int:
         raise SfeError(code, lib().sfe_last_error().decode(errors="replace") or
                        lib().sfe_strerror(code).decode())
     return code
+
+
+def ydrop_params(**kw) -> YdropParams:
+    """sfe_ydrop_params_default(), then the given fields."""
+    p = YdropParams()
+    _check(lib().sfe_ydrop_params_default(C.byref(p)))
+    for k, v in kw.items():
+        if k == "scores":
+            p.scores[:] = [int(x) for x in np.asarray(v, dtype=np.int64).reshape(16)]
+        else:
+            setattr(p, k, v)
+    return p
 
 
 def default_params(**kw) -> Params:
@@ -204,6 +238,29 @@ class Context:
         ptr, nbytes, keep = _buf(keys)
         _check(lib().sfe_test_radix_sort(self.h, ptr, nbytes // 8, int(lo), int(hi),
                                          int(bool(device_count))))
+
+    def gapped_extend(self, target, query, hsps, params: YdropParams | None = None,
+                      cap: int | None = None):
+        """Gapped Y-drop extension of the HSPs (sfe_gapped_extend): (alignments as numpy
+        GALIGN_DTYPE sorted, stats dict)."""
+        p = params or ydrop_params()
+        tptr, tn, tkeep = _buf(target)
+        qptr, qn, qkeep = _buf(query)
+        if isinstance(hsps, np.ndarray) and hsps.dtype != np.int32:
+            hsps = np.ascontiguousarray(hsps).view(np.int32).reshape(-1)
+        hptr, hn, hkeep = _buf(hsps)
+        n = C.c_int64(0)
+        st = YdropStats()
+        cap = 1 << 16 if cap is None else int(cap)
+        while True:
+            buf = np.zeros(max(cap, 1), dtype=GALIGN_DTYPE)
+            code = lib().sfe_gapped_extend(self.h, tptr, tn, qptr, qn, hptr, hn // 20, C.byref(p),
+                                           buf.ctypes.data, cap, C.byref(n), C.byref(st))
+            if code == EOVERFLOW and n.value > cap:
+                cap = int(n.value)
+                continue
+            _check(code)
+            return buf[: n.value], st.as_dict()
 
     def set_walk(self, params: Params | None) -> None:
         """Walk settings for later ungapped_xdrop calls (sfe_ctx_set_walk); None: defaults."""

@@ -92,14 +92,15 @@ def _c_layout(struct: str, fields: list[str], tmp) -> dict:
     return {k: int(v) for k, v in (l.split() for l in out if l)}
 
 
-@pytest.mark.parametrize("name", ["Params", "Stats"])
+@pytest.mark.parametrize("name", ["Params", "Stats", "YdropParams", "YdropStats"])
 def test_ctypes_mirrors_match_the_c_layout(name, tmp_path):
     import shutil
     if not shutil.which("gcc"):
         pytest.skip("no C compiler")
     from paper_2606_06811_gb300 import sfe
     cls = getattr(sfe, name)
-    struct = {"Params": "sfe_params", "Stats": "sfe_stats"}[name]
+    struct = {"Params": "sfe_params", "Stats": "sfe_stats", "YdropParams": "sfe_ydrop_params",
+              "YdropStats": "sfe_ydrop_stats"}[name]
     fields = [f for f, _ in cls._fields_]
     lay = _c_layout(struct, fields, tmp_path)
     assert lay["size"] == ctypes.sizeof(cls)
