@@ -560,6 +560,8 @@ def run_sfe(a, rank, world, local):
         torch.cuda.synchronize()
         line["seeds"] = run_seed_sweep(a, ctx, T, Q, pair, out, step)
         line["speculative_window"] = run_spec_study(a, ctx, T, Q, pair)
+        hs_plain, _ = ctx.run(T, Q, pkg.default_params(), out=out)
+        line["gapped"] = run_gapped_study(a, ctx, T, Q, pair, hs_plain.clone())
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_line(pair, a.cpu_seconds)
     ctx.close()
@@ -570,6 +572,8 @@ def run_sfe(a, rank, world, local):
         sub = argparse.Namespace(**vars(a))
         sub.steps, sub.warmup = a.sub_steps, max(3, a.sub_warmup)
         line["batch_pairs"] = run_batch_bench(sub, rank, world, local, emit=False)
+        torch.cuda.empty_cache()
+        line["ydrop_filter"] = run_ydrop_filter_study(sub, local)
         torch.cuda.empty_cache()
         sub.seed = 5
         line["large_pair_100mb"] = run_large(sub, local)
@@ -756,6 +760,113 @@ def run_seed_sweep(a, ctx, T, Q, pair, out, step_fn) -> list:
 
 
 SPEC_WINDOWS = [1, 2, 4, 8, 16, 32]
+GAPPED_BATCHES = [64, 1024, 16384, 0]
+
+
+def gapped_recovery(pair, A) -> dict:
+    """Planted blocks covered by gapped alignments (boxes): on the block's
+    strand, overlapping its target range, with the box's start or end diagonal
+    within 50 + 3% of the block's length of the block's diagonal."""
+    total, covered, found = 0, 0, 0
+    for b in pair.blocks:
+        strand = 1 if b.rc else 0
+        qb = (pair.qlen - b.qstart - b.qlen) if b.rc else b.qstart
+        d0, tol = b.tstart - qb, 50 + 0.03 * b.tlen
+        m = ((A["strand"] == strand) & (A["tstart"] < b.tstart + b.tlen) & (A["tend"] > b.tstart) &
+             ((np.abs(A["tstart"] - A["qstart"] - d0) <= tol) |
+              (np.abs(A["tend"] - A["qend"] - d0) <= tol)))
+        total += b.tlen
+        if not m.any():
+            continue
+        found += 1
+        iv = sorted(zip(np.maximum(A["tstart"][m], b.tstart).tolist(),
+                        np.minimum(A["tend"][m], b.tstart + b.tlen).tolist()))
+        end, cov = -1, 0
+        for x, y in iv:
+            if y > end:
+                cov += y - max(x, end)
+                end = y
+        covered += cov
+    return {"blocks_found": found / max(1, len(pair.blocks)),
+            "block_bases_covered": covered / max(1, total)}
+
+
+def run_gapped_study(a, ctx, T, Q, pair, hsps) -> dict:
+    """The gapped Y-drop stage after the filter (Algorithm 1 / 3) on the pair's
+    HSPs: time, shadow work and planted-block recovery against the batch size."""
+    import paper_2606_06811_gb300 as pkg
+    rows = []
+    for K in GAPPED_BATCHES:
+        prm = pkg.ydrop_params(batch=K)
+        for _ in range(1):
+            A, st = ctx.gapped_extend(T, Q, hsps, prm)
+        A, st = ctx.gapped_extend(T, Q, hsps, prm)
+        work = st["cells"] + st["shadow_cells"]
+        rows.append({"batch": K if K else "all", "device_ms": round(st["device_ms"], 3),
+                     "total_ms": round(st["total_ms"], 3), "batches": st["batches"],
+                     "extended": st["extended"], "skipped": st["skipped"],
+                     "shadow": st["shadow"], "shadow_fraction": st["shadow_cells"] / max(1, work),
+                     "cells": st["cells"], "committed": st["committed"],
+                     "gcups_device": work / max(1e-9, st["device_ms"] / 1e3) / 1e9,
+                     **gapped_recovery(pair, A)})
+    return {"anchors": int(hsps.shape[0]), "gap_open": 400, "gap_extend": 30, "ydrop": 9400,
+            "gapped_thresh": 3000, "band": 256, "rows": rows,
+            "ungapped_hsps": block_recovery(pair, hsps.cpu().numpy())}
+
+
+def run_ydrop_filter_study(a, local) -> dict:
+    """Y-drop as the filter (Darwin-WGA's idea, the paper's closing section): the
+    seed hits of a 1 Mb pair of the 10 Mb generator extended directly by the 2-D
+    Y-drop (Y = X = 910, threshold 3000) against the X-drop filter followed by the
+    gapped stage (Y = 9400), both through the same kernels."""
+    import torch
+    import paper_2606_06811_gb300 as pkg
+    dev = torch.device("cuda", local)
+    pair, Ta, Qa = make_workload(2, 0.1)
+    T = torch.from_numpy(Ta.copy()).to(dev)
+    Q = torch.from_numpy(Qa.copy()).to(dev)
+    res = {"workload": "plain_pair_10mb at scale 0.1", "tlen": pair.tlen, "qlen": pair.qlen}
+    with pkg.Context(local) as ctx:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ctx.run(T, Q, pkg.default_params())
+        torch.cuda.synchronize()
+        e0.record()
+        hs, st = ctx.run(T, Q, pkg.default_params())
+        e1.record()
+        torch.cuda.synchronize()
+        filt_ms = e0.elapsed_time(e1)
+        H = torch.from_numpy(np.ascontiguousarray(hs).view(np.int32).reshape(-1, 5).copy()).to(dev)
+        A, gst = ctx.gapped_extend(T, Q, H, pkg.ydrop_params())
+        res["xdrop_then_gapped"] = {"filter_ms": round(filt_ms, 3), "hsps": int(H.shape[0]),
+                                    "gapped_device_ms": round(gst["device_ms"], 3),
+                                    "gapped_total_ms": round(gst["total_ms"], 3),
+                                    "alignments": gst["committed"], **gapped_recovery(pair, A)}
+        ix = ctx.index_build(T, pkg.default_params())
+        try:
+            cap = 1 << 24
+            while True:
+                buf = torch.zeros((cap, 3), dtype=torch.int32, device=dev)
+                try:
+                    _, n = ctx.seed_hits(ix, Q, out=buf)
+                    break
+                except pkg.SfeError:
+                    cap *= 2
+        finally:
+            ix.close()
+        anc = torch.zeros((n, 5), dtype=torch.int32, device=dev)
+        anc[:, :3] = buf[:n]
+        anc[:, 3] = 19
+        prm = pkg.ydrop_params(ydrop=910)
+        ctx.gapped_extend(T, Q, anc, prm)
+        A2, yst = ctx.gapped_extend(T, Q, anc, prm)
+        res["ydrop_as_filter"] = {"anchors": int(n), "ydrop": 910,
+                                  "device_ms": round(yst["device_ms"], 3),
+                                  "total_ms": round(yst["total_ms"], 3),
+                                  "extended": yst["extended"], "skipped": yst["skipped"],
+                                  "shadow": yst["shadow"], "cells": yst["cells"],
+                                  "alignments": yst["committed"], **gapped_recovery(pair, A2)}
+    return res
 
 
 def block_diagonal_hits(hits, pair):
