@@ -148,8 +148,10 @@ def test_batch_pairs_4096_full_list(pkg):
     dev = torch.device("cuda", 0)
     T = torch.from_numpy(np.frombuffer(synth.decode(Tc), np.uint8).copy()).to(dev)
     Q = torch.from_numpy(np.frombuffer(synth.decode(Qc), np.uint8).copy()).to(dev)
+    t0 = time.perf_counter()
     R, hits, ext, cells = oracle_pairs(pairs)
-    print(f"batch oracle: {R.shape[0]} HSPs, {hits} hits, {cells} cells")
+    print(f"batch oracle: {oracle.host_cores()} host cores, {time.perf_counter() - t0:.1f} s, "
+          f"{R.shape[0]} HSPs, {hits} hits, {cells} cells")
     with pkg.Context(0) as ctx:
         h, st = ctx.run_batch(T, toff, Q, qoff, pkg.default_params(), cap=1 << 22)
         G = np.ascontiguousarray(h).view(np.int32).reshape(-1, 6)
