@@ -142,47 +142,61 @@ __global__ void __launch_bounds__(BLOCK) bidx_fill(const uint32_t *__restrict__ 
     }
 }
 
-// Hits of query position q (pair P, strand s) against P's tables: counted, or
-// written from `o` on when WRITE. Both buckets' bounds are loaded together,
-// then each bucket is scanned for the entries its table accepts.
-template <bool WRITE>
-__device__ __forceinline__ uint32_t bhits_at(const uint32_t *__restrict__ Qs, long long qg,
-                                             long long q, const PairInfo &P, int pair, int s,
-                                             const SeedPattern &pat, int transition, int dbits,
-                                             long long nb, const uint32_t *__restrict__ off,
-                                             const uint64_t *__restrict__ entries,
-                                             uint64_t *__restrict__ out, unsigned long long o) {
-    const uint32_t k = spaced_key(Qs, qg, pat);
+// Hits of query position q (pair P, strand s) against P's tables. The probe
+// (seed key, the two buckets' bounds, the hit word's fixed part) is made once;
+// the buckets are scanned once to count the entries their tables accept and,
+// for a position with hits, once more to write them from `o` on.
+struct BProbe {
+    uint32_t k, a1, e1, a2, e2, hi_base;
+    long long dq;  // D = t + dq
+};
+
+__device__ __forceinline__ BProbe bprobe(const uint32_t *__restrict__ Qs, long long qg,
+                                         long long q, const PairInfo &P, int pair, int s,
+                                         const SeedPattern &pat, int transition, int dbits,
+                                         long long nb, const uint32_t *__restrict__ off) {
+    BProbe b;
+    b.k = spaced_key(Qs, qg, pat);
     const Split sp = split_of(pat.weight);
-    const long long b1 = P.boff + (table1_key(k, sp) >> (sp.ik - P.bbits));
-    const long long b2 = nb + P.boff + (table2_key(k, sp) >> (sp.ik - P.bbits));
-    const uint32_t a1 = __ldg(off + b1), e1 = __ldg(off + b1 + 1);
-    const uint32_t a2 = transition ? __ldg(off + b2) : 0u;
-    const uint32_t e2 = transition ? __ldg(off + b2 + 1) : 0u;
-    const uint32_t hi_base = ((uint32_t)pair << (dbits + 1)) | ((uint32_t)s << dbits);
-    const long long dq = (long long)P.qlen - pat.span - q;  // D = t + dq
+    const long long b1 = P.boff + (table1_key(b.k, sp) >> (sp.ik - P.bbits));
+    const long long b2 = nb + P.boff + (table2_key(b.k, sp) >> (sp.ik - P.bbits));
+    b.a1 = __ldg(off + b1);
+    b.e1 = __ldg(off + b1 + 1);
+    b.a2 = transition ? __ldg(off + b2) : 0u;
+    b.e2 = transition ? __ldg(off + b2 + 1) : 0u;
+    b.hi_base = ((uint32_t)pair << (dbits + 1)) | ((uint32_t)s << dbits);
+    b.dq = (long long)P.qlen - pat.span - q;
+    return b;
+}
+
+template <bool WRITE>
+__device__ __forceinline__ uint32_t bhits_scan(const BProbe &b, const SeedPattern &pat,
+                                               int transition,
+                                               const uint64_t *__restrict__ entries,
+                                               uint64_t *__restrict__ out, unsigned long long o) {
+    const Split sp = split_of(pat.weight);
     uint32_t c = 0;
-    for (uint32_t j = a1; j < e1; j++) {
+    for (uint32_t j = b.a1; j < b.e1; j++) {
         const uint64_t ent = __ldg(entries + j);
-        const uint32_t x = (uint32_t)(ent >> 32) ^ k;
+        const uint32_t x = (uint32_t)(ent >> 32) ^ b.k;
         // A exact, classes equal, at most one transition in B (none without transitions)
         const bool hit = transition ? ((x & (sp.low | sp.highA)) == 0 && __popc(x & sp.highB) <= 1)
                                     : x == 0;
         if (!hit) continue;
         if (WRITE) {
             const uint32_t t = (uint32_t)ent;
-            out[o + c] = ((uint64_t)(hi_base | (uint32_t)(t + dq)) << 32) | t;
+            out[o + c] = ((uint64_t)(b.hi_base | (uint32_t)(t + b.dq)) << 32) | t;
         }
         c++;
     }
-    for (uint32_t j = a2; j < e2; j++) {
+    for (uint32_t j = b.a2; j < b.e2; j++) {
         const uint64_t ent = __ldg(entries + j);
-        const uint32_t x = (uint32_t)(ent >> 32) ^ k;
+        const uint32_t x = (uint32_t)(ent >> 32) ^ b.k;
         // B exact, classes equal, exactly one transition in A
         if ((x & (sp.low | sp.highB)) != 0 || __popc(x & sp.highA) != 1) continue;
         if (WRITE) {
             const uint32_t t = (uint32_t)ent;
-            out[o + c] = ((uint64_t)(hi_base | (uint32_t)(t + dq)) << 32) | t;
+            out[o + c] = ((uint64_t)(b.hi_base | (uint32_t)(t + b.dq)) << 32) | t;
         }
         c++;
     }
@@ -203,7 +217,10 @@ __device__ __forceinline__ void query_item(const long long *__restrict__ qprefix
 
 // One pass over the query side: each thread counts the hits of its query
 // position, a warp reserves room for all of its lanes' hits with one atomic,
-// and the hits are written there (the probes read again, now from L1/L2).
+// and the hits are written there (the probe's buckets scanned again, now from
+// L1/L2; the probe itself is kept in registers: recomputing it for the few
+// positions with hits ran the whole probe path with one or two lanes of a
+// warp active).
 // Output order is not fixed; the caller sorts the hits by their whole word.
 // Writes stop at `cap`; *total still counts every hit, so the caller can
 // retry with enough room.
@@ -231,9 +248,9 @@ __global__ void __launch_bounds__(BLOCK) bhits_emit(const uint32_t *__restrict__
     for (long long base = q0; base < min(nq, q0 + ITEM); base += BLOCK) {
         const long long q = base + threadIdx.x;
         const bool valid = q < min(nq, q0 + ITEM);
-        const uint32_t c = valid ? bhits_at<false>(Qs, qb + q, q, P, pair, s, pat, transition,
-                                                   dbits, nb, off, entries, nullptr, 0)
-                                 : 0u;
+        BProbe pr{};
+        if (valid) pr = bprobe(Qs, qb + q, q, P, pair, s, pat, transition, dbits, nb, off);
+        const uint32_t c = valid ? bhits_scan<false>(pr, pat, transition, entries, nullptr, 0) : 0u;
         uint32_t incl = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -245,9 +262,7 @@ __global__ void __launch_bounds__(BLOCK) bhits_emit(const uint32_t *__restrict__
         if (lane == 31 && wsum) wbase = atomicAdd(total, (unsigned long long)wsum);
         wbase = __shfl_sync(0xffffffffu, wbase, 31);
         const unsigned long long o = wbase + incl - c;
-        if (c && o + c <= cap)
-            bhits_at<true>(Qs, qb + q, q, P, pair, s, pat, transition, dbits, nb, off, entries, hits,
-                           o);
+        if (c && o + c <= cap) bhits_scan<true>(pr, pat, transition, entries, hits, o);
     }
 }
 
