@@ -8,13 +8,19 @@
 // anti-diagonals (H, E, F of every computed cell) in shared memory slots of at
 // most `band` cells; lanes take the cells of anti-diagonal d in chunks of 32,
 // each reading its diagonal predecessor from d - 2 and its two gap
-// predecessors from d - 1, and warp ballots and reductions give the live range
-// and the best cell. A cell is live while H >= best - Y (best over the earlier
-// anti-diagonals); anti-diagonal d computes every cell from the lowest to the
-// highest i next to a live cell of d - 1 or one diagonal step from a live cell
-// of d - 2, at most `band` of them, and the half stops after two
-// anti-diagonals without a live cell. Same rule, same cells, same result as
-// the oracle's or_ydrop_half.
+// predecessors from d - 1. Each lane keeps its live rows and its first best
+// cell over the chunks, and four warp reductions per anti-diagonal give the
+// live range and the best cell. A cell is live while H >= best - Y (best over
+// the earlier anti-diagonals); anti-diagonal d computes every cell from the
+// lowest to the highest i next to a live cell of d - 1 or one diagonal step
+// from a live cell of d - 2, at most `band` of them, and the half stops after
+// two anti-diagonals without a live cell. Same rule, same cells, same result
+// as the oracle's or_ydrop_half.
+//
+// (Measured and not kept: the two anti-diagonals in registers, lane L holding
+// rows base + 32 r + L of a sliding window and passing row i - 1 to lane L + 1
+// by a rotation shuffle, as in the paper's shuffle-systolic kernel: 124
+// registers and 4 CTAs per SM, 142 against 156 GCUPS.)
 #include <climits>
 
 #include "sfe_internal.cuh"
@@ -87,7 +93,12 @@ __global__ void __launch_bounds__(YD_WARPS * 32) ydrop_half_kernel(
         clo = max(clo, max(0LL, d - QL));
         chi = min(min(chi, TL), d);
         chi = min(chi, clo + band - 1);
-        long long L0 = 1, R0 = 0, dbest = YD_NEG, dbi = 0;
+        // the lane's live rows and first best cell, combined over the warp once
+        // per anti-diagonal: a ballot and a reduction per chunk put a
+        // warp-wide dependency between the chunks (measured on the 10 Mb
+        // pair's anchors, batch 16,384: 126 against 156 GCUPS). Rows and
+        // columns kept in 32 bits measured slower (150 GCUPS).
+        int lfirst = INT_MAX, llast = -1, lbest = YD_NEG, lrow = INT_MAX;
         const YdSlot c0 = slot(s0), c1 = slot(s1), c2 = slot(s2);
         for (long long base = clo; base <= chi; base += 32) {
             const long long i = base + lane, j = d - i;
@@ -113,17 +124,21 @@ __global__ void __launch_bounds__(YD_WARPS * 32) ydrop_half_kernel(
                 c0.E[i - clo] = e;
                 c0.F[i - clo] = f;
             }
-            const bool live = h > YD_NEG;
-            const unsigned lm = __ballot_sync(0xffffffffu, live);
-            if (lm) {
-                if (L0 > R0) L0 = base + __ffs(lm) - 1;
-                R0 = base + 31 - __clz(lm);
-                const int m = __reduce_max_sync(0xffffffffu, live ? h : YD_NEG);
-                if (m > dbest) {
-                    dbest = m;
-                    dbi = base + __ffs(__ballot_sync(0xffffffffu, live && h == m)) - 1;
+            if (h > YD_NEG) {  // chunks in increasing rows: the lane's first best
+                if (lfirst == INT_MAX) lfirst = (int)i;
+                llast = (int)i;
+                if (h > lbest) {
+                    lbest = h;
+                    lrow = (int)i;
                 }
             }
+        }
+        const int dbest = __reduce_max_sync(0xffffffffu, lbest);
+        long long L0 = 1, R0 = 0, dbi = 0;
+        if (dbest > YD_NEG) {
+            dbi = __reduce_min_sync(0xffffffffu, lbest == dbest ? lrow : INT_MAX);
+            L0 = __reduce_min_sync(0xffffffffu, lfirst);
+            R0 = __reduce_max_sync(0xffffffffu, llast);
         }
         if (clo <= chi) cells += chi - clo + 1;
         __syncwarp();  // this anti-diagonal's cells are written before the next reads them
