@@ -37,12 +37,6 @@ struct YdSlot {
     int *H, *E, *F;
 };
 
-__device__ __forceinline__ int yd_base(const uint32_t *__restrict__ S, long long p0, int dir,
-                                       long long i) {
-    // base consumed by step i (1-based) of a half from p0 in direction dir
-    return (int)base_at(S, dir > 0 ? p0 + i - 1 : p0 - i);
-}
-
 __global__ void __launch_bounds__(YD_WARPS * 32) ydrop_half_kernel(
     const uint32_t *__restrict__ T, long long tlen, const uint32_t *__restrict__ Qp,
     const uint32_t *__restrict__ Qm, long long qlen, const int4 *__restrict__ anchors,
@@ -65,6 +59,12 @@ __global__ void __launch_bounds__(YD_WARPS * 32) ydrop_half_kernel(
     const long long t0 = a.y, q0 = a.z;
     const long long TL = dir > 0 ? tlen - t0 : t0, QL = dir > 0 ? qlen - q0 : q0;
     const int go = prm.gap_open, ge = prm.gap_extend, Y = prm.ydrop;
+    // base consumed by step i of the half: word (o >> 4), bits 2 (o & 15) of
+    // Tw / Qw with o = c + ts * i (forward: position p0 + i - 1, backward:
+    // p0 - i; o may be negative going backward, >> and & then floor it)
+    const int ts = dir;
+    const uint32_t *Tw = T + (t0 >> 4), *Qw = Q + (q0 >> 4);
+    const int tc = (int)(t0 & 15) - (dir > 0 ? 1 : 0), qc = (int)(q0 & 15) - (dir > 0 ? 1 : 0);
     // anti-diagonal 0: the origin in slot 1 (d - 1); slot 2 (d - 2) empty
     int s0 = 0, s1 = 1, s2 = 2;
     if (lane == 0) {
@@ -96,40 +96,59 @@ __global__ void __launch_bounds__(YD_WARPS * 32) ydrop_half_kernel(
         // the lane's live rows and first best cell, combined over the warp once
         // per anti-diagonal: a ballot and a reduction per chunk put a
         // warp-wide dependency between the chunks (measured on the 10 Mb
-        // pair's anchors, batch 16,384: 126 against 156 GCUPS). Rows and
-        // columns kept in 32 bits measured slower (150 GCUPS).
+        // pair's anchors, batch 16,384: 126 against 156 GCUPS)
         int lfirst = INT_MAX, llast = -1, lbest = YD_NEG, lrow = INT_MAX;
+        // a cell is dead below this (best - Y, or at most YD_NEG: no predecessor)
+        const int floor_h = (int)max(best - Y, (long long)YD_NEG + 1);
         const YdSlot c0 = slot(s0), c1 = slot(s1), c2 = slot(s2);
-        for (long long base = clo; base <= chi; base += 32) {
-            const long long i = base + lane, j = d - i;
-            const bool in = i <= chi;
+        // 32-bit rows and slot pointers offset by the slots' first rows, set
+        // once per anti-diagonal (13% fewer instructions than 64-bit rows and
+        // offsets per cell: 156 -> 179 GCUPS); an empty range gets a first row
+        // no i reaches
+        const int ilo = (int)clo, ihi = (int)chi;
+        const bool e1 = lo1 > hi1, e2 = lo2 > hi2;
+        const int l1 = e1 ? -(1 << 30) : (int)lo1, w1 = e1 ? 0 : (int)(hi1 - lo1);
+        const int l2 = e2 ? -(1 << 30) : (int)lo2, w2 = e2 ? 0 : (int)(hi2 - lo2);
+        const int *H2m = e2 ? c2.H : c2.H - l2 - 1;  // H2m[i]: H of row i - 1 on d - 2
+        const int *H1o = e1 ? c1.H : c1.H - l1, *E1o = e1 ? c1.E : c1.E - l1;
+        const int *H1m = e1 ? c1.H : c1.H - l1 - 1, *F1m = e1 ? c1.F : c1.F - l1 - 1;
+        int *H0 = c0.H - ilo, *E0 = c0.E - ilo, *F0 = c0.F - ilo;
+        const int d32 = (int)d;  // j = d - i in 32 bits (exact: j < 2^31)
+        for (int b = ilo; b <= ihi; b += 32) {
+            const int i = b + lane, j = d32 - i;
             int h = YD_NEG, e = YD_NEG, f = YD_NEG;
-            if (in) {
+            if (i <= ihi) {
                 int dg = YD_NEG;
-                if (i >= 1 && j >= 1 && i - 1 >= lo2 && i - 1 <= hi2) {
-                    const int hp = c2.H[i - 1 - lo2];
-                    if (hp > YD_NEG) dg = hp + lut[yd_base(T, t0, dir, i) * 4 + yd_base(Q, q0, dir, j)];
+                if (j >= 1 && (unsigned)(i - 1 - l2) <= (unsigned)w2) {
+                    const int hp = H2m[i];
+                    if (hp > YD_NEG) {
+                        const int ot = tc + ts * i, oq = qc + ts * j;
+                        const int bt = (int)((__ldg(Tw + (ot >> 4)) >> ((ot & 15) * 2)) & 3u);
+                        const int bq = (int)((__ldg(Qw + (oq >> 4)) >> ((oq & 15) * 2)) & 3u);
+                        dg = hp + lut[bt * 4 + bq];
+                    }
                 }
-                if (j >= 1 && i >= lo1 && i <= hi1) {
-                    const int hp = c1.H[i - lo1];
-                    if (hp > YD_NEG) e = max(c1.E[i - lo1] - ge, hp - go - ge);
+                const bool in1 = (unsigned)(i - l1) <= (unsigned)w1;
+                if (j >= 1 && in1) {
+                    const int hp = H1o[i];
+                    if (hp > YD_NEG) e = max(E1o[i] - ge, hp - go - ge);
                 }
-                if (i >= 1 && i - 1 >= lo1 && i - 1 <= hi1) {
-                    const int hp = c1.H[i - 1 - lo1];
-                    if (hp > YD_NEG) f = max(c1.F[i - 1 - lo1] - ge, hp - go - ge);
+                if ((unsigned)(i - 1 - l1) <= (unsigned)w1) {
+                    const int hp = H1m[i];
+                    if (hp > YD_NEG) f = max(F1m[i] - ge, hp - go - ge);
                 }
                 h = max(dg, max(e, f));
-                if (h <= YD_NEG || (long long)h < best - Y) h = e = f = YD_NEG;
-                c0.H[i - clo] = h;
-                c0.E[i - clo] = e;
-                c0.F[i - clo] = f;
+                if (h < floor_h) h = e = f = YD_NEG;
+                H0[i] = h;
+                E0[i] = e;
+                F0[i] = f;
             }
             if (h > YD_NEG) {  // chunks in increasing rows: the lane's first best
-                if (lfirst == INT_MAX) lfirst = (int)i;
-                llast = (int)i;
+                if (lfirst == INT_MAX) lfirst = i;
+                llast = i;
                 if (h > lbest) {
                     lbest = h;
-                    lrow = (int)i;
+                    lrow = i;
                 }
             }
         }
