@@ -5,8 +5,10 @@
 // paper's systolic kernel maps one anchor-half per block. The affine-gap
 // dynamic program is evaluated by anti-diagonals d = i + j: cell (i, j) has
 // consumed i target and j query bases. The warp keeps the last two
-// anti-diagonals (H, E, F of every computed cell) in shared memory slots of at
-// most `band` cells; lanes take the cells of anti-diagonal d in chunks of 32,
+// anti-diagonals in shared memory slots of at most `band` cells (H of d - 2,
+// d - 1 and d; E and F only of d - 1 and d: 7 KB per warp at band 256, so 8
+// CTAs of 4 warps fit an SM where 9 slots allowed 6: 182 -> 189 GCUPS); lanes
+// take the cells of anti-diagonal d in chunks of 32,
 // each reading its diagonal predecessor from d - 2 and its two gap
 // predecessors from d - 1. Each lane keeps its live rows and its first best
 // cell over the chunks, and four warp reductions per anti-diagonal give the
@@ -29,7 +31,7 @@ namespace sfe {
 
 namespace {
 
-constexpr int YD_WARPS = 4;        // warps per CTA (each owns 9 * band ints of shared memory)
+constexpr int YD_WARPS = 4;        // warps per CTA (each owns 7 * band ints of shared memory)
 constexpr int YD_NEG = -(1 << 29); // -inf that survives subtracting a gap cost
 constexpr int YD_LIMIT = 1 << 30;  // a score above this flags overflow
 
@@ -49,9 +51,10 @@ __global__ void __launch_bounds__(YD_WARPS * 32) ydrop_half_kernel(
     const int task = blockIdx.x * YD_WARPS + wib;
     if (task >= ntasks) return;  // whole warp
     const int band = prm.band;
-    int *wbuf = yd_smem + wib * 9 * band;
-    auto slot = [&](int s) {  // H, E, F of one anti-diagonal
-        return YdSlot{wbuf + 3 * s * band, wbuf + (3 * s + 1) * band, wbuf + (3 * s + 2) * band};
+    // H of three anti-diagonals (d, d - 1, d - 2), E and F of two (d, d - 1)
+    int *wbuf = yd_smem + wib * 7 * band;
+    auto slot = [&](int s, int k) {
+        return YdSlot{wbuf + s * band, wbuf + (3 + k) * band, wbuf + (5 + k) * band};
     };
     const int4 a = anchors[task >> 1];
     const int dir = (task & 1) ? -1 : 1;
@@ -66,11 +69,11 @@ __global__ void __launch_bounds__(YD_WARPS * 32) ydrop_half_kernel(
     const uint32_t *Tw = T + (t0 >> 4), *Qw = Q + (q0 >> 4);
     const int tc = (int)(t0 & 15) - (dir > 0 ? 1 : 0), qc = (int)(q0 & 15) - (dir > 0 ? 1 : 0);
     // anti-diagonal 0: the origin in slot 1 (d - 1); slot 2 (d - 2) empty
-    int s0 = 0, s1 = 1, s2 = 2;
+    int s0 = 0, s1 = 1, s2 = 2, k0 = 0, k1 = 1;
     if (lane == 0) {
-        slot(s1).H[0] = 0;
-        slot(s1).E[0] = YD_NEG;
-        slot(s1).F[0] = YD_NEG;
+        slot(s1, k1).H[0] = 0;
+        slot(s1, k1).E[0] = YD_NEG;
+        slot(s1, k1).F[0] = YD_NEG;
     }
     __syncwarp();
     long long lo1 = 0, hi1 = 0, L1 = 0, R1 = 0, lo2 = 1, hi2 = 0, L2 = 1, R2 = 0;
@@ -100,7 +103,7 @@ __global__ void __launch_bounds__(YD_WARPS * 32) ydrop_half_kernel(
         int lfirst = INT_MAX, llast = -1, lbest = YD_NEG, lrow = INT_MAX;
         // a cell is dead below this (best - Y, or at most YD_NEG: no predecessor)
         const int floor_h = (int)max(best - Y, (long long)YD_NEG + 1);
-        const YdSlot c0 = slot(s0), c1 = slot(s1), c2 = slot(s2);
+        const YdSlot c0 = slot(s0, k0), c1 = slot(s1, k1), c2 = slot(s2, k0);  // c2: H only
         // 32-bit rows and slot pointers offset by the slots' first rows, set
         // once per anti-diagonal (13% fewer instructions than 64-bit rows and
         // offsets per cell: 156 -> 179 GCUPS); an empty range gets a first row
@@ -171,6 +174,9 @@ __global__ void __launch_bounds__(YD_WARPS * 32) ydrop_half_kernel(
         s2 = s1;
         s1 = s0;
         s0 = sfree;
+        const int kf = k1;
+        k1 = k0;
+        k0 = kf;
         lo2 = lo1;
         hi2 = hi1;
         L2 = L1;
@@ -197,7 +203,7 @@ __global__ void __launch_bounds__(YD_WARPS * 32) ydrop_half_kernel(
 
 }  // namespace
 
-size_t ydrop_smem_bytes(int band) { return (size_t)YD_WARPS * 9 * band * sizeof(int); }
+size_t ydrop_smem_bytes(int band) { return (size_t)YD_WARPS * 7 * band * sizeof(int); }
 
 cudaError_t launch_ydrop(const uint32_t *T, long long tlen, const uint32_t *Qp,
                          const uint32_t *Qm, long long qlen, const int4 *anchors, int nanchors,
