@@ -1663,7 +1663,9 @@ int sfe_gapped_extend(sfe_ctx *c, const uint8_t *target, int64_t tlen, const uin
     TRY(ensure_t(c, SL_YHALF, (size_t)std::max(1LL, 2 * K), &dhalf));
     std::vector<int4> ban;
     std::vector<int> bidx;
-    std::vector<YdHalf> half;
+    std::vector<YdHalf> half, hlaunch;
+    std::vector<int4> blaunch;
+    std::vector<int> lorder;
     ban.reserve((size_t)K);
     bidx.reserve((size_t)K);
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -1692,18 +1694,34 @@ int sfe_gapped_extend(sfe_ctx *c, const uint8_t *target, int64_t tlen, const uin
         }
         if (ban.empty()) break;
         st.batches++;
-        // phase 2: every anchor of the batch, both halves, on the GPU
+        // phase 2: every anchor of the batch, both halves, on the GPU. The
+        // warps start in launch order, so the anchors of the longest ungapped
+        // HSPs (those in long homologous regions, whose extensions run far)
+        // go first and a long extension does not start at the end of the
+        // batch; the results come back in the batch's order for the commit.
         const int nb = (int)ban.size();
         half.resize(2 * (size_t)nb);
-        cudaError_t e = cudaMemcpyAsync(dan, ban.data(), nb * sizeof(int4),
+        lorder.resize((size_t)nb);
+        for (int b = 0; b < nb; b++) lorder[b] = b;
+        std::stable_sort(lorder.begin(), lorder.end(),
+                         [&](int x, int y) { return H[bidx[x]].len > H[bidx[y]].len; });
+        blaunch.resize((size_t)nb);
+        for (int k = 0; k < nb; k++) blaunch[k] = ban[lorder[k]];
+        hlaunch.resize(2 * (size_t)nb);
+        cudaError_t e = cudaMemcpyAsync(dan, blaunch.data(), nb * sizeof(int4),
                                         cudaMemcpyHostToDevice, c->st);
         if (e == cudaSuccess) e = cudaEventRecord(ev[0], c->st);
         if (e == cudaSuccess) e = launch_ydrop(Tp, tlen, Qp, Qm, qlen, dan, nb, yp, dhalf, c->st);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->st);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(half.data(), dhalf, 2 * (size_t)nb * sizeof(YdHalf),
+            e = cudaMemcpyAsync(hlaunch.data(), dhalf, 2 * (size_t)nb * sizeof(YdHalf),
                                 cudaMemcpyDeviceToHost, c->st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+        if (e == cudaSuccess)
+            for (int k = 0; k < nb; k++) {
+                half[2 * (size_t)lorder[k]] = hlaunch[2 * (size_t)k];
+                half[2 * (size_t)lorder[k] + 1] = hlaunch[2 * (size_t)k + 1];
+            }
         float ms = 0.f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
         if (e != cudaSuccess) {
