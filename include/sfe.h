@@ -170,8 +170,7 @@ typedef struct {
                                    covered at once (32 / spec_window lanes each) and commits
                                    them in t order; hits an earlier commit covers are skipped
                                    and their work is counted in stats.shadow_cells. Same output
-                                   as the other modes; one pair or hit list at a time (not
-                                   sfe_run_batch) */
+                                   as the other modes, for a pair, a hit list or a batch */
 
 /* Statistics of one call. cells is the work measure of the method: seed span
  * plus the bases scored on both sides, summed over hits that were extended. */

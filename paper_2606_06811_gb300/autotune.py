@@ -1,10 +1,12 @@
 """Autotuner of the walk's schedule parameters.
 
 The walk of the filter stage has parameters that change its speed but never
-its output: the walk mode (two launches with fixed hit ranges, or one
-persistent launch fed by a device work counter), the lane cap (bases a lane
-scores on one side before it hands the diagonal to a warp), the hits per
-chunk of the persistent walk and the chunk order. `tune` times every
+its output: the walk mode (two launches with fixed hit ranges, one
+persistent launch fed by a device work counter, or the speculative window
+walk), the lane cap (bases a lane scores on one side before it hands the
+diagonal to a warp), the hits per chunk of the persistent walk and the chunk
+order (the diagonal-bin schedule), and the lanes per hit of the speculative
+walk (32 / spec_window: one warp, a group or one lane per hit). `tune` times every
 candidate of a search space on the caller's own workload with CUDA events,
 checks that every candidate returns the same HSP list, byte for byte, and
 keeps the fastest. Results are cached in a JSON file keyed by the GPU, the
@@ -27,10 +29,12 @@ from . import sfe
 
 # name -> candidate values; entries that make no sense together are skipped
 DEFAULT_SPACE = {
-    "walk_mode": [sfe.WALK_TWO_LAUNCHES, sfe.WALK_PERSISTENT],
+    "walk_mode": [sfe.WALK_TWO_LAUNCHES, sfe.WALK_PERSISTENT, sfe.WALK_SPECULATIVE],
     "lane_cap": [64, 128, 256],
     "walk_chunk": [32, 128],
     "walk_schedule": [sfe.SCHED_NATURAL, sfe.SCHED_LARGEST_FIRST],
+    # lanes per hit of the speculative walk: 32 / spec_window
+    "spec_window": [4, 1, 32],
 }
 
 
@@ -49,16 +53,28 @@ def _library_id() -> str:
 def candidates(space: dict) -> list[dict]:
     keys = list(space)
     out = []
+    def first(c, k):  # the parameter takes only the space's first value
+        return k not in c or c[k] == space[k][0]
+
     for vals in itertools.product(*(space[k] for k in keys)):
         c = dict(zip(keys, vals))
-        persistent = c.get("walk_mode", sfe.WALK_TWO_LAUNCHES) == sfe.WALK_PERSISTENT
-        if not persistent:
-            # chunks and their order belong to the persistent walk only
+        mode = c.get("walk_mode", sfe.WALK_TWO_LAUNCHES)
+        if mode != sfe.WALK_PERSISTENT:
+            # chunk sizes and their order belong to the persistent walk only
             if c.get("walk_schedule", sfe.SCHED_NATURAL) != sfe.SCHED_NATURAL:
                 continue
-            if "walk_chunk" in c and c["walk_chunk"] != space["walk_chunk"][0]:
+            if not first(c, "walk_chunk"):
                 continue
             c.pop("walk_chunk", None)
+        if mode == sfe.WALK_SPECULATIVE:
+            # lanes per hit come from the window; no lane tier, no hand-off
+            if not first(c, "lane_cap"):
+                continue
+            c.pop("lane_cap", None)
+        elif not first(c, "spec_window"):
+            continue
+        else:
+            c.pop("spec_window", None)
         out.append(c)
     return out
 

@@ -509,7 +509,6 @@ int walk_tiers(sfe_ctx *c, const uint64_t *hits, long long n, WalkParams &wp, ui
     wp.queue_len = &sm->queue_len;
     CK(cudaMemsetAsync(&sm->queue_len, 0, 4, c->st));
     if (p->walk_mode == SFE_WALK_SPECULATIVE) {
-        if (wp.pairs) return fail(SFE_EINVAL, "SFE_WALK_SPECULATIVE walks one pair at a time");
         Span sp(c, SFE_STAGE_WALK_WARPS);
         wp.work_next = &sm->work_next;
         wp.chunk = p->walk_chunk > 0 ? (uint32_t)p->walk_chunk : walk_auto_chunk(n);

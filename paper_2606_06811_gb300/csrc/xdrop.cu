@@ -753,7 +753,7 @@ __device__ __forceinline__ Side group_side(const uint32_t *__restrict__ T,
     return {best, blen, scored};
 }
 
-template <int W>
+template <int W, bool BATCH>
 __global__ void __launch_bounds__(W_BLOCK) walk_spec_kernel(const uint64_t *__restrict__ hits,
                                                             uint32_t n, WalkParams wp) {
     constexpr int K = 32 / W;
@@ -762,16 +762,20 @@ __global__ void __launch_bounds__(W_BLOCK) walk_spec_kernel(const uint64_t *__re
     __syncthreads();
     const int lane = threadIdx.x & 31, g = lane / W, gl = lane & (W - 1);
     const int span = wp.span, X = wp.xdrop;
-    const long long qoff = wp.qlen - span;
     unsigned long long ext = 0, cells = 0, shadow = 0, tasks = 0;
     uint32_t status = 0;
+    uint32_t nchunks = wp.nchunks;
+    if (wp.nd) {  // the hit count lives on the device (n is the buffer's size)
+        n = (uint32_t)min((unsigned long long)n, *wp.nd);
+        nchunks = (n + wp.chunk - 1) / wp.chunk;
+    }
     SegCtx c;
-    seg_ctx<false>(wp, 0u, c);
+    seg_ctx<BATCH>(wp, 0u, c);
     while (true) {
         uint32_t w = 0;
         if (lane == 0) w = atomicAdd(wp.work_next, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
-        if (w >= wp.nchunks) break;
+        if (w >= nchunks) break;
         uint32_t i = w * wp.chunk;
         const uint32_t end = (uint32_t)min((long long)n, (long long)i + wp.chunk);
         // a diagonal that started before this chunk belongs to the previous one
@@ -780,7 +784,9 @@ __global__ void __launch_bounds__(W_BLOCK) walk_spec_kernel(const uint64_t *__re
         while (i < end) {
             const uint32_t D = diag_of(hits[i]);
             const uint32_t se = segment_end(hits, i, n, D);
-            const long long Dl = (long long)(D & 0x7FFFFFFFu);
+            if (BATCH) seg_ctx<BATCH>(wp, D, c);  // the diagonal's pair and strand
+            const long long Dl = BATCH ? c.D : (long long)(D & 0x7FFFFFFFu);
+            const long long qoff = c.qoff;
             int E = wp.Ecarry ? wp.Ecarry[Dl] : INT_MIN;
             tasks++;
             uint32_t j = i;
@@ -795,15 +801,15 @@ __global__ void __launch_bounds__(W_BLOCK) walk_spec_kernel(const uint64_t *__re
                 int s = 0;
                 if (active)
                     for (int k = gl; k < span; k += W)
-                        s += lut[base_at(wp.T, t + k) * 4u + base_at(c.Q, q + k)];
+                        s += lut[base_at(wp.T, c.tb + t + k) * 4u + base_at(c.Q, c.qb + q + k)];
                 s = grp_incl_sum<W>(s, gl);
                 const int s0 = __shfl_sync(0xffffffffu, s, (lane & ~(W - 1)) + W - 1);
-                const int ravail = active ? (int)min(wp.tlen - t - span, wp.qlen - q - span) : 0;
+                const int ravail = active ? (int)min(c.tlen - t - span, c.qlen - q - span) : 0;
                 const int lavail = active ? (int)min(t, q) : 0;
-                const Side r = group_side<W>(wp.T, c.Q, t + span, q + span, +1, ravail, active, X,
-                                             lut, lane, status);
-                const Side l = group_side<W>(wp.T, c.Q, t - 1, q - 1, -1, lavail, active, X, lut,
-                                             lane, status);
+                const Side r = group_side<W>(wp.T, c.Q, c.tb + t + span, c.qb + q + span, +1,
+                                             ravail, active, X, lut, lane, status);
+                const Side l = group_side<W>(wp.T, c.Q, c.tb + t - 1, c.qb + q - 1, -1, lavail,
+                                             active, X, lut, lane, status);
                 // commit in t order
                 for (int gg = 0; gg < K && j + gg < se; gg++) {
                     const int src = gg * W;
@@ -827,7 +833,7 @@ __global__ void __launch_bounds__(W_BLOCK) walk_spec_kernel(const uint64_t *__re
                     cells += work;
                     if (lane == 0) log_ext(wp, c, tg, qg, rsc, lsc);
                     const bool pass = score >= wp.thresh;
-                    if (pass && lane == 0) emit<false>(wp, c, tg, qg, lbl, rbl, score, status);
+                    if (pass && lane == 0) emit<BATCH>(wp, c, tg, qg, lbl, rbl, score, status);
                     if (pass || !(wp.flags & SFE_SKIP_PASSING_ONLY)) E = (int)(tg + span + rbl);
                 }
                 j += K;
@@ -1007,24 +1013,32 @@ cudaError_t launch_walk_persistent(const uint64_t *hits, long long n, WalkParams
     return launch_persistent_t<false, true>(hits, n, wp, st);
 }
 
+template <bool BATCH>
+static cudaError_t launch_spec(const uint64_t *hits, uint32_t n, const WalkParams &wp, int window,
+                               unsigned grid, cudaStream_t st) {
+    switch (window) {
+    case 1: walk_spec_kernel<32, BATCH><<<grid, W_BLOCK, 0, st>>>(hits, n, wp); break;
+    case 2: walk_spec_kernel<16, BATCH><<<grid, W_BLOCK, 0, st>>>(hits, n, wp); break;
+    case 4: walk_spec_kernel<8, BATCH><<<grid, W_BLOCK, 0, st>>>(hits, n, wp); break;
+    case 8: walk_spec_kernel<4, BATCH><<<grid, W_BLOCK, 0, st>>>(hits, n, wp); break;
+    case 16: walk_spec_kernel<2, BATCH><<<grid, W_BLOCK, 0, st>>>(hits, n, wp); break;
+    default: walk_spec_kernel<1, BATCH><<<grid, W_BLOCK, 0, st>>>(hits, n, wp); break;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_walk_speculative(const uint64_t *hits, long long n, WalkParams wp, int window,
                                     cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    if (wp.pairs) return cudaErrorInvalidValue;  // one pair (or one hit list) at a time
     if (wp.chunk == 0) wp.chunk = walk_auto_chunk(n);
     wp.nchunks = (uint32_t)((n + wp.chunk - 1) / wp.chunk);
     const unsigned grid = (unsigned)(4 * sms());
+    if (window != 1 && window != 2 && window != 4 && window != 8 && window != 16 && window != 32)
+        return cudaErrorInvalidValue;
     g_launches++;
-    switch (window) {
-    case 1: walk_spec_kernel<32><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, wp); break;
-    case 2: walk_spec_kernel<16><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, wp); break;
-    case 4: walk_spec_kernel<8><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, wp); break;
-    case 8: walk_spec_kernel<4><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, wp); break;
-    case 16: walk_spec_kernel<2><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, wp); break;
-    case 32: walk_spec_kernel<1><<<grid, W_BLOCK, 0, st>>>(hits, (uint32_t)n, wp); break;
-    default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+    if (wp.pairs)
+        return launch_spec<true>(hits, (uint32_t)n, wp, window, grid, st);
+    return launch_spec<false>(hits, (uint32_t)n, wp, window, grid, st);
 }
 
 size_t walk_schedule_temp_bytes(long long n, uint32_t chunk) {

@@ -71,9 +71,14 @@ def test_autotune_candidates_skip_meaningless_combinations():
     cs = autotune.candidates(autotune.DEFAULT_SPACE)
     two = [c for c in cs if c["walk_mode"] == sfe.WALK_TWO_LAUNCHES]
     per = [c for c in cs if c["walk_mode"] == sfe.WALK_PERSISTENT]
+    spec = [c for c in cs if c["walk_mode"] == sfe.WALK_SPECULATIVE]
     assert len(two) == 3 and all("walk_chunk" not in c for c in two)
-    assert all(c["walk_schedule"] == sfe.SCHED_NATURAL for c in two)
+    assert all(c["walk_schedule"] == sfe.SCHED_NATURAL for c in two + spec)
     assert len(per) == 3 * 2 * 2
+    assert sorted(c["spec_window"] for c in spec) == [1, 4, 32]
+    assert all("lane_cap" not in c and "walk_chunk" not in c for c in spec)
+    assert all("spec_window" not in c for c in two + per)
+    assert len(cs) == len(two) + len(per) + len(spec)
     assert len({tuple(sorted(c.items())) for c in cs}) == len(cs)
 
 

@@ -46,7 +46,7 @@ def check(P, pairs, **kw):
     names = {"hsp_thresh": "thresh", "seed_pattern": "pattern"}
     okw = {names.get(k, k): v for k, v in kw.items()
            if k not in ("lane_cap", "lanes_per_sm", "tile_hits", "walk_mode", "walk_chunk",
-                        "walk_schedule")}
+                        "walk_schedule", "spec_window")}
     H, hits, ext, cells = oracle_batch(pairs, **okw)
     G, st = gpu_batch(P, pairs, **kw)
     assert G.shape == H.shape and np.array_equal(G, H)
@@ -81,6 +81,14 @@ def test_batch_single_strand_and_lane_cap(pkg):
 def test_batch_walk_modes(pkg, mode, sched, chunk):
     pairs = synth.batch_pairs(seed=6, n_pairs=64, len_lo=1000, len_hi=30_000)
     check(pkg, pairs, walk_mode=mode, walk_schedule=sched, walk_chunk=chunk, lane_cap=32)
+
+
+@pytest.mark.parametrize("window", [1, 4, 32])
+def test_batch_speculative_window(pkg, window):
+    """The speculative window walk (32 / window lanes per hit) over a batch:
+    every pair's HSPs as the oracle's, chunks that split pairs included."""
+    pairs = synth.batch_pairs(seed=8, n_pairs=48, len_lo=1000, len_hi=20_000)
+    check(pkg, pairs, walk_mode=pkg.WALK_SPECULATIVE, spec_window=window, walk_chunk=5)
 
 
 def _variant(pairs):

@@ -369,13 +369,7 @@ def test_speculative_window_through_the_hit_list_call(pkg, ctx):
     assert_same(got, st, ref)
 
 
-def test_speculative_window_rejects_a_batch_and_bad_windows(pkg, ctx):
-    from synth.workloads import concat_batch
-    pairs = synth.batch_pairs(seed=7, n_pairs=4, len_lo=2000, len_hi=5000)
-    T, toff, Q, qoff = concat_batch(pairs)
-    with pytest.raises(pkg.SfeError):
-        ctx.run_batch(T, toff, Q, qoff, pkg.default_params(input_codes=1,
-                                                           walk_mode=pkg.WALK_SPECULATIVE))
+def test_speculative_window_rejects_bad_windows(pkg, ctx):
     p = synth.tiny_pair(2, length=5_000, n_blocks=2)
     for bad in (3, 64, -1):
         with pytest.raises(pkg.SfeError):
