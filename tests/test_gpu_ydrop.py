@@ -87,6 +87,26 @@ def test_gapped_stage_on_anchors_at_the_sequence_ends(pkg, ctx):
     _ok(got, sts, ref)
 
 
+def test_gapped_stage_with_an_alignment_larger_than_its_grid(pkg, ctx):
+    """A query that copies 80 kb of the target: one alignment box spans more
+    grid cells (1024 x 1024 bases each) than the committed-box index lists per
+    box, so it is kept on the index's short list; every later anchor inside
+    it must still be skipped, and anchors outside it extended."""
+    st = synth.Stream(41, "ybig")
+    T = synth.iid_bases(st.child("T"), 90_000, 0.45)
+    Q = np.concatenate([T[5_000:85_000], synth.iid_bases(st.child("Q"), 6_000, 0.45)])
+    H = np.zeros(5, dtype=oracle.HSP_DTYPE)
+    H[0] = (0, 40_000, 35_000, 2_000, 190_000)  # on the copied diagonal, highest score first
+    H[1] = (0, 10_000, 5_000, 500, 50_000)      # inside the copy's box: skipped
+    H[2] = (0, 70_000, 65_000, 800, 80_000)     # inside as well
+    H[3] = (1, 1_000, 2_000, 40, 3_500)         # other strand: extended
+    H[4] = (0, 88_000, 83_000, 40, 3_000)       # past the copy's end on the target
+    for batch in (1, 2, 0):
+        got, sts, ref = _run(pkg, ctx, T, Q, H, batch)
+        _ok(got, sts, ref)
+    assert ref.stats["skipped"] + ref.stats["shadow"] >= 2
+
+
 def test_gapped_stage_device_buffers_and_small_capacity(pkg, ctx):
     import torch
     p = synth.tiny_pair(3, length=100_000, n_blocks=20)
