@@ -201,6 +201,173 @@ __global__ void __launch_bounds__(YD_WARPS * 32) ydrop_half_kernel(
     }
 }
 
+// The same extension with a CTA of YC_WARPS warps per anchor half, for
+// batches too small to fill the GPU with one warp per half (the paper's
+// Section 8: cooperative warps per anchor half raise the occupancy of small
+// speculative batches). Warp w computes rows clo + 32 w .. clo + 32 w + 31 of
+// each anti-diagonal (the band is at most YC_WARPS chunks); each warp reduces
+// its live rows and first best cell, one barrier per anti-diagonal publishes
+// the slots and the partial results, and every thread combines the partials
+// in warp order (lower rows first), so all warps hold the same state. Same
+// cells, same result as the warp kernel.
+constexpr int YC_WARPS = YD_MAX_BAND / 32;
+constexpr int YC_MAX_TASKS_PER_SM = 8;  // CTAs of YC_WARPS warps an SM holds (2048 threads)
+
+__global__ void __launch_bounds__(YC_WARPS * 32) ydrop_coop_kernel(
+    const uint32_t *__restrict__ T, long long tlen, const uint32_t *__restrict__ Qp,
+    const uint32_t *__restrict__ Qm, long long qlen, const int4 *__restrict__ anchors,
+    YdParams prm, YdHalf *__restrict__ out) {
+    __shared__ int lut[16];
+    __shared__ int slots[7 * YD_MAX_BAND];
+    __shared__ int part[2][YC_WARPS][4];  // per warp: best, its first row, first / last live row
+    if (threadIdx.x < 16) lut[threadIdx.x] = prm.scores[threadIdx.x];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int task = blockIdx.x;  // one anchor half per CTA: the grid is the task count
+    const int band = prm.band;
+    auto slot = [&](int s, int k) {
+        return YdSlot{slots + s * band, slots + (3 + k) * band, slots + (5 + k) * band};
+    };
+    const int4 a = anchors[task >> 1];
+    const int dir = (task & 1) ? -1 : 1;
+    const uint32_t *Q = a.x ? Qm : Qp;
+    const long long t0 = a.y, q0 = a.z;
+    const long long TL = dir > 0 ? tlen - t0 : t0, QL = dir > 0 ? qlen - q0 : q0;
+    const int go = prm.gap_open, ge = prm.gap_extend, Y = prm.ydrop;
+    const int ts = dir;
+    const uint32_t *Tw = T + (t0 >> 4), *Qw = Q + (q0 >> 4);
+    const int tc = (int)(t0 & 15) - (dir > 0 ? 1 : 0), qc = (int)(q0 & 15) - (dir > 0 ? 1 : 0);
+    int s0 = 0, s1 = 1, s2 = 2, k0 = 0, k1 = 1;
+    if (threadIdx.x == 0) {
+        slot(s1, k1).H[0] = 0;
+        slot(s1, k1).E[0] = YD_NEG;
+        slot(s1, k1).F[0] = YD_NEG;
+    }
+    __syncthreads();
+    long long lo1 = 0, hi1 = 0, L1 = 0, R1 = 0, lo2 = 1, hi2 = 0, L2 = 1, R2 = 0;
+    long long best = 0, cells = 0;
+    int bi = 0, bj = 0, par = 0;
+    uint32_t status = 0;
+    for (long long d = 1;; d++) {
+        if (L1 > R1 && L2 > R2) break;  // the same decision in every thread
+        long long clo, chi;
+        if (L1 <= R1 && L2 <= R2) {
+            clo = min(L1, L2 + 1);
+            chi = max(R1 + 1, R2 + 1);
+        } else if (L1 <= R1) {
+            clo = L1;
+            chi = R1 + 1;
+        } else {
+            clo = L2 + 1;
+            chi = R2 + 1;
+        }
+        clo = max(clo, max(0LL, d - QL));
+        chi = min(min(chi, TL), d);
+        chi = min(chi, clo + band - 1);
+        const int floor_h = (int)max(best - Y, (long long)YD_NEG + 1);
+        const YdSlot c0 = slot(s0, k0), c1 = slot(s1, k1), c2 = slot(s2, k0);
+        const int ilo = (int)clo, ihi = (int)chi;
+        const bool e1 = lo1 > hi1, e2 = lo2 > hi2;
+        const int l1 = e1 ? -(1 << 30) : (int)lo1, w1 = e1 ? 0 : (int)(hi1 - lo1);
+        const int l2 = e2 ? -(1 << 30) : (int)lo2, w2 = e2 ? 0 : (int)(hi2 - lo2);
+        int lfirst = INT_MAX, llast = -1, lbest = YD_NEG, lrow = INT_MAX;
+        {
+            const int i = ilo + 32 * w + lane, j = (int)d - i;
+            if (i <= ihi) {
+                int dg = YD_NEG, e = YD_NEG, f = YD_NEG;
+                if (j >= 1 && (unsigned)(i - 1 - l2) <= (unsigned)w2) {
+                    const int hp = c2.H[i - 1 - l2];
+                    if (hp > YD_NEG) {
+                        const int ot = tc + ts * i, oq = qc + ts * j;
+                        const int bt = (int)((__ldg(Tw + (ot >> 4)) >> ((ot & 15) * 2)) & 3u);
+                        const int bq = (int)((__ldg(Qw + (oq >> 4)) >> ((oq & 15) * 2)) & 3u);
+                        dg = hp + lut[bt * 4 + bq];
+                    }
+                }
+                if (j >= 1 && (unsigned)(i - l1) <= (unsigned)w1) {
+                    const int hp = c1.H[i - l1];
+                    if (hp > YD_NEG) e = max(c1.E[i - l1] - ge, hp - go - ge);
+                }
+                if ((unsigned)(i - 1 - l1) <= (unsigned)w1) {
+                    const int hp = c1.H[i - 1 - l1];
+                    if (hp > YD_NEG) f = max(c1.F[i - 1 - l1] - ge, hp - go - ge);
+                }
+                int h = max(dg, max(e, f));
+                if (h < floor_h) h = e = f = YD_NEG;
+                c0.H[i - ilo] = h;
+                c0.E[i - ilo] = e;
+                c0.F[i - ilo] = f;
+                if (h > YD_NEG) {
+                    lfirst = llast = lrow = i;
+                    lbest = h;
+                }
+            }
+        }
+        const int wb = __reduce_max_sync(0xffffffffu, lbest);
+        const int wr = __reduce_min_sync(0xffffffffu, lbest == wb ? lrow : INT_MAX);
+        const int wf = __reduce_min_sync(0xffffffffu, lfirst);
+        const int wl = __reduce_max_sync(0xffffffffu, llast);
+        if (lane == 0) {
+            part[par][w][0] = wb;
+            part[par][w][1] = wr;
+            part[par][w][2] = wf;
+            part[par][w][3] = wl;
+        }
+        __syncthreads();  // the anti-diagonal's cells and partials are published
+        int dbest = YD_NEG, dbi = 0, L0 = INT_MAX, R0 = -1;
+#pragma unroll
+        for (int k = 0; k < YC_WARPS; k++) {  // warps in increasing rows: the first best
+            const int b = part[par][k][0];
+            if (b > dbest) {
+                dbest = b;
+                dbi = part[par][k][1];
+            }
+            L0 = min(L0, part[par][k][2]);
+            R0 = max(R0, part[par][k][3]);
+        }
+        par ^= 1;  // the next anti-diagonal writes the other partials
+        if (clo <= chi) cells += chi - clo + 1;
+        if (dbest > best) {
+            best = dbest;
+            bi = dbi;
+            bj = (int)(d - dbi);
+            if (best > YD_LIMIT) status |= ST_SCORE_OVERFLOW;
+        }
+        const int sfree = s2;
+        s2 = s1;
+        s1 = s0;
+        s0 = sfree;
+        const int kf = k1;
+        k1 = k0;
+        k0 = kf;
+        lo2 = lo1;
+        hi2 = hi1;
+        L2 = L1;
+        R2 = R1;
+        lo1 = clo;
+        hi1 = chi;
+        if (dbest > YD_NEG) {
+            L1 = L0;
+            R1 = R0;
+        } else {
+            L1 = 1;
+            R1 = 0;
+        }
+        if (clo > chi) {
+            lo1 = 1;
+            hi1 = 0;
+        }
+    }
+    if (threadIdx.x == 0) {
+        YdHalf r;
+        r.best = (int)best;
+        r.bi = bi;
+        r.bj = bj;
+        r.status = status;
+        r.cells = cells;
+        out[task] = r;
+    }
+}
+
 }  // namespace
 
 size_t ydrop_smem_bytes(int band) { return (size_t)YD_WARPS * 7 * band * sizeof(int); }
@@ -217,8 +384,14 @@ cudaError_t launch_ydrop(const uint32_t *T, long long tlen, const uint32_t *Qp,
     });
     if (e != cudaSuccess) return e;
     const int ntasks = 2 * nanchors;
-    const unsigned grid = (unsigned)((ntasks + YD_WARPS - 1) / YD_WARPS);
     g_launches++;
+    if (ntasks <= YC_MAX_TASKS_PER_SM * device_sms()) {
+        // too few halves to fill the GPU a warp each: a CTA per half
+        ydrop_coop_kernel<<<(unsigned)ntasks, YC_WARPS * 32, 0, st>>>(T, tlen, Qp, Qm, qlen,
+                                                                       anchors, prm, out);
+        return cudaGetLastError();
+    }
+    const unsigned grid = (unsigned)((ntasks + YD_WARPS - 1) / YD_WARPS);
     ydrop_half_kernel<<<grid, YD_WARPS * 32, smem, st>>>(T, tlen, Qp, Qm, qlen, anchors, ntasks,
                                                          prm, out);
     return cudaGetLastError();
