@@ -270,7 +270,10 @@ int sfe_ungapped_xdrop(sfe_ctx *ctx, const sfe_index *index, const uint8_t *quer
  * carried across tiles, so the result does not depend on the tiling. Scratch
  * (context-owned, reused by later calls): the index, two hit buffers per
  * tile, and, unless SFE_NO_CELL_PLANES, 4-bit copies of the target and the
- * query strands when they take at most 64 MB.
+ * query strands when they take at most 64 MB. Lengths: each sequence below
+ * 2^31 - 1024 bases and the two together below 2^31 (a diagonal index has 31
+ * bits; the same holds for sfe_seed_hits and sfe_ungapped_xdrop), else
+ * SFE_EINVAL before any GPU work.
  */
 int sfe_run(sfe_ctx *ctx, const uint8_t *target, int64_t tlen, const uint8_t *query, int64_t qlen,
             const sfe_params *params, sfe_hsp *hsps, int64_t cap, int64_t *nhsps,

@@ -260,6 +260,15 @@ int check_len(long long n, const char *what) {
     return SFE_OK;
 }
 
+// A walk packs the diagonal index t - q + (qlen - span) in 31 bits (the hit
+// list's walk layout keeps the strand in the top bit of the word), so a
+// target and a query walked together stay below 2^31 bases.
+int check_pair(long long tlen, long long qlen) {
+    if (tlen + qlen > (long long)INT_MAX)
+        return fail(SFE_EINVAL, "target and query together must be shorter than 2^31 bases");
+    return SFE_OK;
+}
+
 int begin(sfe_ctx *c, int flags = 0) {
     if (!c) return fail(SFE_EINVAL, "context is NULL");
     CK(cudaSetDevice(c->device));
@@ -860,6 +869,7 @@ int sfe_seed_hits(sfe_ctx *c, const sfe_index *ix, const uint8_t *query, int64_t
     if (!ix || !nhits) return fail(SFE_EINVAL, "index or nhits is NULL");
     if (strands < 1 || strands > 3) return fail(SFE_EINVAL, "strands must be 1, 2 or 3");
     TRY(check_len(qlen, "query"));
+    TRY(check_pair(ix->tlen, qlen));
     TRY(begin(c));
     const IndexView v = view_of(ix);
     const void *qdev = nullptr;
@@ -916,6 +926,7 @@ int sfe_ungapped_xdrop(sfe_ctx *c, const sfe_index *ix, const uint8_t *query, in
     if (!ix || !nhsps || !scores) return fail(SFE_EINVAL, "index, scores or nhsps is NULL");
     if (nhits < 0 || nhits >= (1LL << 32)) return fail(SFE_EINVAL, "nhits out of range");
     TRY(check_len(qlen, "query"));
+    TRY(check_pair(ix->tlen, qlen));
     if (!c) return fail(SFE_EINVAL, "context is NULL");
     sfe_params p;
     sfe_params_default(&p);
@@ -996,6 +1007,7 @@ int sfe_run(sfe_ctx *c, const uint8_t *target, int64_t tlen, const uint8_t *quer
     TRY(check_params(params));
     TRY(check_len(tlen, "target"));
     TRY(check_len(qlen, "query"));
+    TRY(check_pair(tlen, qlen));
     SeedPattern pat;
     TRY(parse_pattern(params->seed_pattern, &pat));
     pat.step = params->step > 1 ? params->step : 1;

@@ -369,6 +369,18 @@ def test_speculative_window_through_the_hit_list_call(pkg, ctx):
     assert_same(got, st, ref)
 
 
+def test_a_pair_longer_than_31_bit_diagonals_is_rejected(pkg, ctx):
+    """A target and a query whose lengths add to 2^31 or more would need a
+    32-bit diagonal index: the call refuses them before touching the data."""
+    import ctypes as C
+    lib = pkg.sfe.lib()
+    n = C.c_int64(0)
+    prm = pkg.default_params()
+    tlen, qlen = (1 << 31) - 2048, 4096
+    code = lib.sfe_run(ctx.h, None, tlen, None, qlen, C.byref(prm), None, 0, C.byref(n), None)
+    assert code == -1 and b"2^31" in lib.sfe_last_error()
+
+
 def test_speculative_window_rejects_bad_windows(pkg, ctx):
     p = synth.tiny_pair(2, length=5_000, n_blocks=2)
     for bad in (3, 64, -1):
