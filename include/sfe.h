@@ -473,6 +473,14 @@ int sfe_gapped_extend(sfe_ctx *ctx, const uint8_t *target, int64_t tlen, const u
                       int64_t qlen, const sfe_hsp *hsps, int64_t nhsps,
                       const sfe_ydrop_params *params, sfe_galign *out, int64_t cap,
                       int64_t *nout, sfe_ydrop_stats *stats);
+/* Test hook (host only, needs no GPU; no counterpart in the paper): the
+ * gapped stage's index of committed alignment boxes. Adds the n boxes in
+ * order, then answers for each of the m queries, given as (strand, t, q)
+ * triples, whether a box contains it (same strand, tstart <= t < tend and
+ * qstart <= q < qend): inside[k] = 1 or 0. SFE_EINVAL on NULL arrays with
+ * n or m above 0, or on a negative count. */
+int sfe_test_committed_boxes(const sfe_galign *boxes, int64_t n, const int32_t *queries,
+                             int64_t m, uint8_t *inside);
 
 /*
  * Allocation-free variant of sfe_ungapped_xdrop (the paper has no counterpart:

@@ -1819,6 +1819,18 @@ int sfe_gapped_extend(sfe_ctx *c, const uint8_t *target, int64_t tlen, const uin
     return SFE_OK;
 }
 
+int sfe_test_committed_boxes(const sfe_galign *boxes, int64_t n, const int32_t *queries,
+                             int64_t m, uint8_t *inside) {
+    if (n < 0 || m < 0) return fail(SFE_EINVAL, "negative count");
+    if ((n > 0 && !boxes) || (m > 0 && (!queries || !inside)))
+        return fail(SFE_EINVAL, "boxes, queries or inside is NULL");
+    CommittedBoxes com;
+    for (int64_t k = 0; k < n; k++) com.add(boxes[k]);
+    for (int64_t k = 0; k < m; k++)
+        inside[k] = com.contains(queries[3 * k], queries[3 * k + 1], queries[3 * k + 2]) ? 1 : 0;
+    return SFE_OK;
+}
+
 }  // extern "C"
 
 extern "C" {

@@ -115,6 +115,8 @@ def lib() -> C.CDLL:
                                         i64, C.POINTER(i64), C.POINTER(YdropStats)]
         L.sfe_test_radix_sort.argtypes = [vp, vp, i64, i32, i32, i32]
         L.sfe_test_radix_sort.restype = C.c_int
+        L.sfe_test_committed_boxes.argtypes = [vp, i64, vp, i64, vp]
+        L.sfe_test_committed_boxes.restype = C.c_int
         L.sfe_ctx_fail_next_allocs.restype = C.c_int
         L.sfe_ctx_destroy.argtypes = [vp]
         L.sfe_ctx_destroy.restype = None
@@ -539,6 +541,19 @@ class MlpData:
             self.close()
         except Exception:
             pass
+
+
+def test_committed_boxes(boxes, queries):
+    """Test hook (host only): for each (strand, t, q) row of `queries`, whether
+    one of the committed alignment boxes (rows of GALIGN_DTYPE fields, added in
+    order) contains it, through the gapped stage's own box index."""
+    b = np.ascontiguousarray(boxes, dtype=np.int32).reshape(-1, 6)
+    q = np.ascontiguousarray(queries, dtype=np.int32).reshape(-1, 3)
+    out = np.zeros(q.shape[0], dtype=np.uint8)
+    _check(lib().sfe_test_committed_boxes(b.ctypes.data if b.size else None, b.shape[0],
+                                          q.ctypes.data if q.size else None, q.shape[0],
+                                          out.ctypes.data if out.size else None))
+    return out.astype(bool)
 
 
 def mlp_param_count() -> int:

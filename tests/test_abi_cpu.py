@@ -111,3 +111,39 @@ def test_ctypes_mirrors_match_the_c_layout(name, tmp_path):
     assert lay["size"] == ctypes.sizeof(cls)
     for f in fields:
         assert lay[f] == getattr(cls, f).offset, f
+
+
+def test_committed_box_index_answers_like_a_scan_of_every_box():
+    """The gapped stage's index of committed boxes (a grid of 1024-base cells
+    per strand, with a short list for boxes spanning many cells) against a
+    scan of every box: small, empty, huge and edge-touching boxes on both
+    strands, queries inside, outside and on every box edge."""
+    import numpy as np
+    from paper_2606_06811_gb300 import sfe
+    rng = np.random.default_rng(7)
+    rows = []
+    for _ in range(400):  # small and medium boxes
+        s = int(rng.integers(0, 2))
+        t0, q0 = int(rng.integers(0, 200_000)), int(rng.integers(0, 200_000))
+        w, h = int(rng.integers(0, 3000)), int(rng.integers(0, 3000))
+        rows.append((s, t0, t0 + w, q0, q0 + h, 5000))
+    rows.append((0, 10_000, 150_000, 20_000, 170_000, 9))  # spans far more than 4096 cells
+    rows.append((1, 0, 120_000, 0, 90_000, 9))
+    rows.append((0, 5_000, 5_000, 6_000, 9_000, 1))        # empty: contains nothing
+    rows.append((1, 1023, 1025, 2047, 2049, 1))            # across cell edges
+    B = np.array(rows, dtype=np.int32)
+    Q = [(int(rng.integers(0, 2)), int(rng.integers(0, 210_000)), int(rng.integers(0, 210_000)))
+         for _ in range(20_000)]
+    for s, t0, t1, q0, q1, _ in rows[-4:] + rows[:50]:
+        for t in (t0 - 1, t0, t1 - 1, t1):
+            for q in (q0 - 1, q0, q1 - 1, q1):
+                if t >= 0 and q >= 0:
+                    Q.append((s, t, q))
+    Q = np.array(Q, dtype=np.int32)
+    got = sfe.test_committed_boxes(B, Q)
+    want = np.zeros(len(Q), dtype=bool)
+    for s, t0, t1, q0, q1, _ in rows:
+        want |= (Q[:, 0] == s) & (t0 <= Q[:, 1]) & (Q[:, 1] < t1) & (q0 <= Q[:, 2]) & (Q[:, 2] < q1)
+    assert np.array_equal(got, want)
+    assert want.sum() > 1000 and (~want).sum() > 1000
+    assert sfe.test_committed_boxes(B[:0], Q[:5]).sum() == 0
